@@ -1,0 +1,70 @@
+"""Dense numpy helpers for the tests (independent of the oracle and the library)."""
+import numpy as np
+
+import graphgen as gg
+
+
+def dense_laplacian(g: gg.Graph) -> np.ndarray:
+    """A = L_w + diag(d) straight from Eq. (1): A_ii = sum_j w_ij + d_i, A_ij = -w_ij."""
+    n = g.n
+    A = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(g.rowptr))
+    A[rows, g.col] = -g.w
+    A[np.arange(n), np.arange(n)] = -A.sum(axis=1)
+    if g.d is not None:
+        A[np.arange(n), np.arange(n)] += g.d
+    return A
+
+
+def prolongation(agg: np.ndarray, nH: int) -> np.ndarray:
+    """Piecewise-constant P: column l is the indicator of aggregate l."""
+    P = np.zeros((agg.size, nH))
+    P[np.arange(agg.size), agg] = 1.0
+    return P
+
+
+def random_graph(n: int, p: float, seed: int, wmax: int = 1, d_frac: float = 0.0, connected=True) -> gg.Graph:
+    """Erdos-Renyi-like graph with integer weights in [1, wmax]; a spanning path keeps it connected."""
+    rng = np.random.default_rng(seed)
+    edges = set()
+    if connected:
+        perm = rng.permutation(n)
+        for a, b in zip(perm[:-1], perm[1:]):
+            edges.add((min(a, b), max(a, b)))
+    for i in range(n):
+        for j in range(i + 1, n):
+            if rng.random() < p:
+                edges.add((i, j))
+    e = np.array(sorted(edges), dtype=np.int64).reshape(-1, 2)
+    w = rng.integers(1, wmax + 1, size=len(e)).astype(np.float64)
+    d = None
+    if d_frac > 0:
+        d = np.where(rng.random(n) < d_frac, rng.integers(1, 4, size=n).astype(np.float64), 0.0)
+        if not d.any():
+            d[0] = 1.0
+    return gg.csr_from_edges(n, e[:, 0], e[:, 1], w, d, name=f"rand{n}_{seed}")
+
+
+def path_graph(n: int) -> gg.Graph:
+    i = np.arange(n - 1)
+    return gg.csr_from_edges(n, i, i + 1, name=f"path{n}")
+
+
+def complete_graph(n: int) -> gg.Graph:
+    i, j = np.triu_indices(n, 1)
+    return gg.csr_from_edges(n, i, j, name=f"K{n}")
+
+
+def star_graph(n: int) -> gg.Graph:
+    return gg.csr_from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n), name=f"star{n}")
+
+
+def cheb_q(coef: np.ndarray, l0: float, l1: float, x: np.ndarray) -> np.ndarray:
+    """Evaluate sum_j c_j T_j(t(x)), t = (2x - l1 - l0)/(l1 - l0), with numpy's chebval."""
+    t = (2.0 * np.asarray(x) - l1 - l0) / (l1 - l0)
+    return np.polynomial.chebyshev.chebval(t, coef)
+
+
+def matrix_function(A: np.ndarray, f) -> np.ndarray:
+    lam, V = np.linalg.eigh(A)
+    return (V * f(lam)) @ V.T
