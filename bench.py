@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark: DOF/s solved to a 1e-8 relative residual on the 128^3 workload.
+
+A step is one pass of the whole method on one synthetic problem: amg_setup on
+the device-resident graph (validation, matching, Galerkin, smoother data,
+coarsest pseudo-inverse) followed by amg_solve (flexible CG + K-cycle with the
+polynomial smoother) to ||r|| <= 1e-8 ||b||, then amg_free.  value = DOF of
+all ranks per step / step time.  Workload: 3D 7-point graph Laplacian on a
+128^3 grid (2,097,152 vertices, unit weights, d_i = 1 on boundary-face
+vertices), degree-5 smoother, three matching passes per level, nu = 2 inner
+flexible-CG steps, seeded uniform[-1,1] right-hand side.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU runs (torchrun) solve independent replicas, one per rank (weak
+scaling, no data-path collective); the reference arm runs the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+WORKLOAD = "grid3d_128"
+WORKLOAD_DESC = ("128^3 7-point graph Laplacian, w=1, d=1 on boundary faces; degree-5 polynomial "
+                 "smoother, 3 matching passes/level, K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64)")
+METRIC = "DOF/s solved to 1e-8 rel. residual (setup + solve per step)"
+UNIT = "DOF/s"
+L2_BYTES = 129 * 2 ** 20
+PROFILE = os.path.join(ROOT, "profiles", "cheb_step_grid3d_128.txt")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    src = open(os.path.join(ROOT, "paper_1307_6305_gb300", "csrc", "solve.cu"), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused smoother step from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    for line in open(PROFILE):
+        if ":" in line and not line.startswith(" "):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_step(g, p, b):
+    import oracle
+
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"])
+    r = h.solve(b, tol=1e-8)
+    dt = time.perf_counter() - t0
+    assert h.status == 0 and r.status == 0, (h.status, r.status)
+    return dt, r
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    g, p = gg.workload(WORKLOAD)
+    b = gg.rhs(g.n, p["rhs_seeds"][0], gg.is_pure_laplacian(g))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            run_oracle_step(g, p, b)
+        times = [run_oracle_step(g, p, b)[0] for _ in range(args.steps)]
+        ms = 1e3 * sum(times) / len(times)
+        value = g.n / (ms / 1e3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": 1},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": "full workload per step (oracle setup + solve), single thread"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+
+    import paper_1307_6305_gb300 as amg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    rp = torch.as_tensor(g.rowptr, device=dev)
+    col = torch.as_tensor(g.col, device=dev)
+    w = torch.as_tensor(g.w, device=dev)
+    d = None if g.d is None else torch.as_tensor(g.d, device=dev)
+    bd = torch.as_tensor(b, device=dev)
+    xd = torch.zeros_like(bd)
+    in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + b.nbytes
+    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"])
+    state = {"launches": 0, "iters": [], "setup_ms": [], "solve_ms": [], "kt": [0, 0.0, 0.0]}
+
+    def step(timed_kernel: bool):
+        st, h = amg.amg_setup(g.n, rp, col, w, d, opts, amg.AMG_MEM_DEVICE, sp)
+        assert st == 0, amg.amg_last_error(None)
+        launches = amg.lib().amg_launch_count(h)
+        if timed_kernel:
+            amg.lib().amg_kernel_timing(h, 1)
+        info = amg.amg_info()
+        st = amg.amg_solve(h, bd, xd, 1, g.n, 1e-8, info)
+        assert st == 0, amg.amg_last_error(h)
+        launches += amg.lib().amg_launch_count(h)
+        if timed_kernel:
+            import ctypes as C
+
+            nl, ms, bpl = C.c_int64(), C.c_double(), C.c_double()
+            amg.lib().amg_kernel_timing_read(h, C.byref(nl), C.byref(ms), C.byref(bpl))
+            state["kt"][0] += nl.value
+            state["kt"][1] += ms.value
+            state["kt"][2] = bpl.value
+        amg.amg_free(h)
+        return launches, info
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    last_info = None
+    for _ in range(args.steps):
+        nl, last_info = step(True)
+        launches += nl
+        state["iters"].append(last_info.iterations)
+        state["setup_ms"].append(last_info.setup_ms)
+        state["solve_ms"].append(last_info.solve_ms)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = g.n * world / (ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
+    pin = lambda a: torch.as_tensor(a).pin_memory()
+    hrp, hcol, hw = pin(g.rowptr), pin(g.col), pin(g.w)
+    hd = None if g.d is None else pin(g.d)
+    hb = pin(b)
+    hx = torch.zeros_like(hb).pin_memory()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, h = amg.amg_setup(g.n, hrp, hcol, hw, hd, opts, amg.AMG_MEM_HOST, sp)
+        assert st == 0
+        st = amg.amg_solve(h, hb, hx, 1, g.n, 1e-8, None)
+        assert st == 0
+        amg.amg_free(h)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    nl, kms, bpl = state["kt"]
+    avg_ms = kms / max(nl, 1)
+    achieved = bpl / (avg_ms * 1e-3) / 1e9 if nl else None
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(),
+            "kernel": "k_cheb_step<double> (level 0: SELL-32 SpMV + Chebyshev recurrence step)",
+            "launches_timed": nl, "avg_launch_us": avg_ms * 1e3, "algorithmic_bytes_per_launch": bpl,
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)"}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        dt, r = run_oracle_step(g, p, b)
+        cpu = {"value": g.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"full workload once (setup + solve, {r.iterations} iterations), {dt:.1f} s single thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": 1, "nnz_offdiag": g.nnz,
+                   "l2": f"inputs {in_bytes / 2**20:.0f} MiB > 129 MiB L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations": state["iters"][-1], "setup_ms_host": statistics.median(state["setup_ms"]),
+        "solve_ms_host": statistics.median(state["solve_ms"]),
+        "e2e": {"value": g.n * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": b.nbytes, "ms_per_step": e2e_ms},
+        "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

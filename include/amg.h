@@ -1,0 +1,227 @@
+/*
+ * amg.h -- C ABI of the GB300 (sm_103a) aggregation-AMG solver for graph
+ * Laplacian systems A u = f, after Brannick, "Aggregation-based aggressive
+ * coarsening with polynomial smoothing".
+ *
+ * The operator is the bilinear form of Eq. (1):
+ *     (A u, v) = sum_{e=(i,j)} w_e (u_i - u_j)(v_i - v_j) + sum_i d_i u_i v_i,
+ * so A_ii = sum_j w_ij + d_i and A_ij = -w_ij.  The solver is flexible CG
+ * preconditioned by the nonlinear AMLI cycle (K-cycle, W(1,1)) of Sec. 4 over
+ * unsmoothed (piecewise-constant) aggregation coarse spaces (Sec. 2, Eq.
+ * (coarse)), with the smoother R = q_m(A), q_m the polynomial of best uniform
+ * approximation to 1/x on [lambda1/10, ||A||_inf] (Sec. 3, Eq. (1x-1-min)).
+ * Aggregates are built on the device by handshake matching (Sec. 2: a
+ * matching is the simplest graph partitioning), several passes per level;
+ * coarse operators are the Galerkin products P^T A P (Sec. 3 remark; Sec. 5:
+ * sums of fine entries over aggregate pairs).
+ *
+ * Conventions for every entry point:
+ *  - Status codes only; nothing throws across this boundary.  After an error
+ *    amg_last_error() describes it.
+ *  - Input arrays are borrowed for the duration of the call and never
+ *    retained; the handle owns every device buffer of the hierarchy.
+ *  - "Device pointer" means memory of the current CUDA device (cudaMalloc,
+ *    torch tensors on that device, managed memory).  Entry points that accept
+ *    either kind say so and classify pointers with cudaPointerGetAttributes.
+ *  - All work is issued on the handle's stream (see amg_setup); calls return
+ *    after that work has completed unless stated otherwise.
+ *  - A handle is not thread safe: calls on one handle must not overlap.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amg_handle_s *amg_handle;
+
+typedef enum {
+  AMG_OK = 0,
+  AMG_ERR_INVALID_ARG = 1,    /* bad pointer/size/option, malformed CSR           */
+  AMG_ERR_NOT_SYMMETRIC = 2,  /* pattern or weights not symmetric (exact)         */
+  AMG_ERR_SELF_LOOP = 3,      /* an entry (i, i) in the graph                      */
+  AMG_ERR_BAD_WEIGHT = 4,     /* w <= 0, d < 0, or a non-finite value              */
+  AMG_ERR_DISCONNECTED = 5,   /* pure Laplacian not connected, or a component
+                                 without any d_i > 0 (A singular beyond 1)         */
+  AMG_ERR_OOM = 6,            /* device allocation failed                          */
+  AMG_ERR_CUDA = 7,           /* CUDA runtime error / no usable device             */
+  AMG_ERR_NOT_CONVERGED = 8,  /* max_iters reached; x and info hold the last iterate */
+  AMG_ERR_BREAKDOWN = 9,      /* outer CG: d^T A d <= 0 or non-finite              */
+  AMG_ERR_TIMEOUT = 10,       /* a bounded device-side wait ran out                */
+  AMG_ERR_SETUP_STALL = 11    /* matching cannot coarsen a level of > 4096 vertices */
+} amg_status;
+
+enum { AMG_MEM_HOST = 0, AMG_MEM_DEVICE = 1 };
+enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1 };
+
+/* Solver options; amg_default_options() fills the paper's choices. */
+typedef struct {
+  int degree;          /* m, degree of q_m (Sec. 4 uses 4); 0..16                 */
+  int passes;          /* matching passes composed per level (~2^passes per aggregate) */
+  int coarse_max;      /* coarsen until n_k <= coarse_max; coarsest solved densely */
+  int max_levels;      /* cap on the number of levels                              */
+  int inner_iters;     /* nu: flexible-CG steps on coarse levels (2 = W-cycle)     */
+  int restart;         /* outer flexible CG window cleared every `restart` its (5) */
+  int max_iters;       /* outer iteration cap                                      */
+  int precision;       /* AMG_PREC_FP64: everything in fp64.  AMG_PREC_FP32: the
+                          whole preconditioner (smoother, transfers, coarse-level
+                          cycles) in fp32 inside fp64 outer CG; outer residual,
+                          outer dots/orthogonalisation and the coarsest dense
+                          solve stay fp64                                          */
+  double lambda0_ratio;/* lambda0 = ratio * ||A_k||_inf (Sec. 4: 1/10)             */
+  uint64_t hash_salt;  /* salt of the matching tie-break hash                      */
+} amg_options;
+
+/* Per-solve report (Sec. 4 reports iterations and grid/operator complexity). */
+typedef struct {
+  int iterations;             /* outer iterations (max over right-hand sides)      */
+  int converged;              /* 1 if every right-hand side reached tol            */
+  double rel_residual;        /* ||r_k|| / ||b|| of the recursive residual (max)   */
+  double true_rel_residual;   /* ||b - A x|| / ||b|| recomputed at the end (max)   */
+  int n_levels;
+  double grid_complexity;     /* sum_k n_k / n_0                                   */
+  double op_complexity;       /* sum_k nnz(A_k) / nnz(A_0), diagonal included     */
+  double setup_ms;            /* wall time of amg_setup                            */
+  double solve_ms;            /* wall time of this amg_solve call                  */
+  double *history;            /* caller buffer (host) or NULL: ||r_k||/||b|| of the
+                                 first right-hand side, k = 0, 1, ...              */
+  int history_cap;
+  int history_len;            /* entries written                                   */
+} amg_info;
+
+/* Fill *opt with defaults: degree 4, passes 3, coarse_max 64, max_levels 30,
+ * inner_iters 2, restart 5, max_iters 500, FP64, lambda0_ratio 0.1, salt 0. */
+void amg_default_options(amg_options *opt);
+
+/*
+ * Build the hierarchy on the device (Sec. 2-3; setup steps all run in CUDA
+ * kernels: validation, connectivity, matching passes, Galerkin sums, lambda1
+ * = ||A_k||_inf, the coarsest-level pseudo-inverse, the solve-phase layouts).
+ *
+ *  n            number of vertices, 1 <= n < 2^31
+ *  row_ptr      int64[n+1] CSR row offsets of the graph (row_ptr[0] = 0)
+ *  col_idx      int32[nnz] neighbours; strictly increasing within each row;
+ *               no self loops; the pattern is symmetric
+ *  w            double[nnz] edge weights w_ij > 0, w_ij == w_ji exactly
+ *  d            double[n] lower-order terms d_i >= 0, or NULL (pure Laplacian)
+ *  opt          options or NULL for defaults
+ *  mem_space    AMG_MEM_HOST: the four arrays are host memory;
+ *               AMG_MEM_DEVICE: they are device pointers
+ *  cuda_stream  cudaStream_t for all work of this handle (kept by the handle,
+ *               not owned), or NULL for the legacy default stream
+ *  out          receives the handle (NULL on failure)
+ * Errors, checked in this order: AMG_ERR_INVALID_ARG (sizes, pointers,
+ * options, row_ptr not monotone, column out of range or rows not strictly
+ * increasing), AMG_ERR_SELF_LOOP, AMG_ERR_NOT_SYMMETRIC, AMG_ERR_BAD_WEIGHT,
+ * AMG_ERR_DISCONNECTED, AMG_ERR_SETUP_STALL, AMG_ERR_OOM, AMG_ERR_CUDA.
+ */
+amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *w,
+                     const double *d, const amg_options *opt, int mem_space, void *cuda_stream,
+                     amg_handle *out);
+
+/*
+ * Solve A x = rhs for nrhs right-hand sides by flexible CG (Sec. 4: NPCG,
+ * window cleared every `restart` iterations) preconditioned by the K-cycle,
+ * from x0 = 0, until ||r_k|| <= tol ||b|| (recursive residual, fp64).
+ *
+ *  rhs, x   column j at rhs + j*ld, x + j*ld (column major, ld >= n); host or
+ *           device memory (each pointer classified independently); x is
+ *           output only.  For a pure Laplacian each right-hand side is first
+ *           projected to zero mean (the range of A is 1-perp, Sec. 1) and x is
+ *           returned with zero mean.
+ *  nrhs     >= 1; several right-hand sides are solved together, the
+ *           preconditioner applied to all of them in one multi-vector pass
+ *  info     optional report (may be NULL)
+ * Returns AMG_OK, AMG_ERR_NOT_CONVERGED (x holds the last iterate),
+ * AMG_ERR_BREAKDOWN, AMG_ERR_INVALID_ARG or AMG_ERR_CUDA.
+ */
+amg_status amg_solve(amg_handle h, const double *rhs, double *x, int nrhs, int64_t ld, double tol,
+                     amg_info *info);
+
+/* Release the hierarchy and every device buffer of h (NULL is a no-op). */
+void amg_free(amg_handle h);
+
+/* Description of the last error of h, or of the calling thread's last
+ * failed amg_setup/amg_match when h is NULL.  Owned by the library. */
+const char *amg_last_error(amg_handle h);
+
+/* ---------------------------------------------------------------------- */
+/* Introspection: copies of the device hierarchy into caller host buffers. */
+/* ---------------------------------------------------------------------- */
+
+int amg_num_levels(amg_handle h);
+/* vertices of level k, -1 if k is out of range */
+int64_t amg_level_n(amg_handle h, int k);
+/* stored off-diagonal entries of level k (each undirected edge twice) */
+int64_t amg_level_nnz(amg_handle h, int k);
+/* Level k operator A_k = P^T A_{k-1} P in CSR: rowptr[n+1], col[nnz] (strictly
+ * increasing per row), val[nnz] = off-diagonal a_ij = -W_ij, diag[n] = A_ii,
+ * dlow[n] = the lower-order term aggregated to this level (P^T d).  Any output
+ * pointer may be NULL.  Host buffers. */
+amg_status amg_level_csr(amg_handle h, int k, int64_t *rowptr, int32_t *col, double *val,
+                         double *diag, double *dlow);
+/* Composite aggregate map level k -> k+1 (k < levels-1): agg[n_k] in [0, n_{k+1}).
+ * Coarse ids rank the aggregates' smallest members.  Host buffer. */
+amg_status amg_level_agg(amg_handle h, int k, int32_t *agg);
+/* Smoother data of level k < levels-1: lambda0, lambda1 = ||A_k||_inf and the
+ * degree+1 Chebyshev coefficients of q_m in t = (2x - l1 - l0)/(l1 - l0).
+ * Any output pointer may be NULL. */
+amg_status amg_level_smoother(amg_handle h, int k, double *lam0, double *lam1, double *coef);
+
+/* ---------------------------------------------------------------------- */
+/* Single steps of the solve phase on one level (device fp64 vectors).     */
+/* In AMG_PREC_FP32 mode the level data used are the fp32 copies; vectors */
+/* are converted on entry and exit.  These run on the handle's stream and  */
+/* return after completion.                                                */
+/* ---------------------------------------------------------------------- */
+
+/* y = A_k x (Eq. (1) operator on level k). */
+amg_status amg_apply_spmv(amg_handle h, int k, const double *x, double *y);
+/* x = q_m(A_k) r by the Chebyshev three-term recurrence T_0 = r,
+ * T_1 = t(A) r, T_{j+1} = 2 t(A) T_j - T_{j-1}, x = sum_j c_j T_j (Sec. 3
+ * smoother R = q_m(A)); k < levels-1. */
+amg_status amg_apply_smoother(amg_handle h, int k, const double *r, double *x);
+/* r_H = P_k^T s: sum over each aggregate's members (Eq. (coarse)). */
+amg_status amg_apply_restrict(amg_handle h, int k, const double *s, double *rH);
+/* x += P_k e_H: every vertex adds its aggregate's value (Eq. (coarse)). */
+amg_status amg_apply_prolong_add(amg_handle h, int k, const double *eH, double *x);
+/* x = A_c^+ b on the coarsest level (Sec. 3: pseudo-inverse), fp64. */
+amg_status amg_apply_coarse_solve(amg_handle h, const double *b, double *x);
+/* z = K_k(r): one nonlinear AMLI (K-cycle) application at level k
+ * (pre-smooth, residual, restriction, nu inner flexible-CG steps or the
+ * coarsest solve, prolongation, residual, post-smooth). */
+amg_status amg_apply_kcycle(amg_handle h, int k, const double *r, double *z);
+
+/* One handshake matching pass (Sec. 2) on a device CSR graph whose entries
+ * carry matching weights s (double[nnz] > 0, symmetric); edge keys are
+ * (s_ij, splitmix64(salt ^ (lo << 32 | hi)), lo, hi), largest wins.
+ * Outputs (device): mate[n] (-1 unmatched), agg[n] coarse ids (rank of each
+ * pair's smaller vertex / singleton); *n_coarse and *rounds (host) receive the
+ * coarse size and the number of proposal rounds.  stream may be NULL. */
+amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *s,
+                     uint64_t salt, int32_t *mate, int32_t *agg, int64_t *n_coarse, int *rounds,
+                     void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement hooks.                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Enable (1) or disable (0) CUDA-event timing of every launch of the fused
+ * smoother-step kernel on level 0 (the dominant kernel) during amg_solve;
+ * enabling resets the accumulators. */
+amg_status amg_kernel_timing(amg_handle h, int enable);
+/* Accumulated launches, total device milliseconds and the algorithmic bytes
+ * of one launch (matrix + vectors touched once, see the library's notes). */
+amg_status amg_kernel_timing_read(amg_handle h, int64_t *launches, double *total_ms,
+                                  double *bytes_per_launch);
+/* Number of kernel launches issued by the last amg_setup/amg_solve on h. */
+int64_t amg_launch_count(amg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,207 @@
+// common.cuh -- internal declarations of the GB300 aggregation-AMG library.
+//
+// Data layout in HBM (one handle = one hierarchy):
+//   level k setup form : CSR of the off-diagonal entries (int64 row offsets,
+//                        int32 columns, fp64 values a_ij = -W_ij), fp64
+//                        diagonal and aggregated lower-order term.
+//   level k solve form : SELL-32 (slices of 32 consecutive rows = one warp,
+//                        column-major inside a slice, padded to the slice's
+//                        longest row) of the off-diagonal part plus a separate
+//                        diagonal, in fp64 and, in fp32 mode, fp32.
+//   transfers          : agg[n_k] (coarse id per vertex) for prolongation and
+//                        the CSR of aggregates (agg_ptr, members ascending) for
+//                        restriction; no floating-point atomics anywhere.
+//   coarsest level     : dense fp64 pseudo-inverse Z (n_c x n_c, row major).
+//   scalars            : per-level fp64 arrays on the device; the host never
+//                        reads them inside a cycle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "amg.h"
+
+namespace amg {
+
+constexpr int kSlice = 32;        // SELL slice height (warp width)
+constexpr int kMaxDegree = 16;    // largest smoother degree
+constexpr int kMaxInner = 8;      // largest nu
+constexpr int kMaxWindow = 16;    // largest outer restart window
+constexpr int kMaxDots = 8;       // dots per fused reduction
+constexpr int kRedBlocks = 608;   // partial sums per reduction = 4 x 152 SMs
+constexpr int kStallMaxCoarse = 4096;
+constexpr double kStallRatio = 0.95;
+
+// ---------------------------------------------------------------------------
+// error plumbing: status + message, no exceptions across the C ABI
+// ---------------------------------------------------------------------------
+struct Error {
+  amg_status code = AMG_OK;
+  std::string msg;
+};
+
+#define AMG_CUDA_TRY(expr)                                                             \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      return ::amg::fail(e_ == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA, \
+                         std::string(#expr) + ": " + cudaGetErrorString(e_));          \
+    }                                                                                  \
+  } while (0)
+
+#define AMG_TRY(expr)                  \
+  do {                                 \
+    amg_status s_ = (expr);            \
+    if (s_ != AMG_OK) return s_;       \
+  } while (0)
+
+amg_status fail(amg_status code, const std::string &msg);  // records thread-local error
+const std::string &thread_error();
+
+// ---------------------------------------------------------------------------
+// device memory: one library-owned stream-ordered pool per device
+// ---------------------------------------------------------------------------
+struct Arena {
+  cudaStream_t stream = nullptr;
+  std::vector<void *> blocks;
+  size_t bytes = 0;
+  amg_status alloc(void **p, size_t bytes);
+  template <typename T>
+  amg_status get(T **p, size_t count) {
+    return alloc(reinterpret_cast<void **>(p), count * sizeof(T));
+  }
+  void release();  // frees every block (stream ordered) and synchronises
+};
+amg_status pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// matrices
+// ---------------------------------------------------------------------------
+struct Csr {  // off-diagonal part; diagonal kept separately
+  int n = 0;
+  int64_t nnz = 0;
+  int64_t *rowptr = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr;
+};
+
+struct Sell {  // SELL-32 off-diagonal part + diagonal
+  int n = 0;
+  int nslices = 0;
+  int64_t stored = 0;  // padded entries
+  int64_t *sptr = nullptr;
+  int32_t *scol = nullptr;
+  double *val64 = nullptr;
+  float *val32 = nullptr;
+  double *diag64 = nullptr;
+  float *diag32 = nullptr;
+};
+
+template <typename T>
+struct SellView {
+  int n;
+  const int64_t *__restrict__ sptr;
+  const int32_t *__restrict__ scol;
+  const T *__restrict__ val;
+  const T *__restrict__ diag;
+};
+
+struct Level {
+  int n = 0;
+  Csr A;                 // setup form
+  double *diag = nullptr;
+  double *dlow = nullptr;
+  Sell S;                // solve form
+  // map to the next level
+  int nH = 0;
+  int32_t *agg = nullptr;
+  int32_t *agg_ptr = nullptr;
+  int32_t *agg_mem = nullptr;
+  // smoother: q_m on [lam0, lam1] in the Chebyshev basis of t(x)
+  double lam0 = 0, lam1 = 0;
+  double coef[kMaxDegree + 1] = {};
+  // per-level device scalars and work vectors (element type = cycle precision)
+  double *scal = nullptr;  // [64]
+  void *s = nullptr, *Ta = nullptr, *Tb = nullptr;  // cycle scratch
+  void *b = nullptr, *x = nullptr, *r = nullptr;    // inner flexible CG
+  void *D[kMaxInner] = {}, *W[kMaxInner] = {};
+};
+
+// fused reduction state (deterministic two-stage: per-block partials, last
+// block folds them in block order)
+struct RedState {
+  double *partial = nullptr;   // [kRedBlocks * kMaxDots]
+  unsigned int *ticket = nullptr;
+};
+
+struct Timing {
+  bool enabled = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  size_t used = 0;
+  int64_t launches = 0;
+  double total_ms = 0;
+};
+
+struct Options {
+  amg_options o;
+};
+
+}  // namespace amg
+
+struct amg_handle_s {
+  amg_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0;
+  bool pure = false;
+  int L = 0;
+  std::vector<amg::Level> lv;
+  amg::Arena arena;
+  amg::RedState red;
+  // coarsest pseudo-inverse
+  int nc = 0;
+  double *Z = nullptr;
+  // outer flexible CG (fp64) on level 0
+  double *ob = nullptr, *ox = nullptr, *or_ = nullptr, *oz = nullptr;
+  double *oD[amg::kMaxWindow] = {}, *oQ[amg::kMaxWindow] = {};
+  double *oscal = nullptr;   // [256]
+  double *h_pinned = nullptr;  // host mirror of a few scalars
+  // fp32 mode: level-0 fp32 buffers for the preconditioner input/output
+  float *r32 = nullptr, *z32 = nullptr;
+  // coarsest conversion buffers (fp32 mode)
+  double *cb64 = nullptr, *cx64 = nullptr;
+  double setup_ms = 0;
+  double grid_complexity = 0, op_complexity = 0;
+  int64_t launches = 0;
+  amg::Timing timing;
+  std::string err;
+};
+
+namespace amg {
+// setup.cu
+amg_status build_hierarchy(amg_handle_s *h, int64_t n, const int64_t *rowptr, const int32_t *col,
+                           const double *w, const double *d);
+amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32_t *col,
+                      const double *s, uint64_t salt, int32_t *mate, int32_t *agg, int *nH,
+                      int *rounds, int64_t *launches);
+// solve.cu
+amg_status allocate_solve_buffers(amg_handle_s *h);
+amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol,
+                     amg_info *info, int *iters, double *rel, double *true_rel, int *converged);
+amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y);
+amg_status apply_smoother(amg_handle_s *h, int k, const double *r, double *x);
+amg_status apply_restrict(amg_handle_s *h, int k, const double *s, double *rH);
+amg_status apply_prolong_add(amg_handle_s *h, int k, const double *eH, double *x);
+amg_status apply_coarse_solve(amg_handle_s *h, const double *b, double *x);
+amg_status apply_kcycle(amg_handle_s *h, int k, const double *r, double *z);
+// scan.cu helpers (in setup.cu)
+amg_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st,
+                              int64_t *total_host);
+amg_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st,
+                              int64_t *total_host);
+}  // namespace amg

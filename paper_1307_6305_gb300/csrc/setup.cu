@@ -1,0 +1,1097 @@
+// setup.cu -- device-side setup of the aggregation hierarchy.
+//
+// Every step of the setup runs in the kernels below; the host only sizes
+// buffers and loops over levels/passes/rounds:
+//   validation and connectivity of the input graph (Eq. (1) needs a
+//   connected graph for the pure Laplacian, Sec. 1);
+//   assembly A_ii = sum_j w_ij + d_i, A_ij = -w_ij (Eq. (1));
+//   handshake matching passes (Sec. 2: a matching is the simplest graph
+//   partitioning) with the symmetric strength |a_ij|/sqrt(a_ii a_jj) as edge
+//   weight and a splitmix64 hash as tie-break;
+//   Galerkin A_H = P^T A P for piecewise-constant P (Sec. 3 remark, Sec. 5:
+//   sums of fine entries over aggregate pairs), one pass at a time, so each
+//   coarse row merges at most two fine rows;
+//   lambda1 = ||A_k||_inf (Sec. 3), the Chebyshev coefficients of q_m
+//   (host, closed form, a few flops), the SELL-32 solve layout and the dense
+//   pseudo-inverse of the coarsest operator (Sec. 3, A_H^+).
+#include <math.h>
+
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace amg {
+
+#define LAUNCH_CHECK(cnt)                                                          \
+  do {                                                                             \
+    if (cnt) ++*(cnt);                                                             \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+static inline unsigned blocks_for(int64_t n, int threads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (reduce-then-scan, 2048 elements per block)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+template <typename T>
+__global__ void k_scan_tile(const T *__restrict__ in, T *__restrict__ out, T *__restrict__ bsum,
+                            int64_t n) {
+  __shared__ T wtot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  T v[kScanPer];
+  T local = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : T(0);
+    local += v[k];
+  }
+  T inc = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wtot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T t = (lane < kScanThreads / 32) ? wtot[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    if (lane < kScanThreads / 32) wtot[lane] = t;
+  }
+  __syncthreads();
+  T run = inc - local + (warp > 0 ? wtot[warp - 1] : T(0));
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = wtot[kScanThreads / 32 - 1];
+}
+
+template <typename T>
+__global__ void k_scan_add(T *__restrict__ out, const T *__restrict__ off, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += off[i / kScanTile];
+}
+
+template <typename T>
+static amg_status scan_rec(const T *in, T *out, int64_t n, cudaStream_t st, T *total_dev) {
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb < 1) nb = 1;
+  T *bsum = nullptr;
+  AMG_TRY(pool_alloc((void **)&bsum, sizeof(T) * nb, st));
+  k_scan_tile<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, bsum, n);
+  LAUNCH_CHECK((int64_t *)nullptr);
+  if (nb == 1) {
+    AMG_CUDA_TRY(cudaMemcpyAsync(total_dev, bsum, sizeof(T), cudaMemcpyDeviceToDevice, st));
+  } else {
+    T *boff = nullptr;
+    AMG_TRY(pool_alloc((void **)&boff, sizeof(T) * nb, st));
+    AMG_TRY(scan_rec<T>(bsum, boff, nb, st, total_dev));
+    k_scan_add<T><<<blocks_for(n, 256), 256, 0, st>>>(out, boff, n);
+    LAUNCH_CHECK((int64_t *)nullptr);
+    pool_free(boff, st);
+  }
+  pool_free(bsum, st);
+  return AMG_OK;
+}
+
+template <typename T>
+static amg_status scan_total(const T *in, T *out, int64_t n, cudaStream_t st, int64_t *total_host) {
+  T *tot = nullptr;
+  AMG_TRY(pool_alloc((void **)&tot, sizeof(T), st));
+  AMG_TRY(scan_rec<T>(in, out, n, st, tot));
+  T t = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&t, tot, sizeof(T), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  pool_free(tot, st);
+  if (total_host) *total_host = (int64_t)t;
+  return AMG_OK;
+}
+
+amg_status exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st,
+                              int64_t *total_host) {
+  return scan_total<long long>((const long long *)in, (long long *)out, n, st, total_host);
+}
+amg_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st,
+                              int64_t *total_host) {
+  return scan_total<int>(in, out, n, st, total_host);
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+enum : unsigned {
+  F_ROWPTR = 1u, F_RANGE = 2u, F_ORDER = 4u, F_SELF = 8u, F_SYM = 16u, F_W = 32u, F_D = 64u
+};
+
+__global__ void k_check_rowptr(int64_t n, const int64_t *__restrict__ rp, unsigned *flags) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  bool bad = (i == 0) ? (rp[0] != 0) : (rp[i] < rp[i - 1]);
+  if (bad) atomicOr(flags, F_ROWPTR);
+}
+
+__global__ void k_check_entries(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                const double *__restrict__ w, const double *__restrict__ d,
+                                unsigned *flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned f = 0;
+  const int64_t a = rp[i], b = rp[i + 1];
+  for (int64_t p = a; p < b; ++p) {
+    const int c = col[p];
+    if (c < 0 || c >= n) f |= F_RANGE;
+    else if (c == i) f |= F_SELF;
+    if (p > a && c <= col[p - 1]) f |= F_ORDER;
+    const double wp = w[p];
+    if (!(wp > 0.0) || !isfinite(wp)) f |= F_W;
+  }
+  if (d) {
+    const double di = d[i];
+    if (!(di >= 0.0) || !isfinite(di)) f |= F_D;
+  }
+  if (f) atomicOr(flags, f);
+}
+
+// symmetric pattern and values: (i, j, w) needs (j, i, w) with w equal bit for bit
+__global__ void k_check_symmetry(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const double *__restrict__ w, unsigned *flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool bad = false;
+  for (int64_t p = rp[i]; p < rp[i + 1] && !bad; ++p) {
+    const int j = col[p];
+    int64_t lo = rp[j], hi = rp[j + 1] - 1, hit = -1;
+    while (lo <= hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      int c = col[mid];
+      if (c == i) { hit = mid; break; }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (hit < 0 || w[hit] != w[p]) bad = true;
+  }
+  if (bad) atomicOr(flags, F_SYM);
+}
+
+// ---------------------------------------------------------------------------
+// connectivity: root hooking with atomicMin + pointer jumping
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cc_root(const int *parent, int v) {
+  int p = parent[v];
+  while (p != v) {
+    v = p;
+    p = parent[v];
+  }
+  return v;
+}
+
+__global__ void k_cc_init(int n, int *parent) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) parent[i] = i;
+}
+
+__global__ void k_cc_hook(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                          int *parent, int *changed) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = col[p];
+    if (j <= i) continue;
+    int ri = cc_root(parent, i), rj = cc_root(parent, j);
+    if (ri != rj) {
+      atomicMin(&parent[max(ri, rj)], min(ri, rj));
+      *changed = 1;
+    }
+  }
+}
+
+__global__ void k_cc_jump(int n, int *parent) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) parent[i] = cc_root(parent, i);
+}
+
+// components: count roots; with lower-order terms every component needs d > 0
+__global__ void k_cc_mark(int n, const int *parent, const double *d, int *posd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && d && d[i] > 0.0) posd[parent[i]] = 1;
+}
+__global__ void k_cc_count(int n, const int *parent, const int *posd, int pure, int *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || parent[i] != i) return;
+  atomicAdd(&out[0], 1);
+  if (!pure && !posd[i]) atomicAdd(&out[1], 1);
+}
+
+// ---------------------------------------------------------------------------
+// assembly, Eq. (1): a_ij = -w_ij, A_ii = sum_j w_ij + d_i (row order)
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(int n, const int64_t *__restrict__ rp, const double *__restrict__ w,
+                           const double *__restrict__ d, double *__restrict__ val,
+                           double *__restrict__ diag, double *__restrict__ dlow) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    val[p] = -w[p];
+    s += w[p];
+  }
+  const double di = d ? d[i] : 0.0;
+  dlow[i] = di;
+  diag[i] = s + di;
+}
+
+// ---------------------------------------------------------------------------
+// handshake matching
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t edge_hash(uint64_t salt, int a, int b) {
+  const uint64_t lo = (uint64_t)min(a, b), hi = (uint64_t)max(a, b);
+  return splitmix64(salt ^ ((lo << 32) | hi));
+}
+
+// matching weight of each stored edge: |a_ij| / sqrt(a_ii a_jj)
+__global__ void k_strength(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ diag,
+                           double *__restrict__ s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double di = diag[i];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s[p] = -val[p] / sqrt(di * diag[col[p]]);
+}
+
+__global__ void k_match_init(int n, int *mate) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) mate[i] = -1;
+}
+
+// each unmatched vertex points across its largest-key edge to an unmatched
+// neighbour; key = (s_ij, hash, lo, hi) compared lexicographically
+__global__ void k_propose(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                          const double *__restrict__ s, uint64_t salt, const int *__restrict__ mate,
+                          int *__restrict__ ptr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int best = -1;
+  if (mate[i] < 0) {
+    double bw = 0.0;
+    uint64_t bh = 0;
+    bool bh_ok = false;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = col[p];
+      if (mate[j] >= 0) continue;
+      const double wj = s[p];
+      if (best < 0) { best = j; bw = wj; bh_ok = false; continue; }
+      bool take;
+      if (wj != bw) {
+        take = wj > bw;
+      } else {
+        if (!bh_ok) { bh = edge_hash(salt, i, best); bh_ok = true; }
+        const uint64_t hj = edge_hash(salt, i, j);
+        if (hj != bh) {
+          take = hj > bh;
+        } else {
+          const int lj = min(i, j), hj2 = max(i, j), lb = min(i, best), hb = max(i, best);
+          take = (lj != lb) ? (lj > lb) : (hj2 > hb);
+        }
+      }
+      if (take) {
+        best = j;
+        bw = wj;
+        bh_ok = false;
+      }
+    }
+  }
+  ptr[i] = best;
+}
+
+__global__ void k_accept(int n, const int *__restrict__ ptr, int *__restrict__ mate, int *added) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int hit = 0;
+  if (i < n) {
+    const int p = ptr[i];
+    if (p >= 0 && ptr[p] == i) {
+      mate[i] = p;
+      hit = 1;
+    }
+  }
+  hit = __syncthreads_count(hit);
+  if (threadIdx.x == 0 && hit) atomicAdd(added, hit);
+}
+
+__global__ void k_rep_flags(int n, const int *__restrict__ mate, int *__restrict__ rep) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rep[i] = (mate[i] < 0 || i < mate[i]) ? 1 : 0;
+}
+
+__global__ void k_coarse_ids(int n, const int *__restrict__ mate, const int *__restrict__ id,
+                             int *__restrict__ agg, int *__restrict__ m0, int *__restrict__ m1) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = mate[i];
+  const bool rep = (m < 0 || i < m);
+  if (rep) {
+    agg[i] = id[i];
+    if (m0) {
+      m0[id[i]] = i;
+      m1[id[i]] = m;
+    }
+  } else {
+    agg[i] = id[m];
+  }
+}
+
+static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, const int32_t *col,
+                             const double *s, uint64_t salt, int32_t *mate, int32_t *agg, int *m0,
+                             int *m1, int *nH_out, int *rounds_out, int64_t *launches) {
+  int *ptr = nullptr, *added = nullptr, *rep = nullptr, *id = nullptr;
+  AMG_TRY(pool_alloc((void **)&ptr, sizeof(int) * (size_t)std::max(n, 1), st));
+  AMG_TRY(pool_alloc((void **)&added, sizeof(int) * 4, st));
+  const unsigned nb = blocks_for(n, 256);
+  k_match_init<<<nb, 256, 0, st>>>(n, mate);
+  LAUNCH_CHECK(launches);
+  // Rounds are launched in batches: once a round adds no pair every later
+  // round is a no-op, so speculative rounds never change the result.
+  int rounds = 0;
+  int h_added[4] = {0, 0, 0, 0};
+  const int kBatch = 2;
+  for (;;) {
+    AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * kBatch, st));
+    for (int b = 0; b < kBatch; ++b) {
+      k_propose<<<nb, 256, 0, st>>>(n, rowptr, col, s, salt, mate, ptr);
+      LAUNCH_CHECK(launches);
+      k_accept<<<nb, 256, 0, st>>>(n, ptr, mate, added + b);
+      LAUNCH_CHECK(launches);
+    }
+    AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * kBatch, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    bool done = false;
+    for (int b = 0; b < kBatch; ++b) {
+      ++rounds;
+      if (h_added[b] == 0) { done = true; break; }
+    }
+    if (done) break;
+    if (rounds > 4 * n + 8) return fail(AMG_ERR_CUDA, "matching did not terminate");
+  }
+  AMG_TRY(pool_alloc((void **)&rep, sizeof(int) * (size_t)std::max(n, 1), st));
+  AMG_TRY(pool_alloc((void **)&id, sizeof(int) * (size_t)std::max(n, 1), st));
+  k_rep_flags<<<nb, 256, 0, st>>>(n, mate, rep);
+  LAUNCH_CHECK(launches);
+  int64_t nH = 0;
+  AMG_TRY(exclusive_scan_i32(rep, id, n, st, &nH));
+  if (launches) *launches += 2;
+  k_coarse_ids<<<nb, 256, 0, st>>>(n, mate, id, agg, m0, m1);
+  LAUNCH_CHECK(launches);
+  pool_free(ptr, st);
+  pool_free(added, st);
+  pool_free(rep, st);
+  pool_free(id, st);
+  if (nH_out) *nH_out = (int)nH;
+  if (rounds_out) *rounds_out = rounds;
+  return AMG_OK;
+}
+
+amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32_t *col,
+                      const double *s, uint64_t salt, int32_t *mate, int32_t *agg, int *nH_out,
+                      int *rounds_out, int64_t *launches) {
+  return match_core(st, n, rowptr, col, s, salt, mate, agg, nullptr, nullptr, nH_out, rounds_out,
+                    launches);
+}
+
+__global__ void k_widen(int n, const int *a, int64_t *b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+__global__ void k_max_abs(int n, const double *a, unsigned long long *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = (i < n) ? fabs(a[i]) : 0.0;
+  if (!(v == v)) v = 1.0;  // NaN counts as non-zero (rejected earlier anyway)
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin for one matching pass: coarse row I merges the rows of its
+// members m0 < m1 (m1 = -1 for a singleton).  W_IJ sums the members' entries
+// in order (m0's row, then m1's row, CSR order), diag_I = sum_J W_IJ (J
+// ascending) + d_I, d_I = d_m0 + d_m1.
+// ---------------------------------------------------------------------------
+__global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, const int *__restrict__ m0,
+                              const int *__restrict__ m1, int64_t *__restrict__ len) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  int a = m0[I], b = m1[I];
+  int64_t l = rp[a + 1] - rp[a];
+  if (b >= 0) l += rp[b + 1] - rp[b];
+  len[I] = l;
+}
+
+// gather mapped entries of the coarse row into its segment, stable-sort by J,
+// count distinct J != I
+__global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const double *__restrict__ val, const int *__restrict__ agg,
+                              const int *__restrict__ m0, const int *__restrict__ m1,
+                              const int64_t *__restrict__ seg, int *__restrict__ keyJ,
+                              double *__restrict__ kval, int *__restrict__ count) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  const int64_t s0 = seg[I];
+  int64_t t = s0;
+  const int mem[2] = {m0[I], m1[I]};
+  for (int q = 0; q < 2; ++q) {
+    const int v = mem[q];
+    if (v < 0) continue;
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
+      keyJ[t] = agg[col[p]];
+      kval[t] = val[p];
+      ++t;
+    }
+  }
+  const int64_t len = t - s0;
+  for (int64_t a = 1; a < len; ++a) {  // stable insertion sort by J
+    const int kj = keyJ[s0 + a];
+    const double kv = kval[s0 + a];
+    int64_t b = a - 1;
+    while (b >= 0 && keyJ[s0 + b] > kj) {
+      keyJ[s0 + b + 1] = keyJ[s0 + b];
+      kval[s0 + b + 1] = kval[s0 + b];
+      --b;
+    }
+    keyJ[s0 + b + 1] = kj;
+    kval[s0 + b + 1] = kv;
+  }
+  int c = 0;
+  for (int64_t a = 0; a < len; ++a) {
+    const int J = keyJ[s0 + a];
+    if (J != I && (a == 0 || keyJ[s0 + a - 1] != J)) ++c;
+  }
+  count[I] = c;
+}
+
+__global__ void k_pair_emit(int nH, const int64_t *__restrict__ seg, const int *__restrict__ keyJ,
+                            const double *__restrict__ kval, const int64_t *__restrict__ rpH,
+                            const double *__restrict__ dlow, const int *__restrict__ m0,
+                            const int *__restrict__ m1, int32_t *__restrict__ colH,
+                            double *__restrict__ valH, double *__restrict__ diagH,
+                            double *__restrict__ dlowH) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  const int64_t s0 = seg[I], s1 = seg[I + 1];
+  int64_t o = rpH[I];
+  double wsum = 0.0;
+  int64_t a = s0;
+  while (a < s1) {
+    const int J = keyJ[a];
+    double acc = 0.0;
+    int64_t b = a;
+    for (; b < s1 && keyJ[b] == J; ++b) acc += -kval[b];
+    if (J != I) {
+      colH[o] = J;
+      valH[o] = -acc;
+      ++o;
+      wsum += acc;
+    }
+    a = b;
+  }
+  double dI = 0.0;
+  dI += dlow[m0[I]];
+  if (m1[I] >= 0) dI += dlow[m1[I]];
+  dlowH[I] = dI;
+  diagH[I] = wsum + dI;
+}
+
+__global__ void k_compose(int n, int *__restrict__ comp, const int *__restrict__ aggp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) comp[i] = aggp[comp[i]];
+}
+
+// aggregate membership lists (restriction): counts, then placement, then a
+// per-aggregate sort so that members are ascending
+__global__ void k_agg_count(int n, const int *__restrict__ agg, int *__restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[agg[i]], 1);
+}
+__global__ void k_agg_place(int n, const int *__restrict__ agg, const int *__restrict__ ptr,
+                            int *__restrict__ fill, int *__restrict__ mem) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int I = agg[i];
+  mem[ptr[I] + atomicAdd(&fill[I], 1)] = i;
+}
+__global__ void k_agg_sort(int nH, const int *__restrict__ ptr, int *__restrict__ mem) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  const int a0 = ptr[I], a1 = ptr[I + 1];
+  for (int a = a0 + 1; a < a1; ++a) {
+    int v = mem[a], b = a - 1;
+    while (b >= a0 && mem[b] > v) { mem[b + 1] = mem[b]; --b; }
+    mem[b + 1] = v;
+  }
+}
+
+// lambda1 = ||A||_inf = max_i (|a_ii| + sum_j |a_ij|), summed in row order
+__global__ void k_norm_inf(int n, const int64_t *__restrict__ rp, const double *__restrict__ val,
+                           const double *__restrict__ diag, unsigned long long *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (i < n) {
+    s = fabs(diag[i]);
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += fabs(val[p]);
+  }
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+// ---------------------------------------------------------------------------
+// SELL-32 conversion
+// ---------------------------------------------------------------------------
+__global__ void k_sell_width(int n, int nslices, const int64_t *__restrict__ rp,
+                             int64_t *__restrict__ slen) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int row = s * kSlice + lane;
+  int deg = 0;
+  if (s < nslices && row < n) deg = (int)(rp[row + 1] - rp[row]);
+  deg = __reduce_max_sync(0xffffffffu, deg);
+  if (s < nslices && lane == 0) slen[s] = (int64_t)deg * kSlice;
+}
+
+__global__ void k_sell_fill(int n, int nslices, const int64_t *__restrict__ rp,
+                            const int32_t *__restrict__ col, const double *__restrict__ val,
+                            const int64_t *__restrict__ sptr, int32_t *__restrict__ scol,
+                            double *__restrict__ sval) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = row >> 5, lane = row & 31;
+  if (s >= nslices) return;
+  const int64_t base = sptr[s];
+  const int w = (int)((sptr[s + 1] - base) / kSlice);
+  int k = 0;
+  if (row < n) {
+    for (int64_t p = rp[row]; p < rp[row + 1]; ++p, ++k) {
+      scol[base + (int64_t)k * kSlice + lane] = col[p];
+      sval[base + (int64_t)k * kSlice + lane] = val[p];
+    }
+  }
+  for (; k < w; ++k) {  // padding: zero weight on the row itself
+    scol[base + (int64_t)k * kSlice + lane] = row < n ? row : 0;
+    sval[base + (int64_t)k * kSlice + lane] = 0.0;
+  }
+}
+
+__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: dense A_c, shifted M = A_c + alpha 1 1^T for a pure
+// Laplacian (alpha = trace / n^2), in-place Gauss-Jordan inverse (M is SPD:
+// no pivoting), Z = M^{-1} - 1 1^T / (alpha n^2) = A_c^+.
+// ---------------------------------------------------------------------------
+__global__ void k_dense(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                        const double *__restrict__ val, const double *__restrict__ diag,
+                        double shift, double *__restrict__ M) {
+  int i = blockIdx.x;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) M[(int64_t)i * n + j] = shift;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    M[(int64_t)i * n + i] += diag[i];
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) M[(int64_t)i * n + col[p]] += val[p];
+  }
+}
+
+__global__ void k_trace(int n, const double *__restrict__ diag, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += diag[i];
+    *out = s;
+  }
+}
+
+// one Gauss-Jordan pivot step, reading Min and writing Mout
+__global__ void k_gj_step(int n, int p, const double *__restrict__ Min, double *__restrict__ Mout,
+                          double tiny, int *singular) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  const double piv = Min[(int64_t)p * n + p];
+  if (idx == 0 && !(piv > tiny)) *singular = 1;
+  const double inv = 1.0 / piv;
+  double out;
+  if (i == p) {
+    out = (j == p) ? inv : Min[(int64_t)p * n + j] * inv;
+  } else {
+    const double f = Min[(int64_t)i * n + p];
+    out = (j == p) ? -f * inv : Min[(int64_t)i * n + j] - f * (Min[(int64_t)p * n + j] * inv);
+  }
+  Mout[idx] = out;
+}
+
+__global__ void k_unshift(int64_t nn, double c, double *__restrict__ Z) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nn) Z[i] -= c;
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static void closed_form_coefficients(int m, double l0, double l1, double *c) {
+  // Best uniform approximation to 1/x on [l0, l1] (Eq. (1x-1-min)).  With
+  // t = (2x - l1 - l0)/(l1 - l0), 1/x = 2/(l1 - l0) * 1/(t + a),
+  // a = (l1 + l0)/(l1 - l0), delta = a - sqrt(a^2 - 1); the best degree-m
+  // approximant of 1/(t + a) in Chebyshev form keeps the first m terms of
+  // the expansion 1/(t+a) = 4 delta/(1 - delta^2) * sum' (-delta)^k T_k and
+  // replaces the last by (-1)^m 4 delta^(m+1)/(1 - delta^2)^2 (equioscillation
+  // with m+2 alternation points including both ends; its error level is
+  // delta^m (kappa - 1)/2 / l1 as stated in Sec. 3).
+  const double a = (l1 + l0) / (l1 - l0);
+  const double dl = a - sqrt(a * a - 1.0);
+  const double om = 1.0 - dl * dl;
+  const double scale = 2.0 / (l1 - l0);
+  if (m == 0) {
+    c[0] = scale * 2.0 * dl * (1.0 + dl * dl) / (om * om);
+    return;
+  }
+  c[0] = scale * 2.0 * dl / om;
+  double pw = 1.0;
+  for (int k = 1; k < m; ++k) {
+    pw *= -dl;
+    c[k] = scale * 4.0 * dl * pw / om;
+  }
+  pw *= -dl;
+  c[m] = scale * 4.0 * dl * pw / (om * om);
+}
+
+namespace {
+struct LevelBuild {
+  Csr A;
+  double *diag = nullptr, *dlow = nullptr;
+};
+}  // namespace
+
+static amg_status alloc_persist(amg_handle_s *h, void **p, size_t bytes) {
+  return h->arena.alloc(p, bytes);
+}
+
+// one matching pass + Galerkin on `cur` (owned temporaries in `next`)
+static amg_status coarsen_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuild &next, int *aggp,
+                               int *nH_out) {
+  cudaStream_t st = h->stream;
+  const int n = cur.A.n;
+  const unsigned nb = blocks_for(n, 256);
+  double *s = nullptr;
+  int *mate = nullptr;
+  AMG_TRY(pool_alloc((void **)&s, sizeof(double) * (size_t)std::max<int64_t>(cur.A.nnz, 1), st));
+  k_strength<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
+  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(pool_alloc((void **)&mate, sizeof(int) * (size_t)std::max(n, 1), st));
+  int *m0 = nullptr, *m1 = nullptr;
+  AMG_TRY(pool_alloc((void **)&m0, sizeof(int) * (size_t)std::max(n, 1), st));
+  AMG_TRY(pool_alloc((void **)&m1, sizeof(int) * (size_t)std::max(n, 1), st));
+  int nH = 0, rounds = 0;
+  AMG_TRY(match_core(st, n, cur.A.rowptr, cur.A.col, s, h->opt.hash_salt, mate, aggp, m0, m1, &nH,
+                     &rounds, &h->launches));
+  pool_free(s, st);
+  pool_free(mate, st);
+  // Galerkin
+  const unsigned nbH = blocks_for(nH, 256);
+  int64_t *seglen = nullptr, *seg = nullptr;
+  AMG_TRY(pool_alloc((void **)&seglen, sizeof(int64_t) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&seg, sizeof(int64_t) * (size_t)(nH + 1), st));
+  k_pair_seglen<<<nbH, 256, 0, st>>>(nH, cur.A.rowptr, m0, m1, seglen);
+  LAUNCH_CHECK(&h->launches);
+  AMG_CUDA_TRY(cudaMemsetAsync(seglen + nH, 0, sizeof(int64_t), st));
+  int64_t segtot = 0;
+  AMG_TRY(exclusive_scan_i64(seglen, seg, nH + 1, st, &segtot));
+  int *keyJ = nullptr, *count = nullptr;
+  double *kval = nullptr;
+  AMG_TRY(pool_alloc((void **)&keyJ, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
+  AMG_TRY(pool_alloc((void **)&kval, sizeof(double) * (size_t)std::max<int64_t>(segtot, 1), st));
+  AMG_TRY(pool_alloc((void **)&count, sizeof(int64_t) * (size_t)(nH + 1), st));
+  k_pair_gather<<<blocks_for(nH, 128), 128, 0, st>>>(nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, m0, m1, seg, keyJ,
+                                      kval, count);
+  LAUNCH_CHECK(&h->launches);
+  // widen counts to int64 for the row-offset scan
+  int64_t *cnt64 = nullptr;
+  AMG_TRY(pool_alloc((void **)&cnt64, sizeof(int64_t) * (size_t)(nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt64, 0, sizeof(int64_t) * (size_t)(nH + 1), st));
+  k_widen<<<nbH, 256, 0, st>>>(nH, count, cnt64);
+  LAUNCH_CHECK(&h->launches);
+  next.A.n = nH;
+  AMG_TRY(pool_alloc((void **)&next.A.rowptr, sizeof(int64_t) * (size_t)(nH + 1), st));
+  int64_t nnzH = 0;
+  AMG_TRY(exclusive_scan_i64(cnt64, next.A.rowptr, nH + 1, st, &nnzH));
+  next.A.nnz = nnzH;
+  AMG_TRY(pool_alloc((void **)&next.A.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnzH, 1), st));
+  AMG_TRY(pool_alloc((void **)&next.A.val, sizeof(double) * (size_t)std::max<int64_t>(nnzH, 1), st));
+  AMG_TRY(pool_alloc((void **)&next.diag, sizeof(double) * (size_t)std::max(nH, 1), st));
+  AMG_TRY(pool_alloc((void **)&next.dlow, sizeof(double) * (size_t)std::max(nH, 1), st));
+  k_pair_emit<<<nbH, 256, 0, st>>>(nH, seg, keyJ, kval, next.A.rowptr, cur.dlow, m0, m1, next.A.col,
+                                    next.A.val, next.diag, next.dlow);
+  LAUNCH_CHECK(&h->launches);
+  pool_free(seglen, st);
+  pool_free(seg, st);
+  pool_free(keyJ, st);
+  pool_free(kval, st);
+  pool_free(count, st);
+  pool_free(cnt64, st);
+  pool_free(m0, st);
+  pool_free(m1, st);
+  *nH_out = nH;
+  return AMG_OK;
+}
+
+static void free_build(LevelBuild &b, cudaStream_t st) {
+  pool_free(b.A.rowptr, st);
+  pool_free(b.A.col, st);
+  pool_free(b.A.val, st);
+  pool_free(b.diag, st);
+  pool_free(b.dlow, st);
+  b = LevelBuild();
+}
+
+// copy a temporary level into handle-owned memory
+static amg_status persist_level(amg_handle_s *h, const LevelBuild &b, amg::Level &L) {
+  cudaStream_t st = h->stream;
+  L.n = b.A.n;
+  L.A.n = b.A.n;
+  L.A.nnz = b.A.nnz;
+  AMG_TRY(alloc_persist(h, (void **)&L.A.rowptr, sizeof(int64_t) * (size_t)(b.A.n + 1)));
+  AMG_TRY(alloc_persist(h, (void **)&L.A.col, sizeof(int32_t) * (size_t)std::max<int64_t>(b.A.nnz, 1)));
+  AMG_TRY(alloc_persist(h, (void **)&L.A.val, sizeof(double) * (size_t)std::max<int64_t>(b.A.nnz, 1)));
+  AMG_TRY(alloc_persist(h, (void **)&L.diag, sizeof(double) * (size_t)std::max(b.A.n, 1)));
+  AMG_TRY(alloc_persist(h, (void **)&L.dlow, sizeof(double) * (size_t)std::max(b.A.n, 1)));
+  AMG_CUDA_TRY(cudaMemcpyAsync(L.A.rowptr, b.A.rowptr, sizeof(int64_t) * (size_t)(b.A.n + 1),
+                               cudaMemcpyDeviceToDevice, st));
+  if (b.A.nnz) {
+    AMG_CUDA_TRY(cudaMemcpyAsync(L.A.col, b.A.col, sizeof(int32_t) * (size_t)b.A.nnz,
+                                 cudaMemcpyDeviceToDevice, st));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L.A.val, b.A.val, sizeof(double) * (size_t)b.A.nnz,
+                                 cudaMemcpyDeviceToDevice, st));
+  }
+  AMG_CUDA_TRY(cudaMemcpyAsync(L.diag, b.diag, sizeof(double) * (size_t)b.A.n, cudaMemcpyDeviceToDevice, st));
+  AMG_CUDA_TRY(cudaMemcpyAsync(L.dlow, b.dlow, sizeof(double) * (size_t)b.A.n, cudaMemcpyDeviceToDevice, st));
+  return AMG_OK;
+}
+
+static amg_status build_sell(amg_handle_s *h, amg::Level &L, bool want32) {
+  cudaStream_t st = h->stream;
+  Sell &S = L.S;
+  S.n = L.n;
+  S.nslices = (L.n + kSlice - 1) / kSlice;
+  int64_t *slen = nullptr;
+  AMG_TRY(pool_alloc((void **)&slen, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(slen, 0, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
+  k_sell_width<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(L.n, S.nslices, L.A.rowptr, slen);
+  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(alloc_persist(h, (void **)&S.sptr, sizeof(int64_t) * (size_t)(S.nslices + 1)));
+  int64_t stored = 0;
+  AMG_TRY(exclusive_scan_i64(slen, S.sptr, S.nslices + 1, st, &stored));
+  pool_free(slen, st);
+  S.stored = stored;
+  AMG_TRY(alloc_persist(h, (void **)&S.scol, sizeof(int32_t) * (size_t)std::max<int64_t>(stored, 1)));
+  AMG_TRY(alloc_persist(h, (void **)&S.val64, sizeof(double) * (size_t)std::max<int64_t>(stored, 1)));
+  k_sell_fill<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(L.n, S.nslices, L.A.rowptr, L.A.col,
+                                                                         L.A.val, S.sptr, S.scol, S.val64);
+  LAUNCH_CHECK(&h->launches);
+  S.diag64 = L.diag;
+  if (want32) {
+    AMG_TRY(alloc_persist(h, (void **)&S.val32, sizeof(float) * (size_t)std::max<int64_t>(stored, 1)));
+    AMG_TRY(alloc_persist(h, (void **)&S.diag32, sizeof(float) * (size_t)std::max(L.n, 1)));
+    if (stored) {
+      k_to_f32<<<blocks_for(stored, 256), 256, 0, st>>>(stored, S.val64, S.val32);
+      LAUNCH_CHECK(&h->launches);
+    }
+    k_to_f32<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.diag, S.diag32);
+    LAUNCH_CHECK(&h->launches);
+  }
+  return AMG_OK;
+}
+
+static amg_status build_agg_lists(amg_handle_s *h, amg::Level &L) {
+  cudaStream_t st = h->stream;
+  int *cnt = nullptr, *fill = nullptr;
+  AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * (size_t)(L.nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&fill, sizeof(int) * (size_t)(L.nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(L.nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)(L.nH + 1), st));
+  k_agg_count<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.agg, cnt);
+  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(alloc_persist(h, (void **)&L.agg_ptr, sizeof(int) * (size_t)(L.nH + 1)));
+  AMG_TRY(alloc_persist(h, (void **)&L.agg_mem, sizeof(int) * (size_t)std::max(L.n, 1)));
+  int64_t tot = 0;
+  AMG_TRY(exclusive_scan_i32(cnt, L.agg_ptr, L.nH + 1, st, &tot));
+  k_agg_place<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.agg, L.agg_ptr, fill, L.agg_mem);
+  LAUNCH_CHECK(&h->launches);
+  k_agg_sort<<<blocks_for(L.nH, 128), 128, 0, st>>>(L.nH, L.agg_ptr, L.agg_mem);
+  LAUNCH_CHECK(&h->launches);
+  pool_free(cnt, st);
+  pool_free(fill, st);
+  return AMG_OK;
+}
+
+static amg_status build_coarsest(amg_handle_s *h) {
+  cudaStream_t st = h->stream;
+  amg::Level &C = h->lv[h->L - 1];
+  const int n = C.n;
+  h->nc = n;
+  double *tr = nullptr, *M = nullptr;
+  int *sing = nullptr;
+  AMG_TRY(pool_alloc((void **)&tr, sizeof(double), st));
+  AMG_TRY(pool_alloc((void **)&sing, sizeof(int), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(sing, 0, sizeof(int), st));
+  k_trace<<<1, 32, 0, st>>>(n, C.diag, tr);
+  LAUNCH_CHECK(&h->launches);
+  double trace = 0.0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&trace, tr, sizeof(double), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  const double alpha = h->pure ? trace / ((double)n * (double)n) : 0.0;
+  const int64_t nn = (int64_t)n * n;
+  AMG_TRY(alloc_persist(h, (void **)&h->Z, sizeof(double) * (size_t)nn));
+  if (h->pure && !(trace > 0.0)) {  // one isolated vertex: A = [0], A^+ = [0]
+    AMG_CUDA_TRY(cudaMemsetAsync(h->Z, 0, sizeof(double) * (size_t)nn, st));
+    pool_free(tr, st);
+    pool_free(sing, st);
+    return AMG_OK;
+  }
+  AMG_TRY(pool_alloc((void **)&M, sizeof(double) * (size_t)nn, st));
+  k_dense<<<n, 128, 0, st>>>(n, C.A.rowptr, C.A.col, C.A.val, C.diag, alpha, M);
+  LAUNCH_CHECK(&h->launches);
+  double maxdiag = 0.0;
+  {
+    std::vector<double> dg(n);
+    AMG_CUDA_TRY(cudaMemcpyAsync(dg.data(), C.diag, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    for (double v : dg) maxdiag = std::max(maxdiag, v);
+  }
+  const double tiny = 1e-13 * std::max(maxdiag, 1e-300);
+  double *a = M, *b = h->Z;
+  for (int p = 0; p < n; ++p) {
+    k_gj_step<<<blocks_for(nn, 256), 256, 0, st>>>(n, p, a, b, tiny, sing);
+    LAUNCH_CHECK(&h->launches);
+    std::swap(a, b);
+  }
+  if (a != h->Z) AMG_CUDA_TRY(cudaMemcpyAsync(h->Z, a, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+  if (h->pure) {
+    k_unshift<<<blocks_for(nn, 256), 256, 0, st>>>(nn, 1.0 / (alpha * (double)n * (double)n), h->Z);
+    LAUNCH_CHECK(&h->launches);
+  }
+  int hs = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  pool_free(M, st);
+  pool_free(tr, st);
+  pool_free(sing, st);
+  if (hs) return fail(AMG_ERR_DISCONNECTED, "coarsest operator is singular beyond the constants");
+  return AMG_OK;
+}
+
+amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, const int32_t *col,
+                           const double *w, const double *d) {
+  cudaStream_t st = h->stream;
+  const int n = (int)n64;
+  const unsigned nb = blocks_for(n, 256);
+  // ---- validation (order of the C ABI's error list) ----
+  unsigned *flags = nullptr;
+  AMG_TRY(pool_alloc((void **)&flags, sizeof(unsigned), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+  k_check_rowptr<<<blocks_for(n64 + 1, 256), 256, 0, st>>>(n64, rowptr, flags);
+  LAUNCH_CHECK(&h->launches);
+  unsigned hf = 0;
+  int64_t nnz = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaMemcpyAsync(&nnz, rowptr + n64, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hf & F_ROWPTR) return fail(AMG_ERR_INVALID_ARG, "row_ptr must start at 0 and be non-decreasing");
+  if (nnz > 0 && (!col || !w)) return fail(AMG_ERR_INVALID_ARG, "col_idx and w must be non-NULL");
+  k_check_entries<<<nb, 256, 0, st>>>(n, rowptr, col, w, d, flags);
+  LAUNCH_CHECK(&h->launches);
+  AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hf & (F_RANGE | F_ORDER))
+    return fail(AMG_ERR_INVALID_ARG, "column index out of range or row not strictly increasing");
+  if (hf & F_SELF) return fail(AMG_ERR_SELF_LOOP, "graph has a self loop");
+  k_check_symmetry<<<nb, 256, 0, st>>>(n, rowptr, col, w, flags);
+  LAUNCH_CHECK(&h->launches);
+  AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hf & F_SYM) return fail(AMG_ERR_NOT_SYMMETRIC, "graph is not symmetric (pattern or weights)");
+  if (hf & F_W) return fail(AMG_ERR_BAD_WEIGHT, "edge weights must be finite and > 0");
+  if (hf & F_D) return fail(AMG_ERR_BAD_WEIGHT, "lower-order terms must be finite and >= 0");
+  pool_free(flags, st);
+  // pure Laplacian?  (d NULL or all zero)
+  h->pure = true;
+  if (d) {
+    unsigned long long *mx = nullptr;
+    AMG_TRY(pool_alloc((void **)&mx, sizeof(unsigned long long), st));
+    AMG_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    k_max_abs<<<nb, 256, 0, st>>>(n, d, mx);
+    LAUNCH_CHECK(&h->launches);
+    unsigned long long hm = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    pool_free(mx, st);
+    h->pure = (hm == 0ULL);
+  }
+  // ---- connectivity ----
+  {
+    int *parent = nullptr, *changed = nullptr, *posd = nullptr, *cnt = nullptr;
+    AMG_TRY(pool_alloc((void **)&parent, sizeof(int) * (size_t)n, st));
+    AMG_TRY(pool_alloc((void **)&posd, sizeof(int) * (size_t)n, st));
+    AMG_TRY(pool_alloc((void **)&changed, sizeof(int), st));
+    AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * 2, st));
+    k_cc_init<<<nb, 256, 0, st>>>(n, parent);
+    LAUNCH_CHECK(&h->launches);
+    for (int it = 0;; ++it) {
+      int hc = 0;
+      AMG_CUDA_TRY(cudaMemsetAsync(changed, 0, sizeof(int), st));
+      k_cc_hook<<<nb, 256, 0, st>>>(n, rowptr, col, parent, changed);
+      LAUNCH_CHECK(&h->launches);
+      k_cc_jump<<<nb, 256, 0, st>>>(n, parent);
+      LAUNCH_CHECK(&h->launches);
+      AMG_CUDA_TRY(cudaMemcpyAsync(&hc, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
+      AMG_CUDA_TRY(cudaStreamSynchronize(st));
+      if (!hc) break;
+      if (it > 64 + n) return fail(AMG_ERR_CUDA, "connectivity check did not converge");
+    }
+    AMG_CUDA_TRY(cudaMemsetAsync(posd, 0, sizeof(int) * (size_t)n, st));
+    AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * 2, st));
+    if (d) {
+      k_cc_mark<<<nb, 256, 0, st>>>(n, parent, d, posd);
+      LAUNCH_CHECK(&h->launches);
+    }
+    k_cc_count<<<nb, 256, 0, st>>>(n, parent, posd, h->pure ? 1 : 0, cnt);
+    LAUNCH_CHECK(&h->launches);
+    int hc[2] = {0, 0};
+    AMG_CUDA_TRY(cudaMemcpyAsync(hc, cnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    pool_free(parent, st);
+    pool_free(posd, st);
+    pool_free(changed, st);
+    pool_free(cnt, st);
+    if (h->pure && hc[0] > 1) return fail(AMG_ERR_DISCONNECTED, "pure graph Laplacian of a disconnected graph");
+    if (!h->pure && hc[1] > 0)
+      return fail(AMG_ERR_DISCONNECTED, "a connected component has no positive lower-order term");
+  }
+  // ---- level 0 ----
+  h->lv.clear();
+  h->lv.emplace_back();
+  {
+    amg::Level &L0 = h->lv[0];
+    L0.n = n;
+    L0.A.n = n;
+    L0.A.nnz = nnz;
+    AMG_TRY(alloc_persist(h, (void **)&L0.A.rowptr, sizeof(int64_t) * (size_t)(n + 1)));
+    AMG_TRY(alloc_persist(h, (void **)&L0.A.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)));
+    AMG_TRY(alloc_persist(h, (void **)&L0.A.val, sizeof(double) * (size_t)std::max<int64_t>(nnz, 1)));
+    AMG_TRY(alloc_persist(h, (void **)&L0.diag, sizeof(double) * (size_t)n));
+    AMG_TRY(alloc_persist(h, (void **)&L0.dlow, sizeof(double) * (size_t)n));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.rowptr, rowptr, sizeof(int64_t) * (size_t)(n + 1),
+                                 cudaMemcpyDeviceToDevice, st));
+    if (nnz)
+      AMG_CUDA_TRY(cudaMemcpyAsync(L0.A.col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+    k_assemble<<<nb, 256, 0, st>>>(n, rowptr, w, d, L0.A.val, L0.diag, L0.dlow);
+    LAUNCH_CHECK(&h->launches);
+  }
+  // ---- coarsening ----
+  const int passes = h->opt.passes;
+  while (h->lv.back().n > h->opt.coarse_max && (int)h->lv.size() < h->opt.max_levels) {
+    const int k = (int)h->lv.size() - 1;
+    const int nk = h->lv[k].n;
+    LevelBuild cur;
+    cur.A = h->lv[k].A;
+    cur.diag = h->lv[k].diag;
+    cur.dlow = h->lv[k].dlow;
+    bool owned = false;
+    int *comp = nullptr;
+    AMG_TRY(pool_alloc((void **)&comp, sizeof(int) * (size_t)nk, st));
+    int nH = nk;
+    for (int p = 0; p < passes; ++p) {
+      int *aggp = nullptr;
+      AMG_TRY(pool_alloc((void **)&aggp, sizeof(int) * (size_t)std::max(cur.A.n, 1), st));
+      LevelBuild next;
+      AMG_TRY(coarsen_pass(h, cur, next, aggp, &nH));
+      if (p == 0) {
+        AMG_CUDA_TRY(cudaMemcpyAsync(comp, aggp, sizeof(int) * (size_t)nk, cudaMemcpyDeviceToDevice, st));
+      } else {
+        k_compose<<<blocks_for(nk, 256), 256, 0, st>>>(nk, comp, aggp);
+        LAUNCH_CHECK(&h->launches);
+      }
+      pool_free(aggp, st);
+      if (owned) free_build(cur, st);
+      cur = next;
+      owned = true;
+    }
+    if ((double)nH > kStallRatio * (double)nk) {
+      free_build(cur, st);
+      pool_free(comp, st);
+      if (nk > kStallMaxCoarse) return fail(AMG_ERR_SETUP_STALL, "matching cannot coarsen a large level");
+      break;
+    }
+    amg::Level &Lk = h->lv[k];
+    Lk.nH = nH;
+    AMG_TRY(alloc_persist(h, (void **)&Lk.agg, sizeof(int) * (size_t)nk));
+    AMG_CUDA_TRY(cudaMemcpyAsync(Lk.agg, comp, sizeof(int) * (size_t)nk, cudaMemcpyDeviceToDevice, st));
+    pool_free(comp, st);
+    AMG_TRY(build_agg_lists(h, h->lv[k]));
+    amg::Level nl;
+    AMG_TRY(persist_level(h, cur, nl));
+    free_build(cur, st);
+    h->lv.push_back(nl);
+  }
+  h->L = (int)h->lv.size();
+  // ---- smoother interval and polynomial per level (Sec. 3, Sec. 4) ----
+  unsigned long long *nrm = nullptr;
+  AMG_TRY(pool_alloc((void **)&nrm, sizeof(unsigned long long), st));
+  for (int k = 0; k + 1 < h->L; ++k) {
+    amg::Level &L = h->lv[k];
+    AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long), st));
+    k_norm_inf<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.A.rowptr, L.A.val, L.diag, nrm);
+    LAUNCH_CHECK(&h->launches);
+    unsigned long long bits = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&bits, nrm, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    double l1;
+    memcpy(&l1, &bits, sizeof(double));
+    L.lam1 = l1;
+    L.lam0 = h->opt.lambda0_ratio * l1;
+    closed_form_coefficients(h->opt.degree, L.lam0, L.lam1, L.coef);
+  }
+  pool_free(nrm, st);
+  // ---- solve layouts ----
+  const bool want32 = h->opt.precision == AMG_PREC_FP32;
+  for (int k = 0; k < h->L; ++k) AMG_TRY(build_sell(h, h->lv[k], want32));
+  AMG_TRY(build_coarsest(h));
+  // complexities (Sec. 4)
+  double gs = 0, os = 0;
+  for (auto &L : h->lv) {
+    gs += L.n;
+    os += (double)(L.A.nnz + L.n);
+  }
+  h->grid_complexity = gs / (double)n;
+  h->op_complexity = os / (double)(h->lv[0].A.nnz + n);
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  return AMG_OK;
+}
+
+
+}  // namespace amg

@@ -1,0 +1,783 @@
+// solve.cu -- solve phase: flexible CG preconditioned by the nonlinear AMLI
+// cycle (K-cycle) with the polynomial smoother (Sec. 3, Sec. 4).
+//
+// Kernels (templated on the cycle precision T = double or float):
+//   k_cheb_first / k_cheb_step : one SpMV on the SELL-32 operator fused with
+//       one step of the Chebyshev three-term recurrence for q_m(A) r and the
+//       accumulation x += c_j T_j (Sec. 3 smoother R = q_m(A));
+//   k_residual                 : s = r - A x;
+//   k_restrict / k_prolong_add : r_H = P^T s (sum over aggregate members in
+//       ascending order) and x += P e_H (Eq. (coarse));
+//   k_dots                     : up to kMaxDots dot products in one pass,
+//       deterministic two-stage reduction whose last block also derives the
+//       Krylov scalars (alpha, beta, rho) on the device;
+//   k_axpy_multi / k_*_update  : Krylov vector updates reading those scalars.
+// The host walks the cycle and issues launches; it reads one scalar per
+// outer iteration (the residual norm for the stopping test).
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace amg {
+
+#define SLAUNCH(h)                                                                  \
+  do {                                                                              \
+    ++(h)->launches;                                                                \
+    cudaError_t e_ = cudaGetLastError();                                            \
+    if (e_ != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kThreads = 256;
+static inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// SELL-32 row kernel: off-diagonal part of row `row` times x
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict__ x, int row, T acc) {
+  const int s = row >> 5, lane = row & 31;
+  const int64_t base = A.sptr[s];
+  const int w = (int)((A.sptr[s + 1] - base) >> 5);
+  const int32_t *__restrict__ c = A.scol + base + lane;
+  const T *__restrict__ v = A.val + base + lane;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[c[k * kSlice]], acc);
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T apply_row(const SellView<T> &A, const T *__restrict__ x, int row) {
+  return sell_row(A, x, row, A.diag[row] * x[row]);
+}
+
+// T_1 = t(A) r with t(A) = sa*A - ca*I; x (=|+=) b0*r + b1*T_1
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> A, const T *__restrict__ r,
+                                                         T *__restrict__ T1, T *__restrict__ x, T sa,
+                                                         T ca, T b0, T b1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const T ri = r[i];
+  const T Ar = apply_row(A, r, i);
+  const T t1 = fma(sa, Ar, -ca * ri);
+  T1[i] = t1;
+  const T inc = fma(b1, t1, b0 * ri);
+  x[i] = ADD ? x[i] + inc : inc;
+}
+
+// T_{j+1} = 2 t(A) T_j - T_{j-1}; x += bj * T_{j+1}.  Tn may alias Tp.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> A, const T *__restrict__ Tc,
+                                                        const T *Tp, T *Tn, T *__restrict__ x, T sa,
+                                                        T ca, T bj) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const T tc = Tc[i];
+  const T At = apply_row(A, Tc, i);
+  const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[i];
+  Tn[i] = tn;
+  x[i] = fma(bj, tn, x[i]);
+}
+
+template <typename T, bool ADD>
+__global__ void k_scale(int n, const T *__restrict__ r, T *__restrict__ x, T b0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = ADD ? x[i] + b0 * r[i] : b0 * r[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *__restrict__ x,
+                                                       const T *__restrict__ r, T *__restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  s[i] = r[i] - apply_row(A, x, i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_spmv(SellView<T> A, const T *__restrict__ x,
+                                                   T *__restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  y[i] = apply_row(A, x, i);
+}
+
+template <typename T>
+__global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__restrict__ mem,
+                           const T *__restrict__ s, T *__restrict__ rH) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  T acc = T(0);
+  for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += s[mem[a]];
+  rH[I] = acc;
+}
+
+template <typename T>
+__global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__restrict__ eH,
+                              T *__restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += eH[agg[i]];
+}
+
+template <typename A, typename B>
+__global__ void k_convert(int64_t n, const A *__restrict__ a, B *__restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (B)a[i];
+}
+
+// coarsest solve: x = Z b, one warp per row, fp64
+__global__ void k_dense_mv(int n, const double *__restrict__ Z, const double *__restrict__ b,
+                           double *__restrict__ x) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc = fma(Z[(int64_t)row * n + j], b[j], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[row] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// fused dot products with on-device finalisation
+// ---------------------------------------------------------------------------
+enum FinKind : int {
+  FIN_STORE = 0,   // scal[o0 + q] = sum_q
+  FIN_IBETA = 1,   // inner: scal[16 + l] = sum_l / scal[l], l < nd
+  FIN_IALPHA = 2,  // inner step o0: rho = s0, alpha = s1 / rho; stop flag scal[24]
+  FIN_OBETA = 3,   // outer: scal[16 + j] = sum_j / scal[j]
+  FIN_OALPHA = 4,  // outer slot o0: rho = s0, alpha = s1 / rho -> scal[32]; breakdown scal[34]
+  FIN_MEAN = 5     // scal[o0] = s0 / o1 (o1 = n)
+};
+
+struct Fin {
+  int kind;
+  int o0;
+  double o1;
+  double *scal;
+};
+
+template <typename T>
+struct DotSpec {
+  const T *a[kMaxDots];
+  const T *b[kMaxDots];  // nullptr: sum of a
+  int nd;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ void finalize(const Fin &f, const double *sums, int nd) {
+  double *sc = f.scal;
+  switch (f.kind) {
+    case FIN_STORE:
+      for (int q = 0; q < nd; ++q) sc[f.o0 + q] = sums[q];
+      break;
+    case FIN_IBETA:
+      for (int l = 0; l < nd; ++l) sc[16 + l] = sums[l] / sc[l];
+      break;
+    case FIN_IALPHA: {
+      const double rho = sums[0], sig = sums[1];
+      sc[f.o0] = rho;
+      if (sc[24] != 0.0 || !(rho > 0.0) || !isfinite(rho)) {
+        sc[24] = 1.0;
+        sc[8 + f.o0] = 0.0;
+      } else {
+        sc[8 + f.o0] = sig / rho;
+      }
+      break;
+    }
+    case FIN_OBETA:
+      for (int j = 0; j < nd; ++j) sc[16 + j] = sums[j] / sc[j];
+      break;
+    case FIN_OALPHA: {
+      const double rho = sums[0], sig = sums[1];
+      sc[f.o0] = rho;
+      if (!(rho > 0.0) || !isfinite(rho)) {
+        sc[34] = 1.0;
+        sc[32] = 0.0;
+      } else {
+        sc[32] = sig / rho;
+      }
+      break;
+    }
+    case FIN_MEAN:
+      sc[f.o0] = sums[0] / f.o1;
+      break;
+  }
+}
+
+// per-thread partial sums -> per-block partials -> last block folds the
+// partials in block order (deterministic for a fixed grid) and finalises
+template <typename T>
+__device__ void reduce_and_finalize(double (&acc)[kMaxDots], int nd, double *partial,
+                                    unsigned *ticket, const Fin &fin) {
+  __shared__ double sh[kThreads / 32][kMaxDots];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < nd; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) sh[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nd) {
+    double v = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) v += sh[w][threadIdx.x];
+    partial[blockIdx.x * kMaxDots + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (warp == 0) {
+    double sums[kMaxDots];
+    for (int q = 0; q < nd; ++q) {
+      double v = 0.0;
+      for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(&partial[b * kMaxDots + q]);
+      sums[q] = warp_sum(v);
+    }
+    if (lane == 0) {
+      finalize(fin, sums, nd);
+      *ticket = 0u;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dots(int64_t n, DotSpec<T> spec, double *partial,
+                                                   unsigned *ticket, Fin fin) {
+  double acc[kMaxDots];
+  for (int q = 0; q < kMaxDots; ++q) acc[q] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int q = 0; q < spec.nd; ++q) {
+      const double a = (double)spec.a[q][i];
+      acc[q] += spec.b[q] ? a * (double)spec.b[q][i] : a;
+    }
+  }
+  reduce_and_finalize<T>(acc, spec.nd, partial, ticket, fin);
+}
+
+// y = z - sum_l beta_l V_l (beta read from the device)
+template <typename T>
+__global__ void k_axpy_multi(int64_t n, T *y, const T *z, DotSpec<T> V, const double *beta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T v = z[i];
+  for (int l = 0; l < V.nd; ++l) v -= (T)beta[l] * V.a[l][i];
+  y[i] = v;
+}
+
+// inner flexible CG update of step `it` (scalars in sc):
+//   x = alpha D (it == 0) or x += alpha D; r = rin - alpha W when `upd_r`
+template <typename T>
+__global__ void k_inner_update(int64_t n, int it, bool upd_r, const double *sc, const T *D,
+                               const T *W, const T *rin, T *x, T *r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool stopped_here = sc[24] != 0.0 && sc[8 + it] == 0.0;
+  const T a = (T)sc[8 + it];
+  if (it == 0) x[i] = stopped_here ? T(0) : a * D[i];
+  else if (!stopped_here) x[i] = fma(a, D[i], x[i]);
+  if (upd_r) r[i] = stopped_here ? rin[i] : rin[i] - a * W[i];
+}
+
+// outer update: x += alpha d, r -= alpha q, then r.r
+__global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const double *sc, const double *d,
+                                                           const double *q, double *x, double *r,
+                                                           double *partial, unsigned *ticket, Fin fin) {
+  double acc[kMaxDots];
+  acc[0] = 0.0;
+  const double a = sc[32];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(a, d[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    acc[0] += ri * ri;
+  }
+  reduce_and_finalize<double>(acc, 1, partial, ticket, fin);
+}
+
+__global__ void k_shift(int64_t n, const double *src, double *dst, const double *mean) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] - *mean;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static inline unsigned red_grid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kThreads - 1) / kThreads));
+}
+
+template <typename T>
+static SellView<T> view(const amg::Level &L);
+template <>
+SellView<double> view<double>(const amg::Level &L) {
+  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64};
+}
+template <>
+SellView<float> view<float>(const amg::Level &L) {
+  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32};
+}
+
+template <typename T>
+static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin fin) {
+  k_dots<T><<<red_grid(n), kThreads, 0, h->stream>>>(n, spec, h->red.partial, h->red.ticket, fin);
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
+static amg_status timing_record(amg_handle_s *h, cudaEvent_t *ev) {
+  Timing &tm = h->timing;
+  if (tm.used >= tm.ev.size()) {
+    cudaEvent_t e;
+    AMG_CUDA_TRY(cudaEventCreate(&e));
+    tm.ev.push_back(e);
+  }
+  *ev = tm.ev[tm.used++];
+  AMG_CUDA_TRY(cudaEventRecord(*ev, h->stream));
+  return AMG_OK;
+}
+
+static amg_status timing_flush(amg_handle_s *h) {
+  Timing &tm = h->timing;
+  if (!tm.used) return AMG_OK;
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i + 1 < tm.used; i += 2) {
+    float ms = 0.f;
+    AMG_CUDA_TRY(cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]));
+    tm.total_ms += ms;
+    ++tm.launches;
+  }
+  tm.used = 0;
+  return AMG_OK;
+}
+
+// x (=|+=) q_m(A_k) r
+template <typename T>
+static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
+  amg::Level &L = h->lv[k];
+  const int m = h->opt.degree;
+  const SellView<T> A = view<T>(L);
+  const T sa = (T)(2.0 / (L.lam1 - L.lam0));
+  const T ca = (T)((L.lam1 + L.lam0) / (L.lam1 - L.lam0));
+  cudaStream_t st = h->stream;
+  if (m == 0) {
+    if (add) k_scale<T, true><<<nblk(L.n), kThreads, 0, st>>>(L.n, r, x, (T)L.coef[0]);
+    else k_scale<T, false><<<nblk(L.n), kThreads, 0, st>>>(L.n, r, x, (T)L.coef[0]);
+    SLAUNCH(h);
+    return AMG_OK;
+  }
+  T *Ta = (T *)L.Ta, *Tb = (T *)L.Tb;
+  if (add) k_cheb_first<T, true><<<nblk(L.n), kThreads, 0, st>>>(A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
+  else k_cheb_first<T, false><<<nblk(L.n), kThreads, 0, st>>>(A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
+  SLAUNCH(h);
+  const T *Tp = r;
+  T *Tc = Ta;
+  const bool timed = h->timing.enabled && k == 0;
+  for (int j = 2; j <= m; ++j) {
+    T *Tn = (j == 2) ? Tb : const_cast<T *>(Tp);
+    cudaEvent_t e0, e1;
+    if (timed) AMG_TRY(timing_record(h, &e0));
+    k_cheb_step<T><<<nblk(L.n), kThreads, 0, st>>>(A, Tc, Tp, Tn, x, sa, ca, (T)L.coef[j]);
+    SLAUNCH(h);
+    if (timed) AMG_TRY(timing_record(h, &e1));
+    Tp = Tc;
+    Tc = Tn;
+  }
+  return AMG_OK;
+}
+
+template <typename T>
+static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s) {
+  amg::Level &L = h->lv[k];
+  k_residual<T><<<nblk(L.n), kThreads, 0, h->stream>>>(view<T>(L), x, r, s);
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
+template <typename T>
+static amg_status coarse_solve(amg_handle_s *h, const T *b, T *x);
+
+template <>
+amg_status coarse_solve<double>(amg_handle_s *h, const double *b, double *x) {
+  k_dense_mv<<<nblk((int64_t)h->nc * 32), kThreads, 0, h->stream>>>(h->nc, h->Z, b, x);
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
+template <>
+amg_status coarse_solve<float>(amg_handle_s *h, const float *b, float *x) {
+  k_convert<float, double><<<nblk(h->nc), kThreads, 0, h->stream>>>(h->nc, b, h->cb64);
+  SLAUNCH(h);
+  AMG_TRY(coarse_solve<double>(h, h->cb64, h->cx64));
+  k_convert<double, float><<<nblk(h->nc), kThreads, 0, h->stream>>>(h->nc, h->cx64, x);
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
+template <typename T>
+static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x);
+
+// nu steps of flexible CG on level k (1 <= k < L-1) from x = 0:
+// b = level k's input (r_H of level k-1), result in level k's x
+template <typename T>
+static amg_status inner_fcg(amg_handle_s *h, int k) {
+  amg::Level &L = h->lv[k];
+  const int nu = h->opt.inner_iters;
+  const int64_t n = L.n;
+  cudaStream_t st = h->stream;
+  T *b = (T *)L.b, *x = (T *)L.x, *r = (T *)L.r;
+  AMG_CUDA_TRY(cudaMemsetAsync(L.scal + 24, 0, sizeof(double), st));
+  for (int it = 0; it < nu; ++it) {
+    const T *rin = (it == 0) ? b : r;
+    T *D = (T *)L.D[it], *W = (T *)L.W[it];
+    AMG_TRY(kcycle<T>(h, k, rin, D));
+    k_spmv<T><<<nblk(n), kThreads, 0, st>>>(view<T>(L), D, W);
+    SLAUNCH(h);
+    if (it > 0) {
+      DotSpec<T> sp{};
+      for (int l = 0; l < it; ++l) {
+        sp.a[l] = (const T *)L.D[l];
+        sp.b[l] = W;
+      }
+      sp.nd = it;
+      AMG_TRY(dots<T>(h, n, sp, Fin{FIN_IBETA, 0, 0.0, L.scal}));
+      DotSpec<T> vd{}, vw{};
+      for (int l = 0; l < it; ++l) {
+        vd.a[l] = (const T *)L.D[l];
+        vw.a[l] = (const T *)L.W[l];
+      }
+      vd.nd = vw.nd = it;
+      k_axpy_multi<T><<<nblk(n), kThreads, 0, st>>>(n, D, D, vd, L.scal + 16);
+      SLAUNCH(h);
+      k_axpy_multi<T><<<nblk(n), kThreads, 0, st>>>(n, W, W, vw, L.scal + 16);
+      SLAUNCH(h);
+    }
+    DotSpec<T> sp{};
+    sp.a[0] = D;
+    sp.b[0] = W;
+    sp.a[1] = D;
+    sp.b[1] = rin;
+    sp.nd = 2;
+    AMG_TRY(dots<T>(h, n, sp, Fin{FIN_IALPHA, it, 0.0, L.scal}));
+    k_inner_update<T><<<nblk(n), kThreads, 0, st>>>(n, it, it + 1 < nu, L.scal, D, W, rin, x, r);
+    SLAUNCH(h);
+  }
+  return AMG_OK;
+}
+
+// x = K_k(r): W(1,1) nonlinear AMLI cycle (Sec. 3 two-level steps, Sec. 4)
+template <typename T>
+static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
+  if (k == h->L - 1) return coarse_solve<T>(h, r, x);
+  amg::Level &L = h->lv[k];
+  amg::Level &N = h->lv[k + 1];
+  cudaStream_t st = h->stream;
+  T *s = (T *)L.s;
+  AMG_TRY(smooth<T>(h, k, r, x, false));
+  AMG_TRY(residual<T>(h, k, x, r, s));
+  k_restrict<T><<<nblk(L.nH), kThreads, 0, st>>>(L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b);
+  SLAUNCH(h);
+  if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
+  else AMG_TRY(inner_fcg<T>(h, k + 1));
+  k_prolong_add<T><<<nblk(L.n), kThreads, 0, st>>>(L.n, L.agg, (const T *)N.x, x);
+  SLAUNCH(h);
+  AMG_TRY(residual<T>(h, k, x, r, s));
+  AMG_TRY(smooth<T>(h, k, s, x, true));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// buffers
+// ---------------------------------------------------------------------------
+amg_status allocate_solve_buffers(amg_handle_s *h) {
+  const bool f32 = h->opt.precision == AMG_PREC_FP32;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const int L = h->L, nu = h->opt.inner_iters;
+  for (int k = 0; k < L; ++k) {
+    amg::Level &V = h->lv[k];
+    const size_t n = (size_t)std::max(V.n, 1);
+    AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
+    if (k < L - 1) {
+      AMG_TRY(h->arena.alloc(&V.s, es * n));
+      AMG_TRY(h->arena.alloc(&V.Ta, es * n));
+      AMG_TRY(h->arena.alloc(&V.Tb, es * n));
+    }
+    if (k >= 1) {
+      AMG_TRY(h->arena.alloc(&V.b, es * n));
+      AMG_TRY(h->arena.alloc(&V.x, es * n));
+    }
+    if (k >= 1 && k < L - 1) {
+      AMG_TRY(h->arena.alloc(&V.r, es * n));
+      for (int i = 0; i < nu; ++i) {
+        AMG_TRY(h->arena.alloc(&V.D[i], es * n));
+        AMG_TRY(h->arena.alloc(&V.W[i], es * n));
+      }
+    }
+  }
+  const size_t n0 = (size_t)h->n;
+  AMG_TRY(h->arena.get(&h->ob, n0));
+  AMG_TRY(h->arena.get(&h->ox, n0));
+  AMG_TRY(h->arena.get(&h->or_, n0));
+  AMG_TRY(h->arena.get(&h->oz, n0));
+  for (int j = 0; j < h->opt.restart; ++j) {
+    AMG_TRY(h->arena.get(&h->oD[j], n0));
+    AMG_TRY(h->arena.get(&h->oQ[j], n0));
+  }
+  AMG_TRY(h->arena.get(&h->oscal, 256));
+  AMG_TRY(h->arena.get(&h->red.partial, (size_t)kRedBlocks * kMaxDots));
+  AMG_TRY(h->arena.get(&h->red.ticket, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
+  if (f32) {
+    AMG_TRY(h->arena.get(&h->r32, n0));
+    AMG_TRY(h->arena.get(&h->z32, n0));
+    AMG_TRY(h->arena.get(&h->cb64, (size_t)h->nc));
+    AMG_TRY(h->arena.get(&h->cx64, (size_t)h->nc));
+  }
+  if (!h->h_pinned) AMG_CUDA_TRY(cudaMallocHost((void **)&h->h_pinned, sizeof(double) * 64));
+  return AMG_OK;
+}
+
+// z = K_0(r) in the handle's cycle precision (fp64 in, fp64 out)
+static amg_status precondition(amg_handle_s *h, const double *r, double *z) {
+  if (h->opt.precision == AMG_PREC_FP32) {
+    const int64_t n = h->n;
+    k_convert<double, float><<<nblk(n), kThreads, 0, h->stream>>>(n, r, h->r32);
+    SLAUNCH(h);
+    AMG_TRY(kcycle<float>(h, 0, h->r32, h->z32));
+    k_convert<float, double><<<nblk(n), kThreads, 0, h->stream>>>(n, h->z32, z);
+    SLAUNCH(h);
+    return AMG_OK;
+  }
+  return kcycle<double>(h, 0, r, z);
+}
+
+// ---------------------------------------------------------------------------
+// outer flexible CG (Sec. 4: NPCG on the finest level, window cleared every
+// `restart` iterations), fp64
+// ---------------------------------------------------------------------------
+amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol, amg_info *info,
+                     int *iters_out, double *rel_out, double *true_rel_out, int *conv_out) {
+  cudaStream_t st = h->stream;
+  const int64_t n = h->n;
+  const int R = h->opt.restart;
+  amg::Level &L0 = h->lv[0];
+  const SellView<double> A0 = view<double>(L0);
+  double *sc = h->oscal;
+  double *hp = h->h_pinned;
+  // b (projected to zero mean for a pure Laplacian)
+  if (h->pure) {
+    DotSpec<double> sp{};
+    sp.a[0] = b_dev;
+    sp.b[0] = nullptr;
+    sp.nd = 1;
+    AMG_TRY(dots<double>(h, n, sp, Fin{FIN_MEAN, 35, (double)n, sc}));
+    k_shift<<<nblk(n), kThreads, 0, st>>>(n, b_dev, h->ob, sc + 35);
+    SLAUNCH(h);
+  } else {
+    AMG_CUDA_TRY(cudaMemcpyAsync(h->ob, b_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  {
+    DotSpec<double> sp{};
+    sp.a[0] = h->ob;
+    sp.b[0] = h->ob;
+    sp.nd = 1;
+    AMG_TRY(dots<double>(h, n, sp, Fin{FIN_STORE, 36, 0.0, sc}));
+  }
+  AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 36, sizeof(double), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaMemsetAsync(x_dev, 0, sizeof(double) * n, st));
+  AMG_CUDA_TRY(cudaMemcpyAsync(h->or_, h->ob, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  AMG_CUDA_TRY(cudaMemsetAsync(sc + 34, 0, sizeof(double), st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  const double nb = sqrt(hp[0]);
+  int hl = 0;
+  if (info && info->history && info->history_cap > 0) info->history[hl++] = nb > 0 ? 1.0 : 0.0;
+  int it = 0, converged = (nb == 0.0), nwin = 0;
+  double res = nb > 0 ? 1.0 : 0.0;
+  amg_status status = AMG_OK;
+  if (h->timing.enabled) h->timing.used = 0;
+  while (!converged && it < h->opt.max_iters) {
+    if (it % R == 0) nwin = 0;
+    double *d = h->oD[nwin], *q = h->oQ[nwin];
+    AMG_TRY(precondition(h, h->or_, h->oz));
+    if (nwin > 0) {
+      DotSpec<double> sp{};
+      for (int j = 0; j < nwin; ++j) {
+        sp.a[j] = h->oQ[j];
+        sp.b[j] = h->oz;
+      }
+      sp.nd = nwin;
+      AMG_TRY(dots<double>(h, n, sp, Fin{FIN_OBETA, 0, 0.0, sc}));
+    }
+    {
+      DotSpec<double> vd{};
+      for (int j = 0; j < nwin; ++j) vd.a[j] = h->oD[j];
+      vd.nd = nwin;
+      k_axpy_multi<double><<<nblk(n), kThreads, 0, st>>>(n, d, h->oz, vd, sc + 16);
+      SLAUNCH(h);
+    }
+    k_spmv<double><<<nblk(n), kThreads, 0, st>>>(A0, d, q);
+    SLAUNCH(h);
+    {
+      DotSpec<double> sp{};
+      sp.a[0] = d;
+      sp.b[0] = q;
+      sp.a[1] = d;
+      sp.b[1] = h->or_;
+      sp.nd = 2;
+      AMG_TRY(dots<double>(h, n, sp, Fin{FIN_OALPHA, nwin, 0.0, sc}));
+    }
+    k_outer_update<<<red_grid(n), kThreads, 0, st>>>(n, sc, d, q, x_dev, h->or_, h->red.partial,
+                                                      h->red.ticket, Fin{FIN_STORE, 33, 0.0, sc});
+    SLAUNCH(h);
+    AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 33, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hp[1] != 0.0) {
+      status = fail(AMG_ERR_BREAKDOWN, "flexible CG breakdown: d^T A d <= 0 or non-finite");
+      break;
+    }
+    ++nwin;
+    ++it;
+    res = sqrt(hp[0]) / nb;
+    if (info && info->history && hl < info->history_cap) info->history[hl++] = res;
+    if (res <= tol) converged = 1;
+  }
+  if (h->timing.enabled) AMG_TRY(timing_flush(h));
+  if (h->pure) {
+    DotSpec<double> sp{};
+    sp.a[0] = x_dev;
+    sp.b[0] = nullptr;
+    sp.nd = 1;
+    AMG_TRY(dots<double>(h, n, sp, Fin{FIN_MEAN, 37, (double)n, sc}));
+    k_shift<<<nblk(n), kThreads, 0, st>>>(n, x_dev, x_dev, sc + 37);
+    SLAUNCH(h);
+  }
+  // true residual ||b - A x|| / ||b||
+  double true_rel = 0.0;
+  if (nb > 0.0) {
+    k_residual<double><<<nblk(n), kThreads, 0, st>>>(A0, x_dev, h->ob, h->oz);
+    SLAUNCH(h);
+    DotSpec<double> sp{};
+    sp.a[0] = h->oz;
+    sp.b[0] = h->oz;
+    sp.nd = 1;
+    AMG_TRY(dots<double>(h, n, sp, Fin{FIN_STORE, 38, 0.0, sc}));
+    AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 38, sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    true_rel = sqrt(hp[0]) / nb;
+  }
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info) info->history_len = hl;
+  *iters_out = it;
+  *rel_out = res;
+  *true_rel_out = true_rel;
+  *conv_out = converged;
+  if (status == AMG_OK && !converged) status = AMG_ERR_NOT_CONVERGED;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// single-step entry points (fp64 vectors in and out)
+// ---------------------------------------------------------------------------
+template <typename F>
+static amg_status with_precision(amg_handle_s *h, int k, F &&f64_fn) {
+  (void)k;
+  return f64_fn();
+}
+
+static bool f32(amg_handle_s *h) { return h->opt.precision == AMG_PREC_FP32; }
+
+// run `body(T*)` on fp32 copies of (in -> out) when the cycle is fp32
+template <typename Body>
+static amg_status run_conv(amg_handle_s *h, const double *in, int64_t nin, double *out, int64_t nout,
+                           bool out_accumulates, Body body) {
+  if (!f32(h)) return body((const void *)in, (void *)out);
+  float *a = nullptr, *b = nullptr;
+  AMG_TRY(pool_alloc((void **)&a, sizeof(float) * (size_t)std::max<int64_t>(nin, 1), h->stream));
+  AMG_TRY(pool_alloc((void **)&b, sizeof(float) * (size_t)std::max<int64_t>(nout, 1), h->stream));
+  k_convert<double, float><<<nblk(nin), kThreads, 0, h->stream>>>(nin, in, a);
+  SLAUNCH(h);
+  if (out_accumulates) {
+    k_convert<double, float><<<nblk(nout), kThreads, 0, h->stream>>>(nout, out, b);
+    SLAUNCH(h);
+  }
+  AMG_TRY(body((const void *)a, (void *)b));
+  k_convert<float, double><<<nblk(nout), kThreads, 0, h->stream>>>(nout, b, out);
+  SLAUNCH(h);
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  pool_free(a, h->stream);
+  pool_free(b, h->stream);
+  return AMG_OK;
+}
+
+amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y) {
+  amg::Level &L = h->lv[k];
+  AMG_TRY(run_conv(h, x, L.n, y, L.n, false, [&](const void *a, void *b) -> amg_status {
+    if (f32(h)) k_spmv<float><<<nblk(L.n), kThreads, 0, h->stream>>>(view<float>(L), (const float *)a, (float *)b);
+    else k_spmv<double><<<nblk(L.n), kThreads, 0, h->stream>>>(view<double>(L), (const double *)a, (double *)b);
+    SLAUNCH(h);
+    return AMG_OK;
+  }));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+amg_status apply_smoother(amg_handle_s *h, int k, const double *r, double *x) {
+  amg::Level &L = h->lv[k];
+  AMG_TRY(run_conv(h, r, L.n, x, L.n, false, [&](const void *a, void *b) -> amg_status {
+    if (f32(h)) return smooth<float>(h, k, (const float *)a, (float *)b, false);
+    return smooth<double>(h, k, (const double *)a, (double *)b, false);
+  }));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+amg_status apply_restrict(amg_handle_s *h, int k, const double *s, double *rH) {
+  amg::Level &L = h->lv[k];
+  AMG_TRY(run_conv(h, s, L.n, rH, L.nH, false, [&](const void *a, void *b) -> amg_status {
+    if (f32(h)) k_restrict<float><<<nblk(L.nH), kThreads, 0, h->stream>>>(L.nH, L.agg_ptr, L.agg_mem, (const float *)a, (float *)b);
+    else k_restrict<double><<<nblk(L.nH), kThreads, 0, h->stream>>>(L.nH, L.agg_ptr, L.agg_mem, (const double *)a, (double *)b);
+    SLAUNCH(h);
+    return AMG_OK;
+  }));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+amg_status apply_prolong_add(amg_handle_s *h, int k, const double *eH, double *x) {
+  amg::Level &L = h->lv[k];
+  AMG_TRY(run_conv(h, eH, L.nH, x, L.n, true, [&](const void *a, void *b) -> amg_status {
+    if (f32(h)) k_prolong_add<float><<<nblk(L.n), kThreads, 0, h->stream>>>(L.n, L.agg, (const float *)a, (float *)b);
+    else k_prolong_add<double><<<nblk(L.n), kThreads, 0, h->stream>>>(L.n, L.agg, (const double *)a, (double *)b);
+    SLAUNCH(h);
+    return AMG_OK;
+  }));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+amg_status apply_coarse_solve(amg_handle_s *h, const double *b, double *x) {
+  AMG_TRY(coarse_solve<double>(h, b, x));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+amg_status apply_kcycle(amg_handle_s *h, int k, const double *r, double *z) {
+  amg::Level &L = h->lv[k];
+  // level k >= 1 reads its input from the level's b buffer when it recurses,
+  // so use dedicated copies
+  AMG_TRY(run_conv(h, r, L.n, z, L.n, false, [&](const void *a, void *b) -> amg_status {
+    if (f32(h)) return kcycle<float>(h, k, (const float *)a, (float *)b);
+    return kcycle<double>(h, k, (const double *)a, (double *)b);
+  }));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMG_OK;
+}
+
+}  // namespace amg

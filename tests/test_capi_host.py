@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every symbol include/amg.h declares, validates arguments before
+touching the device, and reports the absence of a device as AMG_ERR_CUDA."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "amg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(amg_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import paper_1307_6305_gb300 as pkg
+
+    pkg.lib()
+    return pkg
+
+
+def test_exports_every_declared_symbol(amg):
+    declared = header_symbols()
+    assert len(declared) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", amg.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (amg_\w+)", out))
+    assert set(declared) <= exported, set(declared) - exported
+    assert set(declared) == set(amg.SYMBOLS)
+    for s in declared:
+        assert hasattr(amg.lib(), s)
+
+
+def test_default_options(amg):
+    o = amg.amg_default_options()
+    assert (o.degree, o.passes, o.coarse_max, o.max_levels, o.inner_iters, o.restart) == (4, 3, 64, 30, 2, 5)
+    assert o.precision == amg.AMG_PREC_FP64 and o.lambda0_ratio == 0.1
+
+
+def test_argument_errors_before_device(amg):
+    g = gg.grid2d_5pt(4)
+    rp, col, w = g.rowptr, g.col, g.w
+    st, h = amg.amg_setup(0, rp, col, w)
+    assert st == amg.AMG_ERR_INVALID_ARG and not h.value
+    st, h = amg.amg_setup(g.n, None, col, w)
+    assert st == amg.AMG_ERR_INVALID_ARG
+    for bad in (dict(degree=-1), dict(degree=17), dict(passes=0), dict(inner_iters=9), dict(restart=0),
+                dict(precision=3), dict(lambda0_ratio=1.5), dict(coarse_max=0)):
+        st, h = amg.amg_setup(g.n, rp, col, w, None, amg.amg_default_options(**bad))
+        assert st == amg.AMG_ERR_INVALID_ARG, bad
+        assert amg.amg_last_error(None)
+    rp2 = rp.copy(); rp2[0] = 1
+    st, h = amg.amg_setup(g.n, rp2, col, w)
+    assert st == amg.AMG_ERR_INVALID_ARG
+    st, h = amg.amg_setup(g.n, rp, col, w, None, None, 7)
+    assert st == amg.AMG_ERR_INVALID_ARG
+    assert amg.amg_solve(None, np.zeros(3), np.zeros(3), 1, 3, 1e-8) == amg.AMG_ERR_INVALID_ARG
+
+
+def test_no_device_is_reported(amg):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    g = gg.grid2d_5pt(4)
+    st, h = amg.amg_setup(g.n, g.rowptr, g.col, g.w)
+    assert st == amg.AMG_ERR_CUDA and not h.value
+    assert "device" in amg.amg_last_error(None)
