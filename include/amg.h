@@ -206,6 +206,25 @@ amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
                      uint64_t salt, int32_t *mate, int32_t *agg, int64_t *n_coarse, int *rounds,
                      void *cuda_stream);
 
+/* The same matching pass as amg_match, but allocation-free.  The paper has
+ * no counterpart: this entry point exists for callers that may not allocate
+ * device memory themselves (their memory belongs to another allocator, such
+ * as a framework's caching allocator holding the GPU's free memory, or they
+ * must avoid the device-wide synchronisation of cudaFree mid-pipeline).
+ * Scratch lives in one fixed device array inside the library (4 MiB per GPU
+ * that loads the library, kept until the process exits), so:
+ *  - n must be <= 1048576 (2^20); larger n returns AMG_ERR_INVALID_ARG;
+ *  - no cudaMalloc/cudaFree or allocating library routine is called;
+ *  - the first call on a device looks up that array's device address (with
+ *    that device current); make that first call before any stream capture;
+ *  - all calls on a device share the array: calls that overlap on the GPU
+ *    (other streams, threads or processes on the same context) race and must
+ *    be serialised by the caller.
+ * Arguments, outputs and results are those of amg_match. */
+amg_status amg_match_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             const double *s, uint64_t salt, int32_t *mate, int32_t *agg,
+                             int64_t *n_coarse, int *rounds, void *cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Measurement hooks.                                                      */
 /* ---------------------------------------------------------------------- */

@@ -38,7 +38,7 @@ SYMBOLS = [
     "amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
     "amg_num_levels", "amg_level_n", "amg_level_nnz", "amg_level_csr", "amg_level_agg",
     "amg_level_smoother", "amg_apply_spmv", "amg_apply_smoother", "amg_apply_restrict",
-    "amg_apply_prolong_add", "amg_apply_coarse_solve", "amg_apply_kcycle", "amg_match",
+    "amg_apply_prolong_add", "amg_apply_coarse_solve", "amg_apply_kcycle", "amg_match", "amg_match_noalloc",
     "amg_kernel_timing", "amg_kernel_timing_read", "amg_launch_count",
 ]
 
@@ -97,6 +97,7 @@ def lib(build_if_missing: bool = True):
                 getattr(L, name).argtypes = [P, I, P, P]
             L.amg_apply_coarse_solve.argtypes = [P, P, P]
             L.amg_match.argtypes = [I64, P, P, P, C.c_uint64, P, P, C.POINTER(I64), C.POINTER(I), P]
+            L.amg_match_noalloc.argtypes = [I64, P, P, P, C.c_uint64, P, P, C.POINTER(I64), C.POINTER(I), P]
             L.amg_kernel_timing.argtypes = [P, I]
             L.amg_kernel_timing_read.argtypes = [P, C.POINTER(I64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.amg_launch_count.argtypes = [P]
@@ -163,6 +164,15 @@ def amg_match(n, row_ptr, col_idx, s, salt, mate, agg, stream=None):
     rounds = C.c_int(0)
     st = lib().amg_match(n, ptr(row_ptr), ptr(col_idx), ptr(s), C.c_uint64(salt), ptr(mate), ptr(agg),
                          C.byref(nH), C.byref(rounds), stream)
+    return st, nH.value, rounds.value
+
+
+def amg_match_noalloc(n, row_ptr, col_idx, s, salt, mate, agg, stream=None):
+    """amg_match without device allocation (fixed in-library scratch, n <= 2^20)."""
+    nH = C.c_int64(0)
+    rounds = C.c_int(0)
+    st = lib().amg_match_noalloc(n, ptr(row_ptr), ptr(col_idx), ptr(s), C.c_uint64(salt), ptr(mate),
+                                 ptr(agg), C.byref(nH), C.byref(rounds), stream)
     return st, nH.value, rounds.value
 
 
