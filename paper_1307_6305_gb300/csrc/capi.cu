@@ -1,5 +1,6 @@
 // capi.cu -- the C ABI declared in include/amg.h: argument checks, handle
 // lifecycle, host/device staging, introspection and measurement hooks.
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -127,6 +128,8 @@ void destroy(amg_handle_s *h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   h->arena.release();
+  if (h->pre_exec) cudaGraphExecDestroy(h->pre_exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -172,6 +175,12 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   amg_handle_s *h = new amg_handle_s();
   h->opt = o;
   h->n = n;
+  {
+    // CUDA-graph replay of the preconditioner is the default; AMG_GB300_GRAPHS=0
+    // issues the same kernels one by one instead (debugging, A/B timing)
+    const char *env = getenv("AMG_GB300_GRAPHS");
+    h->use_graph = !(env && env[0] == '0');
+  }
   cudaGetDevice(&h->device);
   // NULL selects the legacy default stream, which orders our work after any
   // work the caller queued on it (e.g. a framework's default stream)
@@ -206,6 +215,7 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   if (!s) s = build_hierarchy(h, n, drp, dcol, dw, dd);
   for (void *p : tmp) pool_free(p, h->stream);
   if (!s) s = allocate_solve_buffers(h);
+  if (!s) s = build_dense_two_level(h);
   if (!s) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = fail(AMG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e));

@@ -126,7 +126,7 @@ struct Level {
   double coef[kMaxDegree + 1] = {};
   // per-level device scalars and work vectors (element type = cycle precision)
   double *scal = nullptr;  // [64]
-  void *s = nullptr, *Ta = nullptr, *Tb = nullptr;  // cycle scratch
+  void *u = nullptr, *s = nullptr, *Ta = nullptr, *Tb = nullptr;  // cycle scratch
   void *b = nullptr, *x = nullptr, *r = nullptr;    // inner flexible CG
   void *D[kMaxInner] = {}, *W[kMaxInner] = {};
 };
@@ -175,10 +175,23 @@ struct amg_handle_s {
   float *r32 = nullptr, *z32 = nullptr;
   // coarsest conversion buffers (fp32 mode)
   double *cb64 = nullptr, *cx64 = nullptr;
+  // level Bk = L-2 applied as one dense operator (fp64, row major), or Bk = -1
+  int Bk = -1;
+  double *Bd = nullptr;
+  double *bb64 = nullptr, *bx64 = nullptr;
   double setup_ms = 0;
   double grid_complexity = 0, op_complexity = 0;
   int64_t launches = 0;
   amg::Timing timing;
+  // the preconditioner application z = K_0(r) on (or_, oz) captured once as a
+  // CUDA graph and replayed every outer iteration
+  bool use_graph = true;
+  bool capturing = false;
+  cudaStream_t cap = nullptr;       // private stream used only for capture
+  cudaGraphExec_t pre_exec = nullptr;
+  bool graph_timed = false;         // graph holds timing event-record nodes
+  size_t graph_events = 0;          // timing events recorded by one replay
+  int64_t graph_kernels = 0;        // kernel nodes per replay
   std::string err;
 };
 
@@ -191,6 +204,7 @@ amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32
                       int *rounds, int64_t *launches);
 // solve.cu
 amg_status allocate_solve_buffers(amg_handle_s *h);
+amg_status build_dense_two_level(amg_handle_s *h);
 amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol,
                      amg_info *info, int *iters, double *rel, double *true_rel, int *converged);
 amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y);

@@ -213,19 +213,21 @@ __device__ void finalize(const Fin &f, const double *sums, int nd) {
 
 // per-thread partial sums -> per-block partials -> last block folds the
 // partials in block order (deterministic for a fixed grid) and finalises
-template <typename T>
-__device__ void reduce_and_finalize(double (&acc)[kMaxDots], int nd, double *partial,
-                                    unsigned *ticket, const Fin &fin) {
-  __shared__ double sh[kThreads / 32][kMaxDots];
+template <int ND>
+__device__ __forceinline__ void reduce_and_finalize(const double (&acc)[ND], double *partial,
+                                                    unsigned *ticket, const Fin &fin) {
+  __shared__ double sh[kThreads / 32][ND];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = 0; q < nd; ++q) {
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
     const double v = warp_sum(acc[q]);
     if (lane == 0) sh[warp][q] = v;
   }
   __syncthreads();
-  if (threadIdx.x < nd) {
+  if (threadIdx.x < ND) {
     double v = 0.0;
+#pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) v += sh[w][threadIdx.x];
     partial[blockIdx.x * kMaxDots + threadIdx.x] = v;
   }
@@ -235,31 +237,103 @@ __device__ void reduce_and_finalize(double (&acc)[kMaxDots], int nd, double *par
   __syncthreads();
   if (!last) return;
   if (warp == 0) {
-    double sums[kMaxDots];
-    for (int q = 0; q < nd; ++q) {
+    double sums[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
       double v = 0.0;
       for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(&partial[b * kMaxDots + q]);
       sums[q] = warp_sum(v);
     }
     if (lane == 0) {
-      finalize(fin, sums, nd);
+      finalize(fin, sums, ND);
       *ticket = 0u;
     }
   }
 }
 
-template <typename T>
+template <typename T, int ND>
 __global__ void __launch_bounds__(kThreads) k_dots(int64_t n, DotSpec<T> spec, double *partial,
                                                    unsigned *ticket, Fin fin) {
-  double acc[kMaxDots];
-  for (int q = 0; q < kMaxDots; ++q) acc[q] = 0.0;
+  double acc[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) acc[q] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    for (int q = 0; q < spec.nd; ++q) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
       const double a = (double)spec.a[q][i];
       acc[q] += spec.b[q] ? a * (double)spec.b[q][i] : a;
     }
   }
-  reduce_and_finalize<T>(acc, spec.nd, partial, ticket, fin);
+  reduce_and_finalize<ND>(acc, partial, ticket, fin);
+}
+
+// y = A x fused with ND dot products; a null operand pointer stands for y
+template <typename T, int ND>
+__global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *__restrict__ x,
+                                                        T *__restrict__ y, DotSpec<T> spec,
+                                                        double *partial, unsigned *ticket, Fin fin) {
+  double acc[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) acc[q] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    const T yi = apply_row(A, x, i);
+    y[i] = yi;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      const double a = spec.a[q] ? (double)spec.a[q][i] : (double)yi;
+      const double b = spec.b[q] ? (double)spec.b[q][i] : (double)yi;
+      acc[q] += a * b;
+    }
+  }
+  reduce_and_finalize<ND>(acc, partial, ticket, fin);
+}
+
+// inner step it > 0: D -= sum_l beta_l D_l, W -= sum_l beta_l W_l, then
+// rho = D.W and sigma = D.rin (FIN_IALPHA)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_orth_dots(int64_t n, T *D, T *W, DotSpec<T> prev,
+                                                        const double *beta, const T *__restrict__ rin,
+                                                        double *partial, unsigned *ticket, Fin fin) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T d = D[i], w = W[i];
+    for (int l = 0; l < prev.nd; ++l) {
+      const T bl = (T)beta[l];
+      d -= bl * prev.a[l][i];
+      w -= bl * prev.b[l][i];
+    }
+    D[i] = d;
+    W[i] = w;
+    acc[0] += (double)d * (double)w;
+    acc[1] += (double)d * (double)rin[i];
+  }
+  reduce_and_finalize<2>(acc, partial, ticket, fin);
+}
+
+// x_out = u + P e_H and s = r - A x_out in one pass: neighbours' values are
+// formed on the fly as u_j + e_H[agg_j] (the same rounding as forming x_out
+// first), so x_out never needs a second read
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, const int *__restrict__ agg,
+                                                               const T *__restrict__ eH,
+                                                               const T *__restrict__ u, const T *__restrict__ r,
+                                                               T *__restrict__ xout, T *__restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const T xi = u[i] + eH[agg[i]];
+  xout[i] = xi;
+  const int sl = i >> 5, lane = i & 31;
+  const int64_t base = A.sptr[sl];
+  const int w = (int)((A.sptr[sl + 1] - base) >> 5);
+  const int32_t *__restrict__ c = A.scol + base + lane;
+  const T *__restrict__ v = A.val + base + lane;
+  T acc = A.diag[i] * xi;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) {
+    const int j = c[k * kSlice];
+    acc = fma(v[k * kSlice], u[j] + eH[agg[j]], acc);
+  }
+  s[i] = r[i] - acc;
 }
 
 // y = z - sum_l beta_l V_l (beta read from the device)
@@ -290,8 +364,7 @@ __global__ void k_inner_update(int64_t n, int it, bool upd_r, const double *sc, 
 __global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const double *sc, const double *d,
                                                            const double *q, double *x, double *r,
                                                            double *partial, unsigned *ticket, Fin fin) {
-  double acc[kMaxDots];
-  acc[0] = 0.0;
+  double acc[1] = {0.0};
   const double a = sc[32];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(a, d[i], x[i]);
@@ -299,12 +372,121 @@ __global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const doub
     r[i] = ri;
     acc[0] += ri * ri;
   }
-  reduce_and_finalize<double>(acc, 1, partial, ticket, fin);
+  reduce_and_finalize<1>(acc, partial, ticket, fin);
 }
 
 __global__ void k_shift(int64_t n, const double *src, double *dst, const double *mean) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[i] - *mean;
+}
+
+// ---------------------------------------------------------------------------
+// block (multi-vector) kernels: a block X of k vectors is stored row major,
+// X[i * k + c] = component i of vector c, so one thread per (row, column)
+// reads each stored matrix entry once per row (broadcast) and the gathered
+// neighbour values of consecutive columns are contiguous
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T sell_row_block(const SellView<T> &A, const T *__restrict__ X, int k, int row,
+                                            int c, T acc) {
+  const int s = row >> 5, lane = row & 31;
+  const int64_t base = A.sptr[s];
+  const int w = (int)((A.sptr[s + 1] - base) >> 5);
+  const int32_t *__restrict__ cc = A.scol + base + lane;
+  const T *__restrict__ v = A.val + base + lane;
+  for (int q = 0; q < w; ++q) acc = fma(v[q * kSlice], X[(int64_t)cc[q * kSlice] * k + c], acc);
+  return acc;
+}
+
+template <typename T, bool ADD>
+__global__ void k_bcheb_first(SellView<T> A, int k, const T *__restrict__ R, T *__restrict__ T1,
+                              T *__restrict__ X, T sa, T ca, T b0, T b1) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)A.n * k) return;
+  const int i = (int)(idx / k), c = (int)(idx % k);
+  const T ri = R[idx];
+  const T Ar = sell_row_block(A, R, k, i, c, A.diag[i] * ri);
+  const T t1 = fma(sa, Ar, -ca * ri);
+  T1[idx] = t1;
+  const T inc = fma(b1, t1, b0 * ri);
+  X[idx] = ADD ? X[idx] + inc : inc;
+}
+
+template <typename T>
+__global__ void k_bcheb_step(SellView<T> A, int k, const T *__restrict__ Tc, const T *Tp, T *Tn,
+                             T *__restrict__ X, T sa, T ca, T bj) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)A.n * k) return;
+  const int i = (int)(idx / k), c = (int)(idx % k);
+  const T tc = Tc[idx];
+  const T At = sell_row_block(A, Tc, k, i, c, A.diag[i] * tc);
+  const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[idx];
+  Tn[idx] = tn;
+  X[idx] = fma(bj, tn, X[idx]);
+}
+
+template <typename T, bool ADD>
+__global__ void k_bscale(int64_t nk, const T *__restrict__ R, T *__restrict__ X, T b0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nk) return;
+  X[idx] = ADD ? X[idx] + b0 * R[idx] : b0 * R[idx];
+}
+
+template <typename T>
+__global__ void k_bresidual(SellView<T> A, int k, const T *__restrict__ X, const T *__restrict__ R,
+                            T *__restrict__ S) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)A.n * k) return;
+  const int i = (int)(idx / k), c = (int)(idx % k);
+  S[idx] = R[idx] - sell_row_block(A, X, k, i, c, A.diag[i] * X[idx]);
+}
+
+template <typename T>
+__global__ void k_brestrict(int nH, int k, const int *__restrict__ ptr, const int *__restrict__ mem,
+                            const T *__restrict__ S, T *__restrict__ RH) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nH * k) return;
+  const int I = (int)(idx / k), c = (int)(idx % k);
+  T acc = T(0);
+  for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += S[(int64_t)mem[a] * k + c];
+  RH[idx] = acc;
+}
+
+template <typename T>
+__global__ void k_bprolong_residual(SellView<T> A, int k, const int *__restrict__ agg,
+                                    const T *__restrict__ EH, const T *__restrict__ U,
+                                    const T *__restrict__ R, T *__restrict__ X, T *__restrict__ S) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)A.n * k) return;
+  const int i = (int)(idx / k), c = (int)(idx % k);
+  const T xi = U[idx] + EH[(int64_t)agg[i] * k + c];
+  X[idx] = xi;
+  const int s = i >> 5, lane = i & 31;
+  const int64_t base = A.sptr[s];
+  const int w = (int)((A.sptr[s + 1] - base) >> 5);
+  T acc = A.diag[i] * xi;
+  for (int q = 0; q < w; ++q) {
+    const int j = A.scol[base + q * kSlice + lane];
+    acc = fma(A.val[base + q * kSlice + lane], U[(int64_t)j * k + c] + EH[(int64_t)agg[j] * k + c], acc);
+  }
+  S[idx] = R[idx] - acc;
+}
+
+// X = Z B for a dense row-major n x n matrix Z and an n x k block B
+__global__ void k_bdense(int n, int k, const double *__restrict__ Z, const double *__restrict__ B,
+                         double *__restrict__ X) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * k) return;
+  const int i = (int)(idx / k), c = (int)(idx % k);
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) acc = fma(Z[(int64_t)i * n + j], B[(int64_t)j * k + c], acc);
+  X[idx] = acc;
+}
+
+__global__ void k_identity(int n, double *__restrict__ X) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  X[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +509,42 @@ SellView<float> view<float>(const amg::Level &L) {
 
 template <typename T>
 static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin fin) {
-  k_dots<T><<<red_grid(n), kThreads, 0, h->stream>>>(n, spec, h->red.partial, h->red.ticket, fin);
+  const unsigned g = red_grid(n);
+  double *P = h->red.partial;
+  unsigned *tk = h->red.ticket;
+  cudaStream_t st = h->stream;
+  switch (spec.nd) {
+    case 1: k_dots<T, 1><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 2: k_dots<T, 2><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 3: k_dots<T, 3><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 4: k_dots<T, 4><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 5: k_dots<T, 5><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 6: k_dots<T, 6><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 7: k_dots<T, 7><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    default: k_dots<T, 8><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+  }
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
+template <typename T>
+static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotSpec<T> &spec, Fin fin) {
+  amg::Level &L = h->lv[k];
+  const unsigned g = red_grid(L.n);
+  double *P = h->red.partial;
+  unsigned *tk = h->red.ticket;
+  cudaStream_t st = h->stream;
+  const SellView<T> A = view<T>(L);
+  switch (spec.nd) {
+    case 1: k_spmv_dots<T, 1><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 2: k_spmv_dots<T, 2><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 3: k_spmv_dots<T, 3><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 4: k_spmv_dots<T, 4><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 5: k_spmv_dots<T, 5><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 6: k_spmv_dots<T, 6><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 7: k_spmv_dots<T, 7><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    default: k_spmv_dots<T, 8><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+  }
   SLAUNCH(h);
   return AMG_OK;
 }
@@ -340,7 +557,20 @@ static amg_status timing_record(amg_handle_s *h, cudaEvent_t *ev) {
     tm.ev.push_back(e);
   }
   *ev = tm.ev[tm.used++];
-  AMG_CUDA_TRY(cudaEventRecord(*ev, h->stream));
+  if (h->capturing) AMG_CUDA_TRY(cudaEventRecordWithFlags(*ev, h->stream, cudaEventRecordExternal));
+  else AMG_CUDA_TRY(cudaEventRecord(*ev, h->stream));
+  return AMG_OK;
+}
+
+// add the elapsed times of the first `count` recorded events (pairs)
+static amg_status timing_accumulate(amg_handle_s *h, size_t count) {
+  Timing &tm = h->timing;
+  for (size_t i = 0; i + 1 < count; i += 2) {
+    float ms = 0.f;
+    AMG_CUDA_TRY(cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]));
+    tm.total_ms += ms;
+    ++tm.launches;
+  }
   return AMG_OK;
 }
 
@@ -348,12 +578,7 @@ static amg_status timing_flush(amg_handle_s *h) {
   Timing &tm = h->timing;
   if (!tm.used) return AMG_OK;
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  for (size_t i = 0; i + 1 < tm.used; i += 2) {
-    float ms = 0.f;
-    AMG_CUDA_TRY(cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]));
-    tm.total_ms += ms;
-    ++tm.launches;
-  }
+  AMG_TRY(timing_accumulate(h, tm.used));
   tm.used = 0;
   return AMG_OK;
 }
@@ -425,7 +650,10 @@ template <typename T>
 static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x);
 
 // nu steps of flexible CG on level k (1 <= k < L-1) from x = 0:
-// b = level k's input (r_H of level k-1), result in level k's x
+// b = level k's input (r_H of level k-1), result in level k's x.  Step it:
+//   D = K_k(rin);  W = A D with the dots D_l.W (l < it) -> beta_l;
+//   D -= sum beta_l D_l, W -= sum beta_l W_l with rho = D.W, sigma = D.rin
+//   -> alpha (for it = 0 both dots come with the SpMV);  x, r update.
 template <typename T>
 static amg_status inner_fcg(amg_handle_s *h, int k) {
   amg::Level &L = h->lv[k];
@@ -438,58 +666,159 @@ static amg_status inner_fcg(amg_handle_s *h, int k) {
     const T *rin = (it == 0) ? b : r;
     T *D = (T *)L.D[it], *W = (T *)L.W[it];
     AMG_TRY(kcycle<T>(h, k, rin, D));
-    k_spmv<T><<<nblk(n), kThreads, 0, st>>>(view<T>(L), D, W);
-    SLAUNCH(h);
-    if (it > 0) {
+    if (it == 0) {
+      DotSpec<T> sp{};
+      sp.a[0] = D;
+      sp.b[0] = nullptr;  // D . (A D)
+      sp.a[1] = rin;
+      sp.b[1] = D;
+      sp.nd = 2;
+      AMG_TRY(spmv_dots<T>(h, k, D, W, sp, Fin{FIN_IALPHA, 0, 0.0, L.scal}));
+    } else {
       DotSpec<T> sp{};
       for (int l = 0; l < it; ++l) {
         sp.a[l] = (const T *)L.D[l];
-        sp.b[l] = W;
+        sp.b[l] = nullptr;  // D_l . (A D)
       }
       sp.nd = it;
-      AMG_TRY(dots<T>(h, n, sp, Fin{FIN_IBETA, 0, 0.0, L.scal}));
-      DotSpec<T> vd{}, vw{};
+      AMG_TRY(spmv_dots<T>(h, k, D, W, sp, Fin{FIN_IBETA, 0, 0.0, L.scal}));
+      DotSpec<T> prev{};
       for (int l = 0; l < it; ++l) {
-        vd.a[l] = (const T *)L.D[l];
-        vw.a[l] = (const T *)L.W[l];
+        prev.a[l] = (const T *)L.D[l];
+        prev.b[l] = (const T *)L.W[l];
       }
-      vd.nd = vw.nd = it;
-      k_axpy_multi<T><<<nblk(n), kThreads, 0, st>>>(n, D, D, vd, L.scal + 16);
-      SLAUNCH(h);
-      k_axpy_multi<T><<<nblk(n), kThreads, 0, st>>>(n, W, W, vw, L.scal + 16);
+      prev.nd = it;
+      k_orth_dots<T><<<red_grid(n), kThreads, 0, st>>>(n, D, W, prev, L.scal + 16, rin, h->red.partial,
+                                                        h->red.ticket, Fin{FIN_IALPHA, it, 0.0, L.scal});
       SLAUNCH(h);
     }
-    DotSpec<T> sp{};
-    sp.a[0] = D;
-    sp.b[0] = W;
-    sp.a[1] = D;
-    sp.b[1] = rin;
-    sp.nd = 2;
-    AMG_TRY(dots<T>(h, n, sp, Fin{FIN_IALPHA, it, 0.0, L.scal}));
     k_inner_update<T><<<nblk(n), kThreads, 0, st>>>(n, it, it + 1 < nu, L.scal, D, W, rin, x, r);
     SLAUNCH(h);
   }
   return AMG_OK;
 }
 
-// x = K_k(r): W(1,1) nonlinear AMLI cycle (Sec. 3 two-level steps, Sec. 4)
+// x = K_k(r): W(1,1) nonlinear AMLI cycle (Sec. 3 two-level steps, Sec. 4):
+//   u = q_m(A) r;  s = r - A u;  r_H = P^T s;  e_H = coarse solve or nu inner
+//   flexible-CG steps;  x = u + P e_H with s = r - A x in the same pass;
+//   x += q_m(A) s.
+template <typename T>
+static amg_status dense_two_level(amg_handle_s *h, const T *r, T *x);
+
+template <>
+amg_status dense_two_level<double>(amg_handle_s *h, const double *r, double *x) {
+  const int n = h->lv[h->Bk].n;
+  k_dense_mv<<<nblk((int64_t)n * 32), kThreads, 0, h->stream>>>(n, h->Bd, r, x);
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
+template <>
+amg_status dense_two_level<float>(amg_handle_s *h, const float *r, float *x) {
+  const int n = h->lv[h->Bk].n;
+  k_convert<float, double><<<nblk(n), kThreads, 0, h->stream>>>(n, r, h->bb64);
+  SLAUNCH(h);
+  AMG_TRY(dense_two_level<double>(h, h->bb64, h->bx64));
+  k_convert<double, float><<<nblk(n), kThreads, 0, h->stream>>>(n, h->bx64, x);
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
 template <typename T>
 static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   if (k == h->L - 1) return coarse_solve<T>(h, r, x);
+  if (k == h->Bk) return dense_two_level<T>(h, r, x);
   amg::Level &L = h->lv[k];
   amg::Level &N = h->lv[k + 1];
   cudaStream_t st = h->stream;
-  T *s = (T *)L.s;
-  AMG_TRY(smooth<T>(h, k, r, x, false));
-  AMG_TRY(residual<T>(h, k, x, r, s));
+  T *s = (T *)L.s, *u = (T *)L.u;
+  AMG_TRY(smooth<T>(h, k, r, u, false));
+  AMG_TRY(residual<T>(h, k, u, r, s));
   k_restrict<T><<<nblk(L.nH), kThreads, 0, st>>>(L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b);
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
-  k_prolong_add<T><<<nblk(L.n), kThreads, 0, st>>>(L.n, L.agg, (const T *)N.x, x);
+  k_prolong_residual<T><<<nblk(L.n), kThreads, 0, st>>>(view<T>(L), L.agg, (const T *)N.x, u, r, x, s);
   SLAUNCH(h);
-  AMG_TRY(residual<T>(h, k, x, r, s));
   AMG_TRY(smooth<T>(h, k, s, x, true));
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the level above the coarsest as one dense operator
+//
+// With the exact coarse solve, the W(1,1) cycle at level L-2 is linear: it is
+// the symmetrised two-level preconditioner of Sec. 3,
+//   B = Rbar + (I - RA) P A_H^+ P^T (I - AR),  Rbar = 2R - RAR,  R = q_m(A).
+// It is visited 2^(L-2) times per outer iteration, each visit a chain of
+// 2m+3 tiny dependent kernels; applying B instead is a single dense matvec.
+// B is built once by running that cycle, step for step, on the identity
+// block (block kernels above, fp64).
+// ---------------------------------------------------------------------------
+constexpr int kDenseTwoLevelMax = 1024;
+
+static amg_status bsmooth(amg_handle_s *h, int k, int ncol, const double *R, double *X, bool add,
+                          double *Ta, double *Tb) {
+  amg::Level &L = h->lv[k];
+  const int m = h->opt.degree;
+  const SellView<double> A = view<double>(L);
+  const double sa = 2.0 / (L.lam1 - L.lam0), ca = (L.lam1 + L.lam0) / (L.lam1 - L.lam0);
+  const int64_t nk = (int64_t)L.n * ncol;
+  cudaStream_t st = h->stream;
+  if (m == 0) {
+    if (add) k_bscale<double, true><<<nblk(nk), kThreads, 0, st>>>(nk, R, X, L.coef[0]);
+    else k_bscale<double, false><<<nblk(nk), kThreads, 0, st>>>(nk, R, X, L.coef[0]);
+    SLAUNCH(h);
+    return AMG_OK;
+  }
+  if (add) k_bcheb_first<double, true><<<nblk(nk), kThreads, 0, st>>>(A, ncol, R, Ta, X, sa, ca, L.coef[0], L.coef[1]);
+  else k_bcheb_first<double, false><<<nblk(nk), kThreads, 0, st>>>(A, ncol, R, Ta, X, sa, ca, L.coef[0], L.coef[1]);
+  SLAUNCH(h);
+  const double *Tp = R;
+  double *Tc = Ta;
+  for (int j = 2; j <= m; ++j) {
+    double *Tn = (j == 2) ? Tb : const_cast<double *>(Tp);
+    k_bcheb_step<double><<<nblk(nk), kThreads, 0, st>>>(A, ncol, Tc, Tp, Tn, X, sa, ca, L.coef[j]);
+    SLAUNCH(h);
+    Tp = Tc;
+    Tc = Tn;
+  }
+  return AMG_OK;
+}
+
+amg_status build_dense_two_level(amg_handle_s *h) {
+  h->Bk = -1;
+  if (h->L < 2) return AMG_OK;
+  const int k = h->L - 2;
+  amg::Level &L = h->lv[k];
+  const int n = L.n, nc = h->nc;
+  if (n > kDenseTwoLevelMax) return AMG_OK;
+  cudaStream_t st = h->stream;
+  const int64_t nn = (int64_t)n * n, cn = (int64_t)nc * n;
+  double *I = nullptr, *U = nullptr, *S = nullptr, *Ta = nullptr, *Tb = nullptr, *RH = nullptr, *EH = nullptr;
+  AMG_TRY(pool_alloc((void **)&I, sizeof(double) * nn, st));
+  AMG_TRY(pool_alloc((void **)&U, sizeof(double) * nn, st));
+  AMG_TRY(pool_alloc((void **)&S, sizeof(double) * nn, st));
+  AMG_TRY(pool_alloc((void **)&Ta, sizeof(double) * nn, st));
+  AMG_TRY(pool_alloc((void **)&Tb, sizeof(double) * nn, st));
+  AMG_TRY(pool_alloc((void **)&RH, sizeof(double) * cn, st));
+  AMG_TRY(pool_alloc((void **)&EH, sizeof(double) * cn, st));
+  AMG_TRY(h->arena.get(&h->Bd, (size_t)nn));
+  k_identity<<<nblk(nn), kThreads, 0, st>>>(n, I);
+  SLAUNCH(h);
+  const SellView<double> A = view<double>(L);
+  AMG_TRY(bsmooth(h, k, n, I, U, false, Ta, Tb));                       // U = R I
+  k_bresidual<double><<<nblk(nn), kThreads, 0, st>>>(A, n, U, I, S);   // S = I - A U
+  SLAUNCH(h);
+  k_brestrict<double><<<nblk(cn), kThreads, 0, st>>>(nc, n, L.agg_ptr, L.agg_mem, S, RH);
+  SLAUNCH(h);
+  k_bdense<<<nblk(cn), kThreads, 0, st>>>(nc, n, h->Z, RH, EH);         // A_H^+ P^T S
+  SLAUNCH(h);
+  k_bprolong_residual<double><<<nblk(nn), kThreads, 0, st>>>(A, n, L.agg, EH, U, I, h->Bd, S);
+  SLAUNCH(h);
+  AMG_TRY(bsmooth(h, k, n, S, h->Bd, true, Ta, Tb));                    // B = U + P.. + R S
+  for (double *p : {I, U, S, Ta, Tb, RH, EH}) pool_free(p, st);
+  h->Bk = k;
   return AMG_OK;
 }
 
@@ -505,6 +834,7 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     const size_t n = (size_t)std::max(V.n, 1);
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1) {
+      AMG_TRY(h->arena.alloc(&V.u, es * n));
       AMG_TRY(h->arena.alloc(&V.s, es * n));
       AMG_TRY(h->arena.alloc(&V.Ta, es * n));
       AMG_TRY(h->arena.alloc(&V.Tb, es * n));
@@ -534,6 +864,11 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   AMG_TRY(h->arena.get(&h->red.partial, (size_t)kRedBlocks * kMaxDots));
   AMG_TRY(h->arena.get(&h->red.ticket, 1));
   AMG_CUDA_TRY(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
+  if (f32 && h->L >= 2) {
+    const size_t nb = (size_t)std::max(h->lv[h->L - 2].n, 1);
+    AMG_TRY(h->arena.get(&h->bb64, nb));
+    AMG_TRY(h->arena.get(&h->bx64, nb));
+  }
   if (f32) {
     AMG_TRY(h->arena.get(&h->r32, n0));
     AMG_TRY(h->arena.get(&h->z32, n0));
@@ -556,6 +891,57 @@ static amg_status precondition(amg_handle_s *h, const double *r, double *z) {
     return AMG_OK;
   }
   return kcycle<double>(h, 0, r, z);
+}
+
+// Capture z = K_0(r) on the fixed buffers (or_, oz) as a CUDA graph.  All
+// Krylov scalars live on the device, so the launch sequence of one
+// application is static and the graph stays valid for the handle's lifetime.
+static amg_status ensure_graph(amg_handle_s *h) {
+  if (!h->use_graph) return AMG_OK;
+  const bool timed = h->timing.enabled;
+  if (h->pre_exec && h->graph_timed == timed) return AMG_OK;
+  if (h->pre_exec) {
+    cudaGraphExecDestroy(h->pre_exec);
+    h->pre_exec = nullptr;
+  }
+  if (!h->cap) AMG_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  const cudaStream_t saved = h->stream;
+  const int64_t saved_launches = h->launches;
+  h->timing.used = 0;
+  AMG_CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  h->stream = h->cap;
+  h->capturing = true;
+  const amg_status s = precondition(h, h->or_, h->oz);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+  h->stream = saved;
+  h->capturing = false;
+  h->graph_kernels = h->launches - saved_launches;
+  h->launches = saved_launches;
+  if (s != AMG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&h->pre_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) {
+    h->pre_exec = nullptr;
+    return fail(AMG_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e2));
+  }
+  h->graph_timed = timed;
+  h->graph_events = h->timing.used;
+  h->timing.used = 0;
+  return AMG_OK;
+}
+
+static amg_status run_precondition(amg_handle_s *h) {
+  if (h->pre_exec) {
+    AMG_CUDA_TRY(cudaGraphLaunch(h->pre_exec, h->stream));
+    h->launches += h->graph_kernels;
+    return AMG_OK;
+  }
+  return precondition(h, h->or_, h->oz);
 }
 
 // ---------------------------------------------------------------------------
@@ -601,11 +987,12 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
   int it = 0, converged = (nb == 0.0), nwin = 0;
   double res = nb > 0 ? 1.0 : 0.0;
   amg_status status = AMG_OK;
+  AMG_TRY(ensure_graph(h));
   if (h->timing.enabled) h->timing.used = 0;
   while (!converged && it < h->opt.max_iters) {
     if (it % R == 0) nwin = 0;
     double *d = h->oD[nwin], *q = h->oQ[nwin];
-    AMG_TRY(precondition(h, h->or_, h->oz));
+    AMG_TRY(run_precondition(h));
     if (nwin > 0) {
       DotSpec<double> sp{};
       for (int j = 0; j < nwin; ++j) {
@@ -638,6 +1025,7 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
     SLAUNCH(h);
     AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 33, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->pre_exec && h->graph_timed) AMG_TRY(timing_accumulate(h, h->graph_events));
     if (hp[1] != 0.0) {
       status = fail(AMG_ERR_BREAKDOWN, "flexible CG breakdown: d^T A d <= 0 or non-finite");
       break;
