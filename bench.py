@@ -150,6 +150,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="fp32: the whole preconditioner in fp32 inside the fp64 outer CG")
     args = ap.parse_args()
     rank, world, local = dist_env()
     g, p = gg.workload(WORKLOAD)
@@ -192,7 +194,8 @@ def main():
     bd = torch.as_tensor(b, device=dev)
     xd = torch.zeros_like(bd)
     in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + b.nbytes
-    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"])
+    prec = amg.AMG_PREC_FP32 if args.precision == "fp32" else amg.AMG_PREC_FP64
+    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=prec)
     state = {"launches": 0, "iters": [], "setup_ms": [], "solve_ms": [], "kt": [0, 0.0, 0.0]}
 
     def step(timed_kernel: bool):
@@ -294,7 +297,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 preconditioner / f64 outer",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": 1, "nnz_offdiag": g.nnz,
                    "l2": f"inputs {in_bytes / 2**20:.0f} MiB > 129 MiB L2 (no flush)",
                    "parallelism": f"replicas x{world}"},

@@ -216,6 +216,7 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   for (void *p : tmp) pool_free(p, h->stream);
   if (!s) s = allocate_solve_buffers(h);
   if (!s) s = build_dense_two_level(h);
+  if (!s) s = prepare_tail(h);
   if (!s) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = fail(AMG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e));

@@ -179,6 +179,11 @@ struct amg_handle_s {
   int Bk = -1;
   double *Bd = nullptr;
   double *bb64 = nullptr, *bx64 = nullptr;
+  // levels >= tail_k0 run as one persistent cluster kernel per inner solve
+  int tail_k0 = -1;
+  int tail_csize = 0;
+  bool tail_cluster = false;
+  void *tail_params = nullptr;
   double setup_ms = 0;
   double grid_complexity = 0, op_complexity = 0;
   int64_t launches = 0;
@@ -205,6 +210,9 @@ amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32
 // solve.cu
 amg_status allocate_solve_buffers(amg_handle_s *h);
 amg_status build_dense_two_level(amg_handle_s *h);
+// tail.cu
+amg_status prepare_tail(amg_handle_s *h);
+amg_status launch_tail(amg_handle_s *h);
 amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol,
                      amg_info *info, int *iters, double *rel, double *true_rel, int *converged);
 amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y);

@@ -737,6 +737,7 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   k_restrict<T><<<nblk(L.nH), kThreads, 0, st>>>(L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b);
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
+  else if (k + 1 == h->tail_k0) AMG_TRY(launch_tail(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
   k_prolong_residual<T><<<nblk(L.n), kThreads, 0, st>>>(view<T>(L), L.agg, (const T *)N.x, u, r, x, s);
   SLAUNCH(h);

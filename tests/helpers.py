@@ -68,3 +68,15 @@ def cheb_q(coef: np.ndarray, l0: float, l1: float, x: np.ndarray) -> np.ndarray:
 def matrix_function(A: np.ndarray, f) -> np.ndarray:
     lam, V = np.linalg.eigh(A)
     return (V * f(lam)) @ V.T
+
+
+def sparse_laplacian(g: gg.Graph):
+    """A = L_w + diag(d) of Eq. (1) as a scipy CSR matrix."""
+    import scipy.sparse as sp
+
+    n = g.n
+    W = sp.csr_matrix((g.w, g.col, g.rowptr), shape=(n, n))
+    deg = np.asarray(W.sum(axis=1)).ravel()
+    if g.d is not None:
+        deg = deg + g.d
+    return (sp.diags(deg) - W).tocsr()
