@@ -180,6 +180,11 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     // issues the same kernels one by one instead (debugging, A/B timing)
     const char *env = getenv("AMG_GB300_GRAPHS");
     h->use_graph = !(env && env[0] == '0');
+    // AMG_GB300_PDL=1 launches the solve kernels with programmatic dependent
+    // launch (overlapping each launch with its predecessor's drain); it
+    // measured neutral on the 128^3 workload, so it is off by default
+    const char *pdl = getenv("AMG_GB300_PDL");
+    h->use_pdl = (pdl && pdl[0] == '1');
   }
   cudaGetDevice(&h->device);
   // NULL selects the legacy default stream, which orders our work after any

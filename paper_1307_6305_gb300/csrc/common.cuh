@@ -182,8 +182,12 @@ struct amg_handle_s {
   // levels >= tail_k0 run as one persistent cluster kernel per inner solve
   int tail_k0 = -1;
   int tail_csize = 0;
-  bool tail_cluster = false;
+  int tail_mode = 0;
+  int tail_test_stall = 0;
   void *tail_params = nullptr;
+  unsigned *tail_bar = nullptr;
+  double *tail_gpart = nullptr;
+  int *tail_err = nullptr;           // set by a tail barrier that timed out
   double setup_ms = 0;
   double grid_complexity = 0, op_complexity = 0;
   int64_t launches = 0;
@@ -191,6 +195,7 @@ struct amg_handle_s {
   // the preconditioner application z = K_0(r) on (or_, oz) captured once as a
   // CUDA graph and replayed every outer iteration
   bool use_graph = true;
+  bool use_pdl = true;              // programmatic dependent launch of solve kernels
   bool capturing = false;
   cudaStream_t cap = nullptr;       // private stream used only for capture
   cudaGraphExec_t pre_exec = nullptr;

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "common.cuh"
 
@@ -31,6 +32,14 @@ namespace amg {
 
 constexpr int kThreads = 256;
 static inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// Programmatic dependent launch: wait until the preceding kernel has
+// completed and its writes are visible, then let the next kernel in the
+// stream be scheduled while this one runs (no-op for ordinary launches)
+__device__ __forceinline__ void pdl_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // SELL-32 row kernel: off-diagonal part of row `row` times x
@@ -57,6 +66,7 @@ template <typename T, bool ADD>
 __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> A, const T *__restrict__ r,
                                                          T *__restrict__ T1, T *__restrict__ x, T sa,
                                                          T ca, T b0, T b1) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const T ri = r[i];
@@ -72,6 +82,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> A, const T *__restrict__ Tc,
                                                         const T *Tp, T *Tn, T *__restrict__ x, T sa,
                                                         T ca, T bj) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const T tc = Tc[i];
@@ -83,6 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> A, const T *
 
 template <typename T, bool ADD>
 __global__ void k_scale(int n, const T *__restrict__ r, T *__restrict__ x, T b0) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   x[i] = ADD ? x[i] + b0 * r[i] : b0 * r[i];
@@ -91,6 +103,7 @@ __global__ void k_scale(int n, const T *__restrict__ r, T *__restrict__ x, T b0)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *__restrict__ x,
                                                        const T *__restrict__ r, T *__restrict__ s) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   s[i] = r[i] - apply_row(A, x, i);
@@ -99,14 +112,19 @@ __global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *_
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_spmv(SellView<T> A, const T *__restrict__ x,
                                                    T *__restrict__ y) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   y[i] = apply_row(A, x, i);
 }
 
+// r_H = P^T s; `flag`, when given, is the next level's inner-CG stop flag,
+// cleared here because the inner solve on r_H starts right after
 template <typename T>
 __global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__restrict__ mem,
-                           const T *__restrict__ s, T *__restrict__ rH) {
+                           const T *__restrict__ s, T *__restrict__ rH, double *flag) {
+  pdl_sync();
+  if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   T acc = T(0);
@@ -117,6 +135,7 @@ __global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__res
 template <typename T>
 __global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__restrict__ eH,
                               T *__restrict__ x) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   x[i] += eH[agg[i]];
@@ -124,6 +143,7 @@ __global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__res
 
 template <typename A, typename B>
 __global__ void k_convert(int64_t n, const A *__restrict__ a, B *__restrict__ b) {
+  pdl_sync();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (B)a[i];
 }
@@ -131,6 +151,7 @@ __global__ void k_convert(int64_t n, const A *__restrict__ a, B *__restrict__ b)
 // coarsest solve: x = Z b, one warp per row, fp64
 __global__ void k_dense_mv(int n, const double *__restrict__ Z, const double *__restrict__ b,
                            double *__restrict__ x) {
+  pdl_sync();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -254,6 +275,7 @@ __device__ __forceinline__ void reduce_and_finalize(const double (&acc)[ND], dou
 template <typename T, int ND>
 __global__ void __launch_bounds__(kThreads) k_dots(int64_t n, DotSpec<T> spec, double *partial,
                                                    unsigned *ticket, Fin fin) {
+  pdl_sync();
   double acc[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) acc[q] = 0.0;
@@ -272,6 +294,7 @@ template <typename T, int ND>
 __global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *__restrict__ x,
                                                         T *__restrict__ y, DotSpec<T> spec,
                                                         double *partial, unsigned *ticket, Fin fin) {
+  pdl_sync();
   double acc[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) acc[q] = 0.0;
@@ -294,6 +317,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_orth_dots(int64_t n, T *D, T *W, DotSpec<T> prev,
                                                         const double *beta, const T *__restrict__ rin,
                                                         double *partial, unsigned *ticket, Fin fin) {
+  pdl_sync();
   double acc[2] = {0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T d = D[i], w = W[i];
@@ -318,6 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
                                                                const T *__restrict__ eH,
                                                                const T *__restrict__ u, const T *__restrict__ r,
                                                                T *__restrict__ xout, T *__restrict__ s) {
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const T xi = u[i] + eH[agg[i]];
@@ -339,6 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
 // y = z - sum_l beta_l V_l (beta read from the device)
 template <typename T>
 __global__ void k_axpy_multi(int64_t n, T *y, const T *z, DotSpec<T> V, const double *beta) {
+  pdl_sync();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   T v = z[i];
@@ -351,6 +377,7 @@ __global__ void k_axpy_multi(int64_t n, T *y, const T *z, DotSpec<T> V, const do
 template <typename T>
 __global__ void k_inner_update(int64_t n, int it, bool upd_r, const double *sc, const T *D,
                                const T *W, const T *rin, T *x, T *r) {
+  pdl_sync();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool stopped_here = sc[24] != 0.0 && sc[8 + it] == 0.0;
@@ -364,6 +391,7 @@ __global__ void k_inner_update(int64_t n, int it, bool upd_r, const double *sc, 
 __global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const double *sc, const double *d,
                                                            const double *q, double *x, double *r,
                                                            double *partial, unsigned *ticket, Fin fin) {
+  pdl_sync();
   double acc[1] = {0.0};
   const double a = sc[32];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -376,6 +404,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const doub
 }
 
 __global__ void k_shift(int64_t n, const double *src, double *dst, const double *mean) {
+  pdl_sync();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[i] - *mean;
 }
@@ -401,6 +430,7 @@ __device__ __forceinline__ T sell_row_block(const SellView<T> &A, const T *__res
 template <typename T, bool ADD>
 __global__ void k_bcheb_first(SellView<T> A, int k, const T *__restrict__ R, T *__restrict__ T1,
                               T *__restrict__ X, T sa, T ca, T b0, T b1) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)A.n * k) return;
   const int i = (int)(idx / k), c = (int)(idx % k);
@@ -415,6 +445,7 @@ __global__ void k_bcheb_first(SellView<T> A, int k, const T *__restrict__ R, T *
 template <typename T>
 __global__ void k_bcheb_step(SellView<T> A, int k, const T *__restrict__ Tc, const T *Tp, T *Tn,
                              T *__restrict__ X, T sa, T ca, T bj) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)A.n * k) return;
   const int i = (int)(idx / k), c = (int)(idx % k);
@@ -427,6 +458,7 @@ __global__ void k_bcheb_step(SellView<T> A, int k, const T *__restrict__ Tc, con
 
 template <typename T, bool ADD>
 __global__ void k_bscale(int64_t nk, const T *__restrict__ R, T *__restrict__ X, T b0) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nk) return;
   X[idx] = ADD ? X[idx] + b0 * R[idx] : b0 * R[idx];
@@ -435,6 +467,7 @@ __global__ void k_bscale(int64_t nk, const T *__restrict__ R, T *__restrict__ X,
 template <typename T>
 __global__ void k_bresidual(SellView<T> A, int k, const T *__restrict__ X, const T *__restrict__ R,
                             T *__restrict__ S) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)A.n * k) return;
   const int i = (int)(idx / k), c = (int)(idx % k);
@@ -444,6 +477,7 @@ __global__ void k_bresidual(SellView<T> A, int k, const T *__restrict__ X, const
 template <typename T>
 __global__ void k_brestrict(int nH, int k, const int *__restrict__ ptr, const int *__restrict__ mem,
                             const T *__restrict__ S, T *__restrict__ RH) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nH * k) return;
   const int I = (int)(idx / k), c = (int)(idx % k);
@@ -456,6 +490,7 @@ template <typename T>
 __global__ void k_bprolong_residual(SellView<T> A, int k, const int *__restrict__ agg,
                                     const T *__restrict__ EH, const T *__restrict__ U,
                                     const T *__restrict__ R, T *__restrict__ X, T *__restrict__ S) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)A.n * k) return;
   const int i = (int)(idx / k), c = (int)(idx % k);
@@ -475,6 +510,7 @@ __global__ void k_bprolong_residual(SellView<T> A, int k, const int *__restrict_
 // X = Z B for a dense row-major n x n matrix Z and an n x k block B
 __global__ void k_bdense(int n, int k, const double *__restrict__ Z, const double *__restrict__ B,
                          double *__restrict__ X) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * k) return;
   const int i = (int)(idx / k), c = (int)(idx % k);
@@ -484,6 +520,7 @@ __global__ void k_bdense(int n, int k, const double *__restrict__ Z, const doubl
 }
 
 __global__ void k_identity(int n, double *__restrict__ X) {
+  pdl_sync();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
   X[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
@@ -491,6 +528,32 @@ __global__ void k_identity(int n, double *__restrict__ X) {
 
 // ---------------------------------------------------------------------------
 // host side
+// launch with programmatic stream serialization (PDL); arguments are
+// converted to the kernel's parameter types before their addresses are taken
+template <typename... KArgs>
+static amg_status plaunch_impl(amg_handle_s *h, cudaStream_t st, void (*kern)(KArgs...), dim3 g, dim3 b,
+                               KArgs... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = h->use_pdl ? 1 : 0;
+  void *p[] = {(void *)&args...};
+  const cudaError_t e = cudaLaunchKernelExC(&cfg, (const void *)kern, p);
+  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return AMG_OK;
+}
+
+template <typename... KArgs, typename... Args>
+static amg_status plaunch(amg_handle_s *h, cudaStream_t st, void (*kern)(KArgs...), dim3 g, dim3 b,
+                          Args &&...args) {
+  return plaunch_impl<KArgs...>(h, st, kern, g, b, KArgs(std::forward<Args>(args))...);
+}
+
 // ---------------------------------------------------------------------------
 static inline unsigned red_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kThreads - 1) / kThreads));
@@ -514,14 +577,14 @@ static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin f
   unsigned *tk = h->red.ticket;
   cudaStream_t st = h->stream;
   switch (spec.nd) {
-    case 1: k_dots<T, 1><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    case 2: k_dots<T, 2><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    case 3: k_dots<T, 3><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    case 4: k_dots<T, 4><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    case 5: k_dots<T, 5><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    case 6: k_dots<T, 6><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    case 7: k_dots<T, 7><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
-    default: k_dots<T, 8><<<g, kThreads, 0, st>>>(n, spec, P, tk, fin); break;
+    case 1: AMG_TRY(plaunch(h, st, k_dots<T, 1>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    case 2: AMG_TRY(plaunch(h, st, k_dots<T, 2>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    case 3: AMG_TRY(plaunch(h, st, k_dots<T, 3>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    case 4: AMG_TRY(plaunch(h, st, k_dots<T, 4>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    case 5: AMG_TRY(plaunch(h, st, k_dots<T, 5>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    case 6: AMG_TRY(plaunch(h, st, k_dots<T, 6>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    case 7: AMG_TRY(plaunch(h, st, k_dots<T, 7>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
+    default: AMG_TRY(plaunch(h, st, k_dots<T, 8>, dim3(g), dim3(kThreads), n, spec, P, tk, fin)); break;
   }
   SLAUNCH(h);
   return AMG_OK;
@@ -536,14 +599,14 @@ static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotS
   cudaStream_t st = h->stream;
   const SellView<T> A = view<T>(L);
   switch (spec.nd) {
-    case 1: k_spmv_dots<T, 1><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    case 2: k_spmv_dots<T, 2><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    case 3: k_spmv_dots<T, 3><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    case 4: k_spmv_dots<T, 4><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    case 5: k_spmv_dots<T, 5><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    case 6: k_spmv_dots<T, 6><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    case 7: k_spmv_dots<T, 7><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
-    default: k_spmv_dots<T, 8><<<g, kThreads, 0, st>>>(A, x, y, spec, P, tk, fin); break;
+    case 1: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 2: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 2>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 3: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 3>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 4: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 4>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 5: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 5>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 6: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 6>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 7: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 7>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    default: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 8>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
   }
   SLAUNCH(h);
   return AMG_OK;
@@ -593,14 +656,14 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
   const T ca = (T)((L.lam1 + L.lam0) / (L.lam1 - L.lam0));
   cudaStream_t st = h->stream;
   if (m == 0) {
-    if (add) k_scale<T, true><<<nblk(L.n), kThreads, 0, st>>>(L.n, r, x, (T)L.coef[0]);
-    else k_scale<T, false><<<nblk(L.n), kThreads, 0, st>>>(L.n, r, x, (T)L.coef[0]);
+    if (add) AMG_TRY(plaunch(h, st, k_scale<T, true>, dim3(nblk(L.n)), dim3(kThreads), L.n, r, x, (T)L.coef[0]));
+    else AMG_TRY(plaunch(h, st, k_scale<T, false>, dim3(nblk(L.n)), dim3(kThreads), L.n, r, x, (T)L.coef[0]));
     SLAUNCH(h);
     return AMG_OK;
   }
   T *Ta = (T *)L.Ta, *Tb = (T *)L.Tb;
-  if (add) k_cheb_first<T, true><<<nblk(L.n), kThreads, 0, st>>>(A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
-  else k_cheb_first<T, false><<<nblk(L.n), kThreads, 0, st>>>(A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
+  if (add) AMG_TRY(plaunch(h, st, k_cheb_first<T, true>, dim3(nblk(L.n)), dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]));
+  else AMG_TRY(plaunch(h, st, k_cheb_first<T, false>, dim3(nblk(L.n)), dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]));
   SLAUNCH(h);
   const T *Tp = r;
   T *Tc = Ta;
@@ -609,7 +672,7 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     T *Tn = (j == 2) ? Tb : const_cast<T *>(Tp);
     cudaEvent_t e0, e1;
     if (timed) AMG_TRY(timing_record(h, &e0));
-    k_cheb_step<T><<<nblk(L.n), kThreads, 0, st>>>(A, Tc, Tp, Tn, x, sa, ca, (T)L.coef[j]);
+    AMG_TRY(plaunch(h, st, k_cheb_step<T>, dim3(nblk(L.n)), dim3(kThreads), A, Tc, Tp, Tn, x, sa, ca, (T)L.coef[j]));
     SLAUNCH(h);
     if (timed) AMG_TRY(timing_record(h, &e1));
     Tp = Tc;
@@ -621,7 +684,7 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
 template <typename T>
 static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s) {
   amg::Level &L = h->lv[k];
-  k_residual<T><<<nblk(L.n), kThreads, 0, h->stream>>>(view<T>(L), x, r, s);
+  AMG_TRY(plaunch(h, h->stream, k_residual<T>, dim3(nblk(L.n)), dim3(kThreads), view<T>(L), x, r, s));
   SLAUNCH(h);
   return AMG_OK;
 }
@@ -631,17 +694,17 @@ static amg_status coarse_solve(amg_handle_s *h, const T *b, T *x);
 
 template <>
 amg_status coarse_solve<double>(amg_handle_s *h, const double *b, double *x) {
-  k_dense_mv<<<nblk((int64_t)h->nc * 32), kThreads, 0, h->stream>>>(h->nc, h->Z, b, x);
+  AMG_TRY(plaunch(h, h->stream, k_dense_mv, dim3(nblk((int64_t)h->nc * 32)), dim3(kThreads), h->nc, h->Z, b, x));
   SLAUNCH(h);
   return AMG_OK;
 }
 
 template <>
 amg_status coarse_solve<float>(amg_handle_s *h, const float *b, float *x) {
-  k_convert<float, double><<<nblk(h->nc), kThreads, 0, h->stream>>>(h->nc, b, h->cb64);
+  AMG_TRY(plaunch(h, h->stream, k_convert<float, double>, dim3(nblk(h->nc)), dim3(kThreads), h->nc, b, h->cb64));
   SLAUNCH(h);
   AMG_TRY(coarse_solve<double>(h, h->cb64, h->cx64));
-  k_convert<double, float><<<nblk(h->nc), kThreads, 0, h->stream>>>(h->nc, h->cx64, x);
+  AMG_TRY(plaunch(h, h->stream, k_convert<double, float>, dim3(nblk(h->nc)), dim3(kThreads), h->nc, h->cx64, x));
   SLAUNCH(h);
   return AMG_OK;
 }
@@ -661,7 +724,7 @@ static amg_status inner_fcg(amg_handle_s *h, int k) {
   const int64_t n = L.n;
   cudaStream_t st = h->stream;
   T *b = (T *)L.b, *x = (T *)L.x, *r = (T *)L.r;
-  AMG_CUDA_TRY(cudaMemsetAsync(L.scal + 24, 0, sizeof(double), st));
+  // the stop flag L.scal[24] was cleared by the restriction that produced b
   for (int it = 0; it < nu; ++it) {
     const T *rin = (it == 0) ? b : r;
     T *D = (T *)L.D[it], *W = (T *)L.W[it];
@@ -688,11 +751,11 @@ static amg_status inner_fcg(amg_handle_s *h, int k) {
         prev.b[l] = (const T *)L.W[l];
       }
       prev.nd = it;
-      k_orth_dots<T><<<red_grid(n), kThreads, 0, st>>>(n, D, W, prev, L.scal + 16, rin, h->red.partial,
-                                                        h->red.ticket, Fin{FIN_IALPHA, it, 0.0, L.scal});
+      AMG_TRY(plaunch(h, st, k_orth_dots<T>, dim3(red_grid(n)), dim3(kThreads), n, D, W, prev, L.scal + 16, rin, h->red.partial,
+                                                        h->red.ticket, Fin{FIN_IALPHA, it, 0.0, L.scal}));
       SLAUNCH(h);
     }
-    k_inner_update<T><<<nblk(n), kThreads, 0, st>>>(n, it, it + 1 < nu, L.scal, D, W, rin, x, r);
+    AMG_TRY(plaunch(h, st, k_inner_update<T>, dim3(nblk(n)), dim3(kThreads), n, it, it + 1 < nu, L.scal, D, W, rin, x, r));
     SLAUNCH(h);
   }
   return AMG_OK;
@@ -708,7 +771,7 @@ static amg_status dense_two_level(amg_handle_s *h, const T *r, T *x);
 template <>
 amg_status dense_two_level<double>(amg_handle_s *h, const double *r, double *x) {
   const int n = h->lv[h->Bk].n;
-  k_dense_mv<<<nblk((int64_t)n * 32), kThreads, 0, h->stream>>>(n, h->Bd, r, x);
+  AMG_TRY(plaunch(h, h->stream, k_dense_mv, dim3(nblk((int64_t)n * 32)), dim3(kThreads), n, h->Bd, r, x));
   SLAUNCH(h);
   return AMG_OK;
 }
@@ -716,10 +779,10 @@ amg_status dense_two_level<double>(amg_handle_s *h, const double *r, double *x) 
 template <>
 amg_status dense_two_level<float>(amg_handle_s *h, const float *r, float *x) {
   const int n = h->lv[h->Bk].n;
-  k_convert<float, double><<<nblk(n), kThreads, 0, h->stream>>>(n, r, h->bb64);
+  AMG_TRY(plaunch(h, h->stream, k_convert<float, double>, dim3(nblk(n)), dim3(kThreads), n, r, h->bb64));
   SLAUNCH(h);
   AMG_TRY(dense_two_level<double>(h, h->bb64, h->bx64));
-  k_convert<double, float><<<nblk(n), kThreads, 0, h->stream>>>(n, h->bx64, x);
+  AMG_TRY(plaunch(h, h->stream, k_convert<double, float>, dim3(nblk(n)), dim3(kThreads), n, h->bx64, x));
   SLAUNCH(h);
   return AMG_OK;
 }
@@ -734,12 +797,13 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   T *s = (T *)L.s, *u = (T *)L.u;
   AMG_TRY(smooth<T>(h, k, r, u, false));
   AMG_TRY(residual<T>(h, k, u, r, s));
-  k_restrict<T><<<nblk(L.nH), kThreads, 0, st>>>(L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b);
+  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b,
+                  N.scal + 24));
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else if (k + 1 == h->tail_k0) AMG_TRY(launch_tail(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
-  k_prolong_residual<T><<<nblk(L.n), kThreads, 0, st>>>(view<T>(L), L.agg, (const T *)N.x, u, r, x, s);
+  AMG_TRY(plaunch(h, st, k_prolong_residual<T>, dim3(nblk(L.n)), dim3(kThreads), view<T>(L), L.agg, (const T *)N.x, u, r, x, s));
   SLAUNCH(h);
   AMG_TRY(smooth<T>(h, k, s, x, true));
   return AMG_OK;
@@ -767,19 +831,19 @@ static amg_status bsmooth(amg_handle_s *h, int k, int ncol, const double *R, dou
   const int64_t nk = (int64_t)L.n * ncol;
   cudaStream_t st = h->stream;
   if (m == 0) {
-    if (add) k_bscale<double, true><<<nblk(nk), kThreads, 0, st>>>(nk, R, X, L.coef[0]);
-    else k_bscale<double, false><<<nblk(nk), kThreads, 0, st>>>(nk, R, X, L.coef[0]);
+    if (add) AMG_TRY(plaunch(h, st, k_bscale<double, true>, dim3(nblk(nk)), dim3(kThreads), nk, R, X, L.coef[0]));
+    else AMG_TRY(plaunch(h, st, k_bscale<double, false>, dim3(nblk(nk)), dim3(kThreads), nk, R, X, L.coef[0]));
     SLAUNCH(h);
     return AMG_OK;
   }
-  if (add) k_bcheb_first<double, true><<<nblk(nk), kThreads, 0, st>>>(A, ncol, R, Ta, X, sa, ca, L.coef[0], L.coef[1]);
-  else k_bcheb_first<double, false><<<nblk(nk), kThreads, 0, st>>>(A, ncol, R, Ta, X, sa, ca, L.coef[0], L.coef[1]);
+  if (add) AMG_TRY(plaunch(h, st, k_bcheb_first<double, true>, dim3(nblk(nk)), dim3(kThreads), A, ncol, R, Ta, X, sa, ca, L.coef[0], L.coef[1]));
+  else AMG_TRY(plaunch(h, st, k_bcheb_first<double, false>, dim3(nblk(nk)), dim3(kThreads), A, ncol, R, Ta, X, sa, ca, L.coef[0], L.coef[1]));
   SLAUNCH(h);
   const double *Tp = R;
   double *Tc = Ta;
   for (int j = 2; j <= m; ++j) {
     double *Tn = (j == 2) ? Tb : const_cast<double *>(Tp);
-    k_bcheb_step<double><<<nblk(nk), kThreads, 0, st>>>(A, ncol, Tc, Tp, Tn, X, sa, ca, L.coef[j]);
+    AMG_TRY(plaunch(h, st, k_bcheb_step<double>, dim3(nblk(nk)), dim3(kThreads), A, ncol, Tc, Tp, Tn, X, sa, ca, L.coef[j]));
     SLAUNCH(h);
     Tp = Tc;
     Tc = Tn;
@@ -805,17 +869,17 @@ amg_status build_dense_two_level(amg_handle_s *h) {
   AMG_TRY(pool_alloc((void **)&RH, sizeof(double) * cn, st));
   AMG_TRY(pool_alloc((void **)&EH, sizeof(double) * cn, st));
   AMG_TRY(h->arena.get(&h->Bd, (size_t)nn));
-  k_identity<<<nblk(nn), kThreads, 0, st>>>(n, I);
+  AMG_TRY(plaunch(h, st, k_identity, dim3(nblk(nn)), dim3(kThreads), n, I));
   SLAUNCH(h);
   const SellView<double> A = view<double>(L);
   AMG_TRY(bsmooth(h, k, n, I, U, false, Ta, Tb));                       // U = R I
-  k_bresidual<double><<<nblk(nn), kThreads, 0, st>>>(A, n, U, I, S);   // S = I - A U
+  AMG_TRY(plaunch(h, st, k_bresidual<double>, dim3(nblk(nn)), dim3(kThreads), A, n, U, I, S));   // S = I - A U
   SLAUNCH(h);
-  k_brestrict<double><<<nblk(cn), kThreads, 0, st>>>(nc, n, L.agg_ptr, L.agg_mem, S, RH);
+  AMG_TRY(plaunch(h, st, k_brestrict<double>, dim3(nblk(cn)), dim3(kThreads), nc, n, L.agg_ptr, L.agg_mem, S, RH));
   SLAUNCH(h);
-  k_bdense<<<nblk(cn), kThreads, 0, st>>>(nc, n, h->Z, RH, EH);         // A_H^+ P^T S
+  AMG_TRY(plaunch(h, st, k_bdense, dim3(nblk(cn)), dim3(kThreads), nc, n, h->Z, RH, EH));         // A_H^+ P^T S
   SLAUNCH(h);
-  k_bprolong_residual<double><<<nblk(nn), kThreads, 0, st>>>(A, n, L.agg, EH, U, I, h->Bd, S);
+  AMG_TRY(plaunch(h, st, k_bprolong_residual<double>, dim3(nblk(nn)), dim3(kThreads), A, n, L.agg, EH, U, I, h->Bd, S));
   SLAUNCH(h);
   AMG_TRY(bsmooth(h, k, n, S, h->Bd, true, Ta, Tb));                    // B = U + P.. + R S
   for (double *p : {I, U, S, Ta, Tb, RH, EH}) pool_free(p, st);
@@ -884,10 +948,10 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
 static amg_status precondition(amg_handle_s *h, const double *r, double *z) {
   if (h->opt.precision == AMG_PREC_FP32) {
     const int64_t n = h->n;
-    k_convert<double, float><<<nblk(n), kThreads, 0, h->stream>>>(n, r, h->r32);
+    AMG_TRY(plaunch(h, h->stream, k_convert<double, float>, dim3(nblk(n)), dim3(kThreads), n, r, h->r32));
     SLAUNCH(h);
     AMG_TRY(kcycle<float>(h, 0, h->r32, h->z32));
-    k_convert<float, double><<<nblk(n), kThreads, 0, h->stream>>>(n, h->z32, z);
+    AMG_TRY(plaunch(h, h->stream, k_convert<float, double>, dim3(nblk(n)), dim3(kThreads), n, h->z32, z));
     SLAUNCH(h);
     return AMG_OK;
   }
@@ -945,6 +1009,23 @@ static amg_status run_precondition(amg_handle_s *h) {
   return precondition(h, h->or_, h->oz);
 }
 
+// A grid barrier of the tail kernel gave up waiting: the kernel returned
+// without further writes; clear its flags so the handle stays usable.
+static amg_status tail_timeout(amg_handle_s *h) {
+  cudaMemsetAsync(h->tail_err, 0, sizeof(int) * 4, h->stream);
+  cudaMemsetAsync(h->tail_bar, 0, sizeof(unsigned) * 4, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return fail(AMG_ERR_TIMEOUT, "a bounded barrier wait of the coarse-level kernel ran out");
+}
+
+static amg_status check_tail(amg_handle_s *h) {
+  if (!h->tail_err) return AMG_OK;
+  int e = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&e, h->tail_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return e ? tail_timeout(h) : AMG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // outer flexible CG (Sec. 4: NPCG on the finest level, window cleared every
 // `restart` iterations), fp64
@@ -965,7 +1046,7 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
     sp.b[0] = nullptr;
     sp.nd = 1;
     AMG_TRY(dots<double>(h, n, sp, Fin{FIN_MEAN, 35, (double)n, sc}));
-    k_shift<<<nblk(n), kThreads, 0, st>>>(n, b_dev, h->ob, sc + 35);
+    AMG_TRY(plaunch(h, st, k_shift, dim3(nblk(n)), dim3(kThreads), n, b_dev, h->ob, sc + 35));
     SLAUNCH(h);
   } else {
     AMG_CUDA_TRY(cudaMemcpyAsync(h->ob, b_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -1007,10 +1088,10 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       DotSpec<double> vd{};
       for (int j = 0; j < nwin; ++j) vd.a[j] = h->oD[j];
       vd.nd = nwin;
-      k_axpy_multi<double><<<nblk(n), kThreads, 0, st>>>(n, d, h->oz, vd, sc + 16);
+      AMG_TRY(plaunch(h, st, k_axpy_multi<double>, dim3(nblk(n)), dim3(kThreads), n, d, h->oz, vd, sc + 16));
       SLAUNCH(h);
     }
-    k_spmv<double><<<nblk(n), kThreads, 0, st>>>(A0, d, q);
+    AMG_TRY(plaunch(h, st, k_spmv<double>, dim3(nblk(n)), dim3(kThreads), A0, d, q));
     SLAUNCH(h);
     {
       DotSpec<double> sp{};
@@ -1021,11 +1102,16 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       sp.nd = 2;
       AMG_TRY(dots<double>(h, n, sp, Fin{FIN_OALPHA, nwin, 0.0, sc}));
     }
-    k_outer_update<<<red_grid(n), kThreads, 0, st>>>(n, sc, d, q, x_dev, h->or_, h->red.partial,
-                                                      h->red.ticket, Fin{FIN_STORE, 33, 0.0, sc});
+    AMG_TRY(plaunch(h, st, k_outer_update, dim3(red_grid(n)), dim3(kThreads), n, sc, d, q, x_dev, h->or_, h->red.partial,
+                                                      h->red.ticket, Fin{FIN_STORE, 33, 0.0, sc}));
     SLAUNCH(h);
     AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 33, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    if (h->tail_err) AMG_CUDA_TRY(cudaMemcpyAsync(hp + 4, h->tail_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->tail_err && *reinterpret_cast<int *>(hp + 4)) {
+      status = tail_timeout(h);
+      break;
+    }
     if (h->pre_exec && h->graph_timed) AMG_TRY(timing_accumulate(h, h->graph_events));
     if (hp[1] != 0.0) {
       status = fail(AMG_ERR_BREAKDOWN, "flexible CG breakdown: d^T A d <= 0 or non-finite");
@@ -1044,13 +1130,13 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
     sp.b[0] = nullptr;
     sp.nd = 1;
     AMG_TRY(dots<double>(h, n, sp, Fin{FIN_MEAN, 37, (double)n, sc}));
-    k_shift<<<nblk(n), kThreads, 0, st>>>(n, x_dev, x_dev, sc + 37);
+    AMG_TRY(plaunch(h, st, k_shift, dim3(nblk(n)), dim3(kThreads), n, x_dev, x_dev, sc + 37));
     SLAUNCH(h);
   }
   // true residual ||b - A x|| / ||b||
   double true_rel = 0.0;
   if (nb > 0.0) {
-    k_residual<double><<<nblk(n), kThreads, 0, st>>>(A0, x_dev, h->ob, h->oz);
+    AMG_TRY(plaunch(h, st, k_residual<double>, dim3(nblk(n)), dim3(kThreads), A0, x_dev, h->ob, h->oz));
     SLAUNCH(h);
     DotSpec<double> sp{};
     sp.a[0] = h->oz;
@@ -1090,14 +1176,14 @@ static amg_status run_conv(amg_handle_s *h, const double *in, int64_t nin, doubl
   float *a = nullptr, *b = nullptr;
   AMG_TRY(pool_alloc((void **)&a, sizeof(float) * (size_t)std::max<int64_t>(nin, 1), h->stream));
   AMG_TRY(pool_alloc((void **)&b, sizeof(float) * (size_t)std::max<int64_t>(nout, 1), h->stream));
-  k_convert<double, float><<<nblk(nin), kThreads, 0, h->stream>>>(nin, in, a);
+  AMG_TRY(plaunch(h, h->stream, k_convert<double, float>, dim3(nblk(nin)), dim3(kThreads), nin, in, a));
   SLAUNCH(h);
   if (out_accumulates) {
-    k_convert<double, float><<<nblk(nout), kThreads, 0, h->stream>>>(nout, out, b);
+    AMG_TRY(plaunch(h, h->stream, k_convert<double, float>, dim3(nblk(nout)), dim3(kThreads), nout, out, b));
     SLAUNCH(h);
   }
   AMG_TRY(body((const void *)a, (void *)b));
-  k_convert<float, double><<<nblk(nout), kThreads, 0, h->stream>>>(nout, b, out);
+  AMG_TRY(plaunch(h, h->stream, k_convert<float, double>, dim3(nblk(nout)), dim3(kThreads), nout, b, out));
   SLAUNCH(h);
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
   pool_free(a, h->stream);
@@ -1108,8 +1194,8 @@ static amg_status run_conv(amg_handle_s *h, const double *in, int64_t nin, doubl
 amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y) {
   amg::Level &L = h->lv[k];
   AMG_TRY(run_conv(h, x, L.n, y, L.n, false, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) k_spmv<float><<<nblk(L.n), kThreads, 0, h->stream>>>(view<float>(L), (const float *)a, (float *)b);
-    else k_spmv<double><<<nblk(L.n), kThreads, 0, h->stream>>>(view<double>(L), (const double *)a, (double *)b);
+    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_spmv<float>, dim3(nblk(L.n)), dim3(kThreads), view<float>(L), (const float *)a, (float *)b));
+    else AMG_TRY(plaunch(h, h->stream, k_spmv<double>, dim3(nblk(L.n)), dim3(kThreads), view<double>(L), (const double *)a, (double *)b));
     SLAUNCH(h);
     return AMG_OK;
   }));
@@ -1130,8 +1216,8 @@ amg_status apply_smoother(amg_handle_s *h, int k, const double *r, double *x) {
 amg_status apply_restrict(amg_handle_s *h, int k, const double *s, double *rH) {
   amg::Level &L = h->lv[k];
   AMG_TRY(run_conv(h, s, L.n, rH, L.nH, false, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) k_restrict<float><<<nblk(L.nH), kThreads, 0, h->stream>>>(L.nH, L.agg_ptr, L.agg_mem, (const float *)a, (float *)b);
-    else k_restrict<double><<<nblk(L.nH), kThreads, 0, h->stream>>>(L.nH, L.agg_ptr, L.agg_mem, (const double *)a, (double *)b);
+    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_restrict<float>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const float *)a, (float *)b, nullptr));
+    else AMG_TRY(plaunch(h, h->stream, k_restrict<double>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const double *)a, (double *)b, nullptr));
     SLAUNCH(h);
     return AMG_OK;
   }));
@@ -1142,8 +1228,8 @@ amg_status apply_restrict(amg_handle_s *h, int k, const double *s, double *rH) {
 amg_status apply_prolong_add(amg_handle_s *h, int k, const double *eH, double *x) {
   amg::Level &L = h->lv[k];
   AMG_TRY(run_conv(h, eH, L.nH, x, L.n, true, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) k_prolong_add<float><<<nblk(L.n), kThreads, 0, h->stream>>>(L.n, L.agg, (const float *)a, (float *)b);
-    else k_prolong_add<double><<<nblk(L.n), kThreads, 0, h->stream>>>(L.n, L.agg, (const double *)a, (double *)b);
+    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_prolong_add<float>, dim3(nblk(L.n)), dim3(kThreads), L.n, L.agg, (const float *)a, (float *)b));
+    else AMG_TRY(plaunch(h, h->stream, k_prolong_add<double>, dim3(nblk(L.n)), dim3(kThreads), L.n, L.agg, (const double *)a, (double *)b));
     SLAUNCH(h);
     return AMG_OK;
   }));
@@ -1166,7 +1252,7 @@ amg_status apply_kcycle(amg_handle_s *h, int k, const double *r, double *z) {
     return kcycle<double>(h, k, (const double *)a, (double *)b);
   }));
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return AMG_OK;
+  return check_tail(h);
 }
 
 }  // namespace amg

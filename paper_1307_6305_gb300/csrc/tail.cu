@@ -56,27 +56,77 @@ struct TailParams {
   TailLevel<T> lv[kTailMaxDepth];  // lv[k - k0]
 };
 
+enum TailMode : int { kModeCTA = 0, kModeCluster = 1, kModeGrid = 2 };
+
 struct TailCtx {
   cg::cluster_group cl;
-  bool cluster;   // false: the whole tail runs in one CTA
+  int mode;       // kModeCTA: one CTA; kModeCluster: one cluster; kModeGrid:
+                  // cooperative grid, one CTA per SM, software barrier
   int rank, csize, tid, nthr;
   double *slots;  // shared [2][kTailMaxCTAs][kMaxDots]
   double *wred;   // shared [kTailThreads/32][kMaxDots]
   double *bcast;  // shared [kMaxDots]
   int phase;
+  // grid mode
+  unsigned *bar;        // [0] arrivals, [1] generation
+  double *gpart;        // [2][gridDim][kMaxDots] partial sums
+  int *err;             // set when a barrier wait runs out
+  long long spin_limit; // polls before a barrier wait gives up
+  int test_stall;       // test hook: wait for a generation that never comes
+  bool failed;
 };
 
-// loads of vectors written inside the kernel: in a cluster the CTAs sit on
-// different SMs whose L1 caches are not coherent, so they read L2 directly;
+// loads of vectors written inside the kernel: CTAs on different SMs do not
+// share (coherent) L1 caches, so cluster and grid modes read L2 directly;
 // in single-CTA mode every reader shares one L1, coherent across
 // __syncthreads, and may use it
 template <typename T>
 __device__ __forceinline__ T ld(const TailCtx &c, const T *p) {
-  return c.cluster ? __ldcg(p) : __ldca(p);
+  return c.mode != kModeCTA ? __ldcg(p) : __ldca(p);
+}
+
+// after a failed barrier every row loop is empty and every later barrier a
+// no-op, so all threads run to the end of the kernel without touching memory
+__device__ __forceinline__ void tail_fail(TailCtx &c) {
+  c.failed = true;
+  c.tid = 0x3fffffff;
+}
+
+// grid-wide barrier with a bounded wait (sense by generation counter)
+__device__ __noinline__ void gbar(TailCtx &c) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = c.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned target = g + 1u + (c.test_stall ? 1u : 0u);
+    if (atomicAdd(c.bar, 1u) == gridDim.x - 1u) {
+      atomicExch(c.bar, 0u);
+      __threadfence();
+      atomicAdd(c.bar + 1, 1u);
+    }
+    int ok = 1;
+    long long it = 0;
+    while ((int)(*gen - target) < 0) {
+      if (++it > c.spin_limit || *(volatile int *)c.err) {
+        atomicExch(c.err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  if (!ok_s) tail_fail(c);
 }
 
 __device__ __forceinline__ void csync(TailCtx &c) {
-  if (c.cluster) c.cl.sync();
+  if (c.failed) return;
+  if (c.mode == kModeCluster) c.cl.sync();
+  else if (c.mode == kModeGrid) gbar(c);
   else __syncthreads();
 }
 
@@ -91,7 +141,32 @@ __device__ __noinline__ void csum(TailCtx &c, double (&v)[ND]) {
     if (lane == 0) c.wred[warp * kMaxDots + q] = t;
   }
   __syncthreads();
-  if (!c.cluster) {
+  if (c.failed) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] = 0.0;
+    return;
+  }
+  if (c.mode == kModeGrid) {
+    double *part = c.gpart + (size_t)c.phase * gridDim.x * kMaxDots;
+    if (threadIdx.x < ND) {
+      double t = 0.0;
+      for (int w = 0; w < kTailThreads / 32; ++w) t += c.wred[w * kMaxDots + threadIdx.x];
+      part[blockIdx.x * kMaxDots + threadIdx.x] = t;
+    }
+    csync(c);
+    if (threadIdx.x < ND) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(&part[b * kMaxDots + threadIdx.x]);
+      c.bcast[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] = c.failed ? 0.0 : c.bcast[q];
+    __syncthreads();
+    c.phase ^= 1;
+    return;
+  }
+  if (c.mode == kModeCTA) {
     if (threadIdx.x < ND) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += c.wred[w * kMaxDots + threadIdx.x];
@@ -337,12 +412,21 @@ __device__ void inner_dev(TailCtx &c, const TailParams<T> &P, int k) {
   }
 }
 
-template <typename T, bool CL>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailParams<T> *__restrict__ Pg) {
+struct TailSync {
+  unsigned *bar;
+  double *gpart;
+  int *err;
+  long long spin_limit;
+  int test_stall;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailParams<T> *__restrict__ Pg, TailSync sy) {
   __shared__ double slots[2 * kTailMaxCTAs * kMaxDots];
   __shared__ double wred[(kTailThreads / 32) * kMaxDots];
   __shared__ double bcast[kMaxDots];
   __shared__ TailParams<T> P;
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // predecessor launched with PDL
   // stage the descriptor block in shared memory
   {
     const int words = (int)(sizeof(TailParams<T>) / sizeof(int));
@@ -350,15 +434,19 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailParams<T> *_
     int *dst = reinterpret_cast<int *>(&P);
     for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
   }
-  TailCtx c{cg::this_cluster(), CL, 0, 1, 0, 0, slots, wred, bcast, 0};
-  if (CL) {
+  TailCtx c{cg::this_cluster(), MODE, 0, 1, 0, 0, slots, wred, bcast, 0,
+            sy.bar, sy.gpart, sy.err, sy.spin_limit, sy.test_stall, false};
+  if (MODE == kModeCluster) {
     c.rank = (int)c.cl.block_rank();
     c.csize = (int)c.cl.num_blocks();
+  } else if (MODE == kModeGrid) {
+    c.rank = blockIdx.x;
+    c.csize = gridDim.x;
   }
   c.tid = c.rank * blockDim.x + threadIdx.x;
   c.nthr = c.csize * blockDim.x;
   __syncthreads();
-  csync(c);  // every CTA's shared memory is live before any remote access
+  csync(c);  // every CTA has started before any remote or grid-wide exchange
   inner_dev<T, 0>(c, P, P.k0);
 }
 
@@ -407,56 +495,74 @@ static void fill_params(amg_handle_s *h, TailParams<T> &P) {
 }
 
 template <typename T>
-static amg_status prepare(amg_handle_s *h, bool cluster) {
-  auto kern = k_tail<T, true>;
+static amg_status prepare(amg_handle_s *h, int mode) {
   int csize = 1;
-  if (cluster) AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  for (int want : {16, 8, 4}) {
-    if (!cluster) break;
+  if (mode == kModeCluster) {
+    auto kern = k_tail<T, kModeCluster>;
+    AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     csize = 0;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(want);
-    cfg.blockDim = dim3(kTailThreads);
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = want;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) {
-      csize = want;
-      break;
+    for (int want : {16, 8, 4}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(want);
+      cfg.blockDim = dim3(kTailThreads);
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = want;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) {
+        csize = want;
+        break;
+      }
+      cudaGetLastError();
     }
-    cudaGetLastError();
+    if (!csize) return fail(AMG_ERR_CUDA, "no thread-block cluster size is schedulable for the tail kernel");
+  } else if (mode == kModeGrid) {
+    int sms = 0, per = 0;
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tail<T, kModeGrid>, kTailThreads, 0));
+    if (per < 1) return fail(AMG_ERR_CUDA, "the grid tail kernel does not fit on an SM");
+    csize = sms;  // one CTA per SM: all co-resident, as a grid barrier needs
   }
-  if (!csize) return fail(AMG_ERR_CUDA, "no thread-block cluster size is schedulable for the tail kernel");
   h->tail_csize = csize;
-  h->tail_cluster = cluster;
+  h->tail_mode = mode;
   TailParams<T> P;
   fill_params(h, P);
   AMG_TRY(h->arena.alloc(&h->tail_params, sizeof(P)));
+  AMG_TRY(h->arena.alloc((void **)&h->tail_bar, sizeof(unsigned) * 4));
+  AMG_TRY(h->arena.alloc((void **)&h->tail_err, sizeof(int) * 4));
+  AMG_TRY(h->arena.alloc((void **)&h->tail_gpart, sizeof(double) * 2 * (size_t)csize * kMaxDots));
+  AMG_CUDA_TRY(cudaMemsetAsync(h->tail_bar, 0, sizeof(unsigned) * 4, h->stream));
+  AMG_CUDA_TRY(cudaMemsetAsync(h->tail_err, 0, sizeof(int) * 4, h->stream));
   AMG_CUDA_TRY(cudaMemcpyAsync(h->tail_params, &P, sizeof(P), cudaMemcpyHostToDevice, h->stream));
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
   return AMG_OK;
 }
 
-// choose k0: the first level >= 1 with at most `max_rows` rows whose levels
-// down to the coarsest fit the compile-time depth; -1 disables the tail.
-// fp32 cycles run the tail in one CTA from the first level of at most 2048
-// rows: there one SM's fp32 rate and L1 hold the level's work and its
-// barrier is an order of magnitude cheaper than a cluster's (a level of
-// several thousand rows would stream its matrix through one SM's L2 port at
-// every phase).  fp64 (2 DFMA/clk per SM on this GPU) keeps the multi-kernel
-// path unless AMG_GB300_TAIL_ROWS asks for the cluster variant.
+// Choose k0, the first level >= 1 with at most `max_rows` rows (levels down
+// to the coarsest must fit the compile-time depth); -1 keeps every level on
+// the multi-kernel path.  Off by default: on GB300 with the 128^3 workload
+// every mode measured slower than the graph-replayed kernels (fp64 solve
+// 56 ms without the tail, 88 ms with the grid mode from 8192 rows; fp32 42
+// vs 77 ms) -- each in-kernel phase still costs several microseconds of
+// dependent memory latency, and a single SM's 2 DFMA/clk starves the one-CTA
+// and cluster modes in fp64.  AMG_GB300_TAIL_ROWS=<rows> enables it and
+// AMG_GB300_TAIL_MODE selects grid (default) / cluster / cta.
 amg_status prepare_tail(amg_handle_s *h) {
   h->tail_k0 = -1;
   const bool f32 = h->opt.precision == AMG_PREC_FP32;
-  int max_rows = f32 ? 2048 : 0;
-  const char *env = getenv("AMG_GB300_TAIL_ROWS");
-  if (env) max_rows = atoi(env);
-  const bool cluster = !f32;
+  int max_rows = 0;
+  int mode = kModeGrid;
+  if (const char *env = getenv("AMG_GB300_TAIL_ROWS")) max_rows = atoi(env);
+  if (const char *env = getenv("AMG_GB300_TAIL_MODE")) {
+    if (!strcmp(env, "cta")) mode = kModeCTA;
+    else if (!strcmp(env, "cluster")) mode = kModeCluster;
+  }
+  h->tail_test_stall = 0;
+  if (const char *env = getenv("AMG_GB300_TAIL_TEST_STALL")) h->tail_test_stall = atoi(env);
   if (max_rows <= 0 || h->L < 3) return AMG_OK;
   int k0 = -1;
   for (int k = 1; k + 1 < h->L; ++k)
@@ -466,15 +572,24 @@ amg_status prepare_tail(amg_handle_s *h) {
     }
   if (k0 < 0 || h->L - k0 > kTailMaxDepth) return AMG_OK;
   h->tail_k0 = k0;
-  amg_status s = f32 ? prepare<float>(h, cluster) : prepare<double>(h, cluster);
+  amg_status s = f32 ? prepare<float>(h, mode) : prepare<double>(h, mode);
   if (s != AMG_OK) h->tail_k0 = -1;
   return s;
 }
 
 template <typename T>
 static amg_status launch(amg_handle_s *h) {
-  if (!h->tail_cluster) {
-    k_tail<T, false><<<1, kTailThreads, 0, h->stream>>>((const TailParams<T> *)h->tail_params);
+  TailSync sy;
+  sy.bar = h->tail_bar;
+  sy.gpart = h->tail_gpart;
+  sy.err = h->tail_err;
+  // about 2^26 polls of >= 64 ns: seconds, far beyond any real wait; the
+  // test hook uses a few thousand polls
+  sy.spin_limit = h->tail_test_stall ? 4096 : (1LL << 26);
+  sy.test_stall = h->tail_test_stall;
+  const TailParams<T> *P = (const TailParams<T> *)h->tail_params;
+  if (h->tail_mode == kModeCTA) {
+    k_tail<T, kModeCTA><<<1, kTailThreads, 0, h->stream>>>(P, sy);
     ++h->launches;
     AMG_CUDA_TRY(cudaGetLastError());
     return AMG_OK;
@@ -484,13 +599,19 @@ static amg_status launch(amg_handle_s *h) {
   cfg.gridDim = dim3(h->tail_csize);
   cfg.blockDim = dim3(kTailThreads);
   cfg.stream = h->stream;
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = h->tail_csize;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tail<T, true>, (const TailParams<T> *)h->tail_params));
+  if (h->tail_mode == kModeCluster) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = h->tail_csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tail<T, kModeCluster>, P, sy));
+  } else {
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tail<T, kModeGrid>, P, sy));
+  }
   ++h->launches;
   return AMG_OK;
 }

@@ -9,9 +9,13 @@
   within a few of the fp64 method's.
 * fp32 K-cycle applications agree with the fp64 oracle to single-precision
   accuracy (1e-4 relative to the result's max norm).
-* The tail kernel (single CTA for fp32 by default; the 16-CTA cluster variant
-  forced for fp64) reproduces the multi-kernel path: fp64 results stay within
-  the fp64 parity bar.
+* The coarse-level tail kernel, in each of its modes (cooperative grid with
+  a bounded software barrier, the default; one 16-CTA cluster; one CTA),
+  reproduces the multi-kernel path: fp64 results stay within the fp64
+  parity bar.
+* A tail barrier whose wait runs out (test hook: it waits for a generation
+  that never comes) ends the kernel without hanging and the solve reports
+  AMG_ERR_TIMEOUT; the device stays usable for the next handle.
 """
 import os
 
@@ -49,19 +53,26 @@ def resid_gap(orc, g, opts, x, xref):
     return np.linalg.norm(sparse_laplacian(g) @ (x - xref))
 
 
-def with_tail(rows, fn):
-    old = os.environ.get("AMG_GB300_TAIL_ROWS")
-    if rows is None:
-        os.environ.pop("AMG_GB300_TAIL_ROWS", None)
-    else:
-        os.environ["AMG_GB300_TAIL_ROWS"] = str(rows)
+def with_env(env, fn):
+    """Run fn with the given environment variables set (None: unset)."""
+    old = {k: os.environ.get(k) for k in env}
+    for k, v in env.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = str(v)
     try:
         return fn()
     finally:
-        if old is None:
-            os.environ.pop("AMG_GB300_TAIL_ROWS", None)
-        else:
-            os.environ["AMG_GB300_TAIL_ROWS"] = old
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def with_tail(rows, fn, mode=None):
+    return with_env({"AMG_GB300_TAIL_ROWS": rows, "AMG_GB300_TAIL_MODE": mode}, fn)
 
 
 GRAPHS = {
@@ -110,11 +121,12 @@ def test_fp32_kcycle_single_precision_accuracy(amg, orc, name):
             assert rel(out.cpu().numpy(), oh.smooth(k, v)) < 1e-5
 
 
+@pytest.mark.parametrize("mode", ["grid", "cluster", "cta"])
 @pytest.mark.parametrize("name", ["grid3d_24_d", "rdiag_96", "rgg_8000"])
-def test_fp64_cluster_tail_matches_oracle(amg, orc, name):
+def test_fp64_tail_modes_match_oracle(amg, orc, name, mode):
     make, opts = GRAPHS[name]
     g = make()
-    gh = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts))
+    gh = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts), mode)
     oh = orc.Hierarchy(g, **opts)
     assert gh.status == 0 and gh.n_levels == oh.n_levels
     for k in range(oh.n_levels):
@@ -133,10 +145,11 @@ def test_fp64_cluster_tail_matches_oracle(amg, orc, name):
     assert rel(xd.cpu().numpy(), ref.x) < 1e-7
 
 
-def test_fp32_tail_matches_fp32_multikernel_path(amg):
+@pytest.mark.parametrize("mode", ["grid", "cluster", "cta"])
+def test_fp32_tail_matches_fp32_multikernel_path(amg, mode):
     g = gg.grid3d_7pt(28, 1.0)
     opts = dict(degree=5, passes=3, precision=amg.AMG_PREC_FP32)
-    a = with_tail(None, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts))
+    a = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts), mode)
     b = with_tail(0, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts))
     v = cuda(gg.uniform_pm1(3, g.n))
     oa = torch.zeros_like(v)
@@ -174,3 +187,20 @@ def test_full_size_rdiag_2048_fp32(amg, orc):
           f"fp32-precond {it32} it, rel err {e32:.2e}, ||A(x-x_orc)||/||b|| {g32:.2e}, true res {t32:.2e}")
     assert abs(it64 - ref.iterations) <= 1 and e64 < 1e-7
     assert it32 <= it64 + 3 and g32 <= 2.1e-8
+
+
+def test_tail_barrier_timeout_is_reported(amg):
+    g = gg.grid3d_7pt(24, 1.0)
+    opts = dict(degree=5, passes=3)
+    bad = with_env({"AMG_GB300_TAIL_ROWS": 1 << 20, "AMG_GB300_TAIL_MODE": "grid", "AMG_GB300_TAIL_TEST_STALL": 1},
+                   lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts))
+    assert bad.status == 0
+    b = cuda(gg.rhs(g.n, 5, False))
+    x = torch.zeros_like(b)
+    st, info, hist = bad.solve(b, x, tol=1e-8)
+    assert st == amg.AMG_ERR_TIMEOUT
+    assert "ran out" in amg.amg_last_error(bad.h)
+    bad.close()
+    good = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts), "grid")
+    st, info, hist = good.solve(b, x, tol=1e-8)
+    assert st == amg.AMG_OK and hist[-1] <= 1e-8
