@@ -34,9 +34,12 @@ sys.path.insert(0, ROOT)
 
 import graphgen as gg  # noqa: E402
 
-WORKLOAD = "grid3d_128"
-WORKLOAD_DESC = ("128^3 7-point graph Laplacian, w=1, d=1 on boundary faces; degree-5 polynomial "
-                 "smoother, 3 matching passes/level, K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64)")
+WORKLOADS = {
+    "grid3d_128": ("128^3 7-point graph Laplacian, w=1, d=1 on boundary faces; degree-5 polynomial "
+                   "smoother, 3 matching passes/level, K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64)"),
+    "grid3d_96x32": ("96^3 7-point graph Laplacian, d=1 on boundary faces, 32 right-hand sides solved in one "
+                     "batched call; degree-5 smoother, 3 passes/level, fp32 preconditioner / fp64 FCG, tol 1e-8"),
+}
 METRIC = "DOF/s solved to 1e-8 rel. residual (setup + solve per step)"
 UNIT = "DOF/s"
 L2_BYTES = 129 * 2 ** 20
@@ -132,15 +135,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_oracle_step(g, p, b):
+def run_oracle_step(g, p, b, ncols=None):
+    """Oracle setup + solve of the first `ncols` right-hand sides (all by default)."""
     import oracle
 
+    nr = b.size // g.n
+    ncols = nr if ncols is None else min(ncols, nr)
     t0 = time.perf_counter()
     h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"])
-    r = h.solve(b, tol=1e-8)
+    for j in range(ncols):
+        r = h.solve(b[j * g.n:(j + 1) * g.n], tol=1e-8)
+        assert r.status == 0, r.status
     dt = time.perf_counter() - t0
-    assert h.status == 0 and r.status == 0, (h.status, r.status)
-    return dt, r
+    assert h.status == 0
+    return dt, r, ncols
 
 
 def main():
@@ -152,27 +160,33 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-variant", action="store_true", help="skip the fp32-preconditioner variant")
+    ap.add_argument("--workload", default="grid3d_128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32: the whole preconditioner in fp32 inside the fp64 outer CG")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOADS[args.workload]
     g, p = gg.workload(WORKLOAD)
-    b = gg.rhs(g.n, p["rhs_seeds"][0], gg.is_pure_laplacian(g))
+    nrhs = len(p["rhs_seeds"])
+    if nrhs > 1:
+        args.precision = "fp32" if p["precision"] else args.precision
+    b = np.concatenate([gg.rhs(g.n, sd, gg.is_pure_laplacian(g)) for sd in p["rhs_seeds"]])
 
     if args.impl == "reference":
         if rank != 0:
             return 0
+        ncols = 1 if nrhs == 1 else 2          # bounded sample: two of the 32 columns
         for _ in range(args.warmup):
-            run_oracle_step(g, p, b)
-        times = [run_oracle_step(g, p, b)[0] for _ in range(args.steps)]
+            run_oracle_step(g, p, b, ncols)
+        times = [run_oracle_step(g, p, b, ncols)[0] for _ in range(args.steps)]
         ms = 1e3 * sum(times) / len(times)
-        value = g.n / (ms / 1e3)
+        value = g.n * ncols / (ms / 1e3)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": 1},
+                "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": nrhs},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": "full workload per step (oracle setup + solve), single thread"},
+                                 "sample": f"oracle setup + {ncols} of {nrhs} right-hand sides per step, single thread"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -193,7 +207,7 @@ def main():
     col = torch.as_tensor(g.col, device=dev)
     w = torch.as_tensor(g.w, device=dev)
     d = None if g.d is None else torch.as_tensor(g.d, device=dev)
-    bd = torch.as_tensor(b, device=dev)
+    bd = torch.as_tensor(b, device=dev)          # column j at bd[j*n:(j+1)*n]
     xd = torch.zeros_like(bd)
     in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + b.nbytes
     prec = amg.AMG_PREC_FP32 if args.precision == "fp32" else amg.AMG_PREC_FP64
@@ -207,7 +221,7 @@ def main():
         if timed_kernel:
             amg.lib().amg_kernel_timing(h, 1)
         info = amg.amg_info()
-        st = amg.amg_solve(h, bd, xd, 1, g.n, 1e-8, info)
+        st = amg.amg_solve(h, bd, xd, nrhs, g.n, 1e-8, info)
         assert st == 0, amg.amg_last_error(h)
         launches += amg.lib().amg_launch_count(h)
         if timed_kernel:
@@ -252,11 +266,11 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = g.n * world / (ms / 1e3)
+    value = g.n * nrhs * world / (ms / 1e3)
 
     # the fp32-preconditioner form on the same workload (the metric compares both)
     variant = None
-    if args.precision == "fp64" and not args.no_variant:
+    if args.precision == "fp64" and nrhs == 1 and not args.no_variant:
         opts32 = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=amg.AMG_PREC_FP32)
         its = []
 
@@ -264,7 +278,7 @@ def main():
             st, h = amg.amg_setup(g.n, rp, col, w, d, opts32, amg.AMG_MEM_DEVICE, sp)
             assert st == 0
             info = amg.amg_info()
-            assert amg.amg_solve(h, bd, xd, 1, g.n, 1e-8, info) == 0
+            assert amg.amg_solve(h, bd, xd, nrhs, g.n, 1e-8, info) == 0
             its.append(info.iterations)
             amg.amg_free(h)
 
@@ -277,7 +291,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms32 = e0.elapsed_time(e1) / args.steps
-        variant = {"fp32_precond": {"value": g.n * world / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+        variant = {"fp32_precond": {"value": g.n * nrhs * world / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
                                     "iterations": its[-1],
                                     "dtype": "f32 preconditioner / f64 outer CG, dots and coarsest solve"}}
 
@@ -295,7 +309,7 @@ def main():
     for _ in range(e2e_steps):
         st, h = amg.amg_setup(g.n, hrp, hcol, hw, hd, opts, amg.AMG_MEM_HOST, sp)
         assert st == 0
-        st = amg.amg_solve(h, hb, hx, 1, g.n, 1e-8, None)
+        st = amg.amg_solve(h, hb, hx, nrhs, g.n, 1e-8, None)
         assert st == 0
         amg.amg_free(h)
     torch.cuda.synchronize()
@@ -331,20 +345,21 @@ def main():
                  "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": flops})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        dt, r = run_oracle_step(g, p, b)
-        cpu = {"value": g.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"full workload once (setup + solve, {r.iterations} iterations), {dt:.1f} s single thread"}
+        dt, r, nc = run_oracle_step(g, p, b, 1 if nrhs == 1 else 2)
+        cpu = {"value": g.n * nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle setup + {nc} of {nrhs} right-hand sides ({r.iterations} iterations), "
+                         f"{dt:.1f} s single thread"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 preconditioner / f64 outer",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": 1, "nnz_offdiag": g.nnz,
+        "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": nrhs, "nnz_offdiag": g.nnz,
                    "l2": f"inputs {in_bytes / 2**20:.0f} MiB > 129 MiB L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "iterations": state["iters"][-1], "setup_ms_host": statistics.median(state["setup_ms"]),
         "solve_ms_host": statistics.median(state["solve_ms"]),
-        "e2e": {"value": g.n * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+        "e2e": {"value": g.n * nrhs * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": b.nbytes, "ms_per_step": e2e_ms},
         "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": ck,
         "variants": variant,

@@ -129,6 +129,8 @@ void destroy(amg_handle_s *h) {
   cudaStreamSynchronize(h->stream);
   h->arena.release();
   if (h->pre_exec) cudaGraphExecDestroy(h->pre_exec);
+  if (h->bpre_exec) cudaGraphExecDestroy(h->bpre_exec);
+  if (h->b_pinned) cudaFreeHost(h->b_pinned);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -249,6 +251,51 @@ amg_status amg_solve(amg_handle h, const double *rhs, double *x, int nrhs, int64
   const int64_t n = h->n;
   double *bstage = nullptr, *xstage = nullptr;
   amg_status s = AMG_OK;
+  const char *benv = getenv("AMG_GB300_BATCHED");
+  if (nrhs >= 2 && !(benv && benv[0] == '0')) {
+    // all right-hand sides together (block kernels, per-column scalars)
+    const double *bd = rhs;
+    double *xd = x;
+    const size_t bytes = sizeof(double) * (size_t)ld * (size_t)nrhs;
+    if (!rdev) s = pool_alloc((void **)&bstage, bytes, h->stream);
+    if (!s && !xdev) s = pool_alloc((void **)&xstage, bytes, h->stream);
+    if (!s && !rdev) {
+      if (cudaMemcpyAsync(bstage, rhs, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        s = fail(AMG_ERR_CUDA, "copy of the right-hand sides");
+      bd = bstage;
+    }
+    if (!xdev) xd = xstage;
+    int it = 0, conv = 0;
+    double rel = 0.0, tr = 0.0;
+    bool brk = false;
+    if (!s) s = solve_batched(h, bd, xd, nrhs, ld, tol, info, &it, &rel, &tr, &conv, &brk);
+    if (!s && !xdev) {
+      if (cudaMemcpyAsync(x, xstage, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        s = fail(AMG_ERR_CUDA, "copy of the solutions");
+    }
+    pool_free(bstage, h->stream);
+    pool_free(xstage, h->stream);
+    if (!s) {
+      cudaError_t e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) s = fail(AMG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+    }
+    if (info) {
+      info->iterations = it;
+      info->converged = conv;
+      info->rel_residual = rel;
+      info->true_rel_residual = tr;
+      info->n_levels = h->L;
+      info->grid_complexity = h->grid_complexity;
+      info->op_complexity = h->op_complexity;
+      info->setup_ms = h->setup_ms;
+      info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (s) return record(h, s);
+    if (brk) return record(h, fail(AMG_ERR_BREAKDOWN, "flexible CG breakdown in at least one column"));
+    if (!conv) return record(h, fail(AMG_ERR_NOT_CONVERGED, "max_iters reached before tol"));
+    return AMG_OK;
+  }
   if (!rdev) s = pool_alloc((void **)&bstage, sizeof(double) * (size_t)n, h->stream);
   if (!s && !xdev) s = pool_alloc((void **)&xstage, sizeof(double) * (size_t)n, h->stream);
   int max_it = 0, all_conv = 1;

@@ -131,6 +131,15 @@ struct Level {
   void *D[kMaxInner] = {}, *W[kMaxInner] = {};
 };
 
+// per-level buffers of the batched (multi right-hand side) path: blocks of
+// up to 32 columns, row major
+struct BatchLevel {
+  double *scal = nullptr;  // [48][32] per-column scalars
+  void *u = nullptr, *s = nullptr, *Ta = nullptr, *Tb = nullptr;
+  void *b = nullptr, *x = nullptr, *r = nullptr;
+  void *D[kMaxInner] = {}, *W[kMaxInner] = {};
+};
+
 // fused reduction state (deterministic two-stage: per-block partials, last
 // block folds them in block order)
 struct RedState {
@@ -181,6 +190,22 @@ struct amg_handle_s {
   double *bb64 = nullptr, *bx64 = nullptr;
   // levels >= tail_k0 run as one persistent cluster kernel per inner solve
   int tail_k0 = -1;
+  // batched path (batch.cu)
+  int bw = 0;                        // allocated block width (0: not yet)
+  int bw_use = 32;                   // block width in use
+  int b_tile = 256;                  // threads per CTA of the block SpMM kernels
+  int tuned_for = 0;
+  std::string tune_log;
+  std::vector<amg::BatchLevel> blv;
+  double *bo_b = nullptr, *bo_x = nullptr, *bo_r = nullptr, *bo_z = nullptr, *bo_t = nullptr;
+  double *boD[amg::kMaxWindow] = {}, *boQ[amg::kMaxWindow] = {};
+  double *bo_scal = nullptr;
+  void *b_r32 = nullptr, *b_z32 = nullptr;
+  double *b_partial = nullptr;
+  unsigned *b_ticket = nullptr;
+  double *b_pinned = nullptr;
+  cudaGraphExec_t bpre_exec = nullptr;
+  int64_t bgraph_kernels = 0;
   int tail_csize = 0;
   int tail_mode = 0;
   int tail_test_stall = 0;
@@ -215,6 +240,9 @@ amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32
 // solve.cu
 amg_status allocate_solve_buffers(amg_handle_s *h);
 amg_status build_dense_two_level(amg_handle_s *h);
+// batch.cu
+amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs, int64_t ld, double tol,
+                         amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown);
 // tail.cu
 amg_status prepare_tail(amg_handle_s *h);
 amg_status launch_tail(amg_handle_s *h);
