@@ -39,7 +39,82 @@ WORKLOADS = {
                    "smoother, 3 matching passes/level, K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64)"),
     "grid3d_96x32": ("96^3 7-point graph Laplacian, d=1 on boundary faces, 32 right-hand sides solved in one "
                      "batched call; degree-5 smoother, 3 passes/level, fp32 preconditioner / fp64 FCG, tol 1e-8"),
+    "serve": ("continuous-batching server: pool of 16 graphs (8 random geometric, 4 2D and 4 3D grids), sizes "
+              "log-uniform in [1e4, 1e6], resident hierarchies, 8 slots, 60 GB cap, Poisson arrivals; "
+              "degree-4 smoother, 3 passes, fp32 preconditioner / fp64 FCG, tol 1e-8"),
 }
+
+
+def serve_bench(args):
+    """Solves/s and p50/p99 latency of the server under Poisson arrivals at
+    1.2x and 0.5x of its saturated throughput."""
+    import torch
+
+    import paper_1307_6305_gb300 as amg
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5)
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e6), 16))
+    graphs = []
+    for i, sz in enumerate(sizes):
+        if i < 8:
+            graphs.append(gg.random_geometric(int(sz), 500 + i))
+        elif i < 12:
+            graphs.append(gg.grid2d_5pt(int(round(np.sqrt(sz)))))
+        else:
+            graphs.append(gg.grid3d_7pt(int(round(sz ** (1.0 / 3.0))), None))
+    rhs = [[gg.rhs(g.n, 7000 + 10 * gi + j, True) for j in range(4)] for gi, g in enumerate(graphs)]
+    srv = amg.Server(60 << 30, 8, degree=4, passes=3, precision=amg.AMG_PREC_FP32)
+    ids = [srv.add_graph(g) for g in graphs]
+    for gi in range(len(graphs)):                      # hierarchies become resident
+        st, _, _, _ = srv.wait(srv.submit(ids[gi], rhs[gi][0]))
+        assert st == 0
+    def pick():
+        gi = int(rng.integers(len(graphs)))
+        return gi, rhs[gi][int(rng.integers(4))]
+    # saturated throughput: everything queued at once
+    burst = [pick() for _ in range(256)]
+    t0 = time.perf_counter()
+    tickets = [srv.submit(ids[gi], b) for gi, b in burst]
+    for t in tickets:
+        assert srv.wait(t)[0] == 0
+    sat = len(burst) / (time.perf_counter() - t0)
+    runs = []
+    for load, count in ((1.2, 2000), (0.5, 600)):
+        rate = load * sat
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+        reqs = [pick() for _ in range(count)]
+        tickets = []
+        t0 = time.perf_counter()
+        for (gi, b), ta in zip(reqs, arrivals):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(ids[gi], b))
+        lat, iters = [], []
+        for t in tickets:
+            st, x, info, ms = srv.wait(t)
+            assert st == 0
+            lat.append(ms)
+            iters.append(info.iterations)
+        wall = time.perf_counter() - t0
+        runs.append({"offered_load": load, "requests": count, "solves_per_s": count / wall,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_iterations": float(np.mean(iters))})
+    stats = srv.stats()
+    srv.close()
+    main = runs[0]
+    line = {"metric": "solves/s under Poisson arrivals at 1.2x saturated throughput (p50/p99 latency)",
+            "value": main["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": main["requests"],
+            "warmup": len(graphs), "ms_per_step": 1e3 / main["solves_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 outer", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serve"], "graphs": [int(g.n) for g in graphs]},
+            "saturated_solves_per_s": sat, "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
+            "runs": runs, "server": {"peak_active": stats.peak_active, "setups": int(stats.setups),
+                                      "evictions": int(stats.evictions),
+                                      "peak_resident_gb": stats.peak_resident_bytes / 2 ** 30}}
+    print(json.dumps(line), flush=True)
+    return 0
 METRIC = "DOF/s solved to 1e-8 rel. residual (setup + solve per step)"
 UNIT = "DOF/s"
 L2_BYTES = 129 * 2 ** 20
@@ -165,6 +240,8 @@ def main():
                     help="fp32: the whole preconditioner in fp32 inside the fp64 outer CG")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.workload == "serve":
+        return serve_bench(args) if args.impl == "ours" and rank == 0 else 0
     WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOADS[args.workload]
     g, p = gg.workload(WORKLOAD)
     nrhs = len(p["rhs_seeds"])

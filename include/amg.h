@@ -226,6 +226,51 @@ amg_status amg_match_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *c
                              int64_t *n_coarse, int *rounds, void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving (not in the paper: a request loop around amg_setup/amg_solve).  */
+/*                                                                        */
+/* Continuous batching on one GPU: registered graphs keep their hierarchy */
+/* resident; solve requests are admitted as soon as one of `max_active`   */
+/* slots and device memory under `mem_cap_bytes` are free (idle           */
+/* hierarchies are evicted least-recently-used first); solves of          */
+/* different graphs run concurrently on their own streams, requests for   */
+/* one graph take turns.  Results are bit-identical to solving alone.     */
+/* All pointers are host memory; the server copies what it needs.         */
+/* ---------------------------------------------------------------------- */
+
+typedef struct amg_server_s *amg_server;
+
+typedef struct {
+  size_t mem_cap_bytes;  /* device bytes for resident hierarchies (>= 1 MiB) */
+  int max_active;        /* concurrent solves, 1..64                         */
+  amg_options opt;       /* solver options of every request                  */
+} amg_server_config;
+
+typedef struct {
+  size_t resident_bytes, peak_resident_bytes;
+  int active, peak_active;
+  int64_t queued, completed, setups, evictions;
+} amg_server_stats_t;
+
+amg_status amg_server_create(const amg_server_config *cfg, amg_server *out);
+/* register a graph (arguments as amg_setup with host memory); the hierarchy
+ * is built by the first request that needs it */
+amg_status amg_server_add_graph(amg_server s, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                const double *w, const double *d, int64_t *graph_id);
+/* queue one right-hand side (n doubles) for graph_id; *ticket identifies it */
+amg_status amg_server_submit(amg_server s, int64_t graph_id, const double *rhs, double tol, int64_t *ticket);
+/* *done = 0 while the request runs; once done, copies the solution into x
+ * (n doubles, may be NULL), the report into info (history not filled), the
+ * submit-to-finish latency into *latency_ms, releases the ticket and returns
+ * the solve's status */
+amg_status amg_server_poll(amg_server s, int64_t ticket, double *x, amg_info *info, int *done,
+                           double *latency_ms);
+/* as amg_server_poll, blocking until the request is done */
+amg_status amg_server_wait(amg_server s, int64_t ticket, double *x, amg_info *info, double *latency_ms);
+amg_status amg_server_stats(amg_server s, amg_server_stats_t *out);
+/* stops the workers after their current solves and frees every hierarchy */
+void amg_server_destroy(amg_server s);
+
+/* ---------------------------------------------------------------------- */
 /* Measurement hooks.                                                      */
 /* ---------------------------------------------------------------------- */
 

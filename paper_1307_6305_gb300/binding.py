@@ -40,6 +40,8 @@ SYMBOLS = [
     "amg_level_smoother", "amg_apply_spmv", "amg_apply_smoother", "amg_apply_restrict",
     "amg_apply_prolong_add", "amg_apply_coarse_solve", "amg_apply_kcycle", "amg_match", "amg_match_noalloc",
     "amg_kernel_timing", "amg_kernel_timing_read", "amg_launch_count",
+    "amg_server_create", "amg_server_add_graph", "amg_server_submit", "amg_server_poll", "amg_server_wait",
+    "amg_server_stats", "amg_server_destroy",
 ]
 
 
@@ -56,6 +58,16 @@ class amg_info(C.Structure):
                 ("grid_complexity", C.c_double), ("op_complexity", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double),
                 ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int), ("history_len", C.c_int)]
+
+
+class amg_server_config(C.Structure):
+    _fields_ = [("mem_cap_bytes", C.c_size_t), ("max_active", C.c_int), ("opt", amg_options)]
+
+
+class amg_server_stats_t(C.Structure):
+    _fields_ = [("resident_bytes", C.c_size_t), ("peak_resident_bytes", C.c_size_t), ("active", C.c_int),
+                ("peak_active", C.c_int), ("queued", C.c_int64), ("completed", C.c_int64),
+                ("setups", C.c_int64), ("evictions", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -102,6 +114,14 @@ def lib(build_if_missing: bool = True):
             L.amg_kernel_timing_read.argtypes = [P, C.POINTER(I64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.amg_launch_count.argtypes = [P]
             L.amg_launch_count.restype = I64
+            L.amg_server_create.argtypes = [C.POINTER(amg_server_config), C.POINTER(C.c_void_p)]
+            L.amg_server_add_graph.argtypes = [P, I64, P, P, P, P, C.POINTER(I64)]
+            L.amg_server_submit.argtypes = [P, I64, P, C.c_double, C.POINTER(I64)]
+            L.amg_server_poll.argtypes = [P, I64, P, C.POINTER(amg_info), C.POINTER(I), C.POINTER(C.c_double)]
+            L.amg_server_wait.argtypes = [P, I64, P, C.POINTER(amg_info), C.POINTER(C.c_double)]
+            L.amg_server_stats.argtypes = [P, C.POINTER(amg_server_stats_t)]
+            L.amg_server_destroy.argtypes = [P]
+            L.amg_server_destroy.restype = None
             _lib = L
     return _lib
 
@@ -271,3 +291,64 @@ class Hierarchy:
 
     def launch_count(self) -> int:
         return lib().amg_launch_count(self.h)
+
+
+class Server:
+    """Continuous-batching solve server (amg_server_* of the C ABI)."""
+
+    def __init__(self, mem_cap_bytes: int, max_active: int, **opts):
+        cfg = amg_server_config()
+        cfg.mem_cap_bytes = int(mem_cap_bytes)
+        cfg.max_active = int(max_active)
+        cfg.opt = amg_default_options(**opts)
+        h = C.c_void_p()
+        self.status = lib().amg_server_create(C.byref(cfg), C.byref(h))
+        if self.status != AMG_OK:
+            raise AmgError(self.status, amg_last_error(None))
+        self.h = h
+        self._n = {}
+
+    def add_graph(self, g) -> int:
+        rp = np.ascontiguousarray(g.rowptr, np.int64)
+        col = np.ascontiguousarray(g.col, np.int32)
+        w = np.ascontiguousarray(g.w, np.float64)
+        d = None if g.d is None else np.ascontiguousarray(g.d, np.float64)
+        gid = C.c_int64()
+        st = lib().amg_server_add_graph(self.h, g.n, ptr(rp), ptr(col), ptr(w), ptr(d), C.byref(gid))
+        if st != AMG_OK:
+            raise AmgError(st, amg_last_error(None))
+        self._n[gid.value] = g.n
+        return gid.value
+
+    def submit(self, graph_id: int, rhs: np.ndarray, tol: float = 1e-8) -> int:
+        rhs = np.ascontiguousarray(rhs, np.float64)
+        t = C.c_int64()
+        st = lib().amg_server_submit(self.h, graph_id, ptr(rhs), tol, C.byref(t))
+        if st != AMG_OK:
+            raise AmgError(st, amg_last_error(None))
+        self._n[("t", t.value)] = self._n[graph_id]
+        return t.value
+
+    def wait(self, ticket: int):
+        """(status, x, info, latency_ms)"""
+        x = np.zeros(self._n.pop(("t", ticket)))
+        info = amg_info()
+        lat = C.c_double()
+        st = lib().amg_server_wait(self.h, ticket, ptr(x), C.byref(info), C.byref(lat))
+        return st, x, info, lat.value
+
+    def stats(self) -> amg_server_stats_t:
+        s = amg_server_stats_t()
+        lib().amg_server_stats(self.h, C.byref(s))
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().amg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

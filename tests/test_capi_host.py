@@ -73,3 +73,22 @@ def test_no_device_is_reported(amg):
     st, h = amg.amg_setup(g.n, g.rowptr, g.col, g.w)
     assert st == amg.AMG_ERR_CUDA and not h.value
     assert "device" in amg.amg_last_error(None)
+
+
+def test_server_argument_errors(amg):
+    import ctypes as C
+
+    cfg = amg.amg_server_config()
+    cfg.mem_cap_bytes = 1 << 30
+    cfg.max_active = 0
+    cfg.opt = amg.amg_default_options()
+    h = C.c_void_p()
+    assert amg.lib().amg_server_create(C.byref(cfg), C.byref(h)) == amg.AMG_ERR_INVALID_ARG
+    cfg.max_active = 2
+    cfg.mem_cap_bytes = 10
+    assert amg.lib().amg_server_create(C.byref(cfg), C.byref(h)) == amg.AMG_ERR_INVALID_ARG
+    import torch
+
+    if not torch.cuda.is_available():
+        cfg.mem_cap_bytes = 1 << 30
+        assert amg.lib().amg_server_create(C.byref(cfg), C.byref(h)) == amg.AMG_ERR_CUDA
