@@ -234,6 +234,9 @@ amg_status amg_match_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *c
 /* hierarchies are evicted least-recently-used first); solves of          */
 /* different graphs run concurrently on their own streams, requests for   */
 /* one graph take turns.  Results are bit-identical to solving alone.     */
+/* A hierarchy's size is its arena bytes, measured at its first setup     */
+/* (estimated from n and nnz before that); a request whose hierarchy      */
+/* alone exceeds mem_cap_bytes completes with AMG_ERR_OOM.                */
 /* All pointers are host memory; the server copies what it needs.         */
 /* ---------------------------------------------------------------------- */
 
@@ -246,6 +249,9 @@ typedef struct {
 } amg_server_config;
 
 typedef struct {
+  /* resident_bytes counts resident hierarchies plus reservations of setups
+   * in progress; peak_resident_bytes is the largest total of resident
+   * hierarchies' measured sizes */
   size_t resident_bytes, peak_resident_bytes;
   int active, peak_active;
   int64_t queued, completed, setups, evictions;

@@ -112,6 +112,7 @@ struct SellView {
 
 struct Level {
   int n = 0;
+  int wps = 1;           // warps per SELL slice in the solve kernels (1, 2, 4 or 8)
   Csr A;                 // setup form
   double *diag = nullptr;
   double *dlow = nullptr;

@@ -25,8 +25,9 @@ namespace amg {
 __global__ void k_match_init(int n, int *mate);
 __global__ void k_propose(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                           const double *__restrict__ s, uint64_t salt, const int *__restrict__ mate,
-                          int *__restrict__ ptr);
-__global__ void k_accept(int n, const int *__restrict__ ptr, int *__restrict__ mate, int *added);
+                          int *__restrict__ ptr, const int *prev);
+__global__ void k_accept(int n, const int *__restrict__ ptr, int *__restrict__ mate, int *added,
+                         const int *prev);
 __global__ void k_rep_flags(int n, const int *__restrict__ mate, int *__restrict__ rep);
 __global__ void k_coarse_ids(int n, const int *__restrict__ mate, const int *__restrict__ id,
                              int *__restrict__ agg, int *__restrict__ m0, int *__restrict__ m1);
@@ -163,8 +164,8 @@ extern "C" amg_status amg_match_noalloc(int64_t n64, const int64_t *row_ptr, con
   for (;;) {
     AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * kBatch, st));  // counters start at zero
     for (int b = 0; b < kBatch; ++b) {
-      k_propose<<<nb, 256, 0, st>>>(n, row_ptr, col_idx, s, salt, mate, work);
-      k_accept<<<nb, 256, 0, st>>>(n, work, mate, added + b);
+      k_propose<<<nb, 256, 0, st>>>(n, row_ptr, col_idx, s, salt, mate, work, nullptr);
+      k_accept<<<nb, 256, 0, st>>>(n, work, mate, added + b, nullptr);
     }
     AMG_CUDA_TRY(cudaGetLastError());
     AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * kBatch, cudaMemcpyDeviceToHost, st));

@@ -37,6 +37,7 @@ struct GraphEntry {
   amg_handle h = nullptr;      // resident hierarchy or null
   cudaStream_t stream = nullptr;
   size_t bytes = 0;            // device bytes of the resident hierarchy (estimate before setup)
+  size_t measured = 0;         // arena bytes of this graph's last hierarchy (0: never set up)
   bool busy = false;           // a solve is using the hierarchy
   int64_t last_used = 0;
 };
@@ -53,10 +54,13 @@ struct Request {
   std::string err;
 };
 
-size_t estimate_bytes(const GraphEntry &g) {
-  // hierarchy ~ 1.4x the fine level's CSR + SELL copies and ~40 n-vectors
+// device bytes to reserve for a graph's hierarchy: the measured size once it
+// has been set up, else an estimate (all levels ~1.2x the fine level: CSR and
+// SELL copies of the matrix, ~25 work vectors per level, ~20 outer vectors)
+size_t reserve_bytes(const GraphEntry &g) {
+  if (g.measured) return g.measured;
   const double nnz = (double)g.rowptr.back(), n = (double)g.n;
-  return (size_t)(1.4 * (nnz * 28.0 + n * 8.0 * 40.0)) + ((size_t)64 << 20);
+  return (size_t)(1.2 * (nnz * 28.0 + n * 200.0) + n * 160.0) + ((size_t)1 << 20);
 }
 
 }  // namespace
@@ -113,8 +117,11 @@ void worker(amg_server_s *s) {
           GraphEntry &ge = s->graphs[r.graph];
           if (ge.busy) continue;
           if (!ge.h) {
-            ge.bytes = estimate_bytes(ge);
-            if (!make_room(s, ge.bytes)) continue;
+            ge.bytes = reserve_bytes(ge);
+            // With no other solve running and every idle hierarchy evicted,
+            // a graph that still does not fit is set up anyway: the check of
+            // its real size after the setup decides (an estimate may be high).
+            if (!make_room(s, ge.bytes) && s->active > 0) continue;
             s->resident_bytes += ge.bytes;  // reserved before the setup
             need_setup = true;
           }
@@ -130,7 +137,6 @@ void worker(amg_server_s *s) {
       }
       ++s->active;
       s->peak_active = std::max(s->peak_active, s->active);
-      s->peak_bytes = std::max(s->peak_bytes, s->resident_bytes);
     }
     Request *r;
     {
@@ -148,11 +154,23 @@ void worker(amg_server_s *s) {
       std::lock_guard<std::mutex> lk(s->mu);
       s->resident_bytes -= g->bytes;
       if (st == AMG_OK) {
-        g->h = h;
-        g->bytes = h->arena.bytes;
-        s->resident_bytes += g->bytes;
-        s->peak_bytes = std::max(s->peak_bytes, s->resident_bytes);
+        g->measured = h->arena.bytes;
         ++s->setups;
+        if (g->measured > s->cfg.mem_cap_bytes) {
+          // this hierarchy alone exceeds the cap: the request fails
+          amg_free(h);
+          g->bytes = 0;
+          st = AMG_ERR_OOM;
+          err = "the hierarchy needs " + std::to_string(g->measured) + " device bytes, more than mem_cap_bytes = " +
+                std::to_string(s->cfg.mem_cap_bytes);
+        } else {
+          g->h = h;
+          g->bytes = g->measured;
+          s->resident_bytes += g->bytes;
+          s->peak_bytes = std::max(s->peak_bytes, s->resident_bytes);
+        }
+      } else {
+        g->bytes = 0;
       }
     }
     if (st == AMG_OK) {

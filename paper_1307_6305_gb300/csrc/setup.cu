@@ -284,10 +284,13 @@ __global__ void k_match_init(int n, int *mate) {
 }
 
 // each unmatched vertex points across its largest-key edge to an unmatched
-// neighbour; key = (s_ij, hash, lo, hi) compared lexicographically
+// neighbour; key = (s_ij, hash, lo, hi) compared lexicographically.  `prev`
+// (optional) is the previous round's count of new pairs: once a round has
+// added none, the matching is maximal and later rounds do nothing.
 __global__ void k_propose(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                           const double *__restrict__ s, uint64_t salt, const int *__restrict__ mate,
-                          int *__restrict__ ptr) {
+                          int *__restrict__ ptr, const int *prev) {
+  if (prev && *prev == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int best = -1;
@@ -323,7 +326,9 @@ __global__ void k_propose(int n, const int64_t *__restrict__ rp, const int32_t *
   ptr[i] = best;
 }
 
-__global__ void k_accept(int n, const int *__restrict__ ptr, int *__restrict__ mate, int *added) {
+__global__ void k_accept(int n, const int *__restrict__ ptr, int *__restrict__ mate, int *added,
+                         const int *prev) {
+  if (prev && *prev == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int hit = 0;
   if (i < n) {
@@ -364,21 +369,23 @@ static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, cons
                              int *m1, int *nH_out, int *rounds_out, int64_t *launches) {
   int *ptr = nullptr, *added = nullptr, *rep = nullptr, *id = nullptr;
   AMG_TRY(pool_alloc((void **)&ptr, sizeof(int) * (size_t)std::max(n, 1), st));
-  AMG_TRY(pool_alloc((void **)&added, sizeof(int) * 4, st));
+  AMG_TRY(pool_alloc((void **)&added, sizeof(int) * 8, st));
   const unsigned nb = blocks_for(n, 256);
   k_match_init<<<nb, 256, 0, st>>>(n, mate);
   LAUNCH_CHECK(launches);
-  // Rounds are launched in batches: once a round adds no pair every later
-  // round is a no-op, so speculative rounds never change the result.
+  // Rounds are launched in batches between host checks; a round after one
+  // that added no pair is a device-side no-op (the matching is maximal), so
+  // the extra rounds of the last batch change nothing.
   int rounds = 0;
-  int h_added[4] = {0, 0, 0, 0};
-  const int kBatch = 2;
+  const int kBatch = 4;
+  int h_added[kBatch] = {0, 0, 0, 0};
   for (;;) {
     AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * kBatch, st));
     for (int b = 0; b < kBatch; ++b) {
-      k_propose<<<nb, 256, 0, st>>>(n, rowptr, col, s, salt, mate, ptr);
+      const int *prev = b ? added + b - 1 : nullptr;
+      k_propose<<<nb, 256, 0, st>>>(n, rowptr, col, s, salt, mate, ptr, prev);
       LAUNCH_CHECK(launches);
-      k_accept<<<nb, 256, 0, st>>>(n, ptr, mate, added + b);
+      k_accept<<<nb, 256, 0, st>>>(n, ptr, mate, added + b, prev);
       LAUNCH_CHECK(launches);
     }
     AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * kBatch, cudaMemcpyDeviceToHost, st));
@@ -447,6 +454,7 @@ __global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, const int 
 
 // gather mapped entries of the coarse row into its segment, stable-sort by J,
 // count distinct J != I
+constexpr int kLocalSort = 64;
 __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                               const double *__restrict__ val, const int *__restrict__ agg,
                               const int *__restrict__ m0, const int *__restrict__ m1,
@@ -467,6 +475,35 @@ __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int3
     }
   }
   const int64_t len = t - s0;
+  if (len <= kLocalSort) {
+    // short row (the usual case): sort in a thread-local array
+    int lk[kLocalSort];
+    double lv[kLocalSort];
+    for (int a = 0; a < len; ++a) {
+      lk[a] = keyJ[s0 + a];
+      lv[a] = kval[s0 + a];
+    }
+    for (int a = 1; a < len; ++a) {  // stable insertion sort by J
+      const int kj = lk[a];
+      const double kv = lv[a];
+      int b = a - 1;
+      while (b >= 0 && lk[b] > kj) {
+        lk[b + 1] = lk[b];
+        lv[b + 1] = lv[b];
+        --b;
+      }
+      lk[b + 1] = kj;
+      lv[b + 1] = kv;
+    }
+    int c = 0;
+    for (int a = 0; a < len; ++a) {
+      keyJ[s0 + a] = lk[a];
+      kval[s0 + a] = lv[a];
+      if (lk[a] != I && (a == 0 || lk[a - 1] != lk[a])) ++c;
+    }
+    count[I] = c;
+    return;
+  }
   for (int64_t a = 1; a < len; ++a) {  // stable insertion sort by J
     const int kj = keyJ[s0 + a];
     const double kv = kval[s0 + a];

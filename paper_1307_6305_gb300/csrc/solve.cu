@@ -15,8 +15,10 @@
 // The host walks the cycle and issues launches; it reads one scalar per
 // outer iteration (the residual norm for the stopping test).
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "common.cuh"
@@ -52,16 +54,91 @@ __device__ __forceinline__ T apply_row(const SellView<T> &A, const T *__restrict
   return sell_row(A, x, row, A.diag[row] * x[row]);
 }
 
+// Split rows for small levels.  With one thread per row, a row of w stored
+// entries costs about w/4 dependent round trips to L2 (column index, then
+// x[col]), and a level of a few thousand rows keeps only a few SMs busy on
+// the slow FP64 pipe.  With WPS > 1 the stored positions of a 32-row slice
+// are dealt round-robin to WPS warps (warp q takes positions q, q + WPS, ...,
+// still coalesced across the slice's rows); the partial sums meet in shared
+// memory and the group's first warp adds them in warp order, so the result is
+// deterministic.  A block of kThreads threads holds kThreads / 32 / WPS
+// slices; `group` numbers those blocks of slices.
+struct SplitIdx {
+  int q, s, lane, i;
+};
+
+template <int WPS>
+__device__ __forceinline__ SplitIdx split_index(int group) {
+  const int warp = threadIdx.x >> 5;
+  SplitIdx ix;
+  ix.q = warp % WPS;
+  ix.lane = threadIdx.x & 31;
+  ix.s = group * (kThreads / 32 / WPS) + warp / WPS;
+  ix.i = ix.s * kSlice + ix.lane;
+  return ix;
+}
+
+// warp q's share of row ix.i's sum, accumulated onto acc; xf(j) gives x_j
+template <typename T, int WPS, typename XF>
+__device__ __forceinline__ T split_partial(const SellView<T> &A, const SplitIdx &ix, T acc, XF xf) {
+  if (ix.i < A.n) {
+    const int64_t base = A.sptr[ix.s];
+    const int w = (int)((A.sptr[ix.s + 1] - base) >> 5);
+    const int32_t *__restrict__ c = A.scol + base + ix.lane;
+    const T *__restrict__ v = A.val + base + ix.lane;
+#pragma unroll 2
+    for (int k = ix.q; k < w; k += WPS) acc = fma(v[k * kSlice], xf(c[k * kSlice]), acc);
+  }
+  return acc;
+}
+
+// meet in shared memory; true in the group's first warp, which then holds
+// the row's full sum in acc.  Block-uniform: every thread must call it.
+template <typename T, int WPS>
+__device__ __forceinline__ bool split_combine(T &acc, T (*part)[32]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  part[warp][lane] = acc;
+  __syncthreads();
+  const bool lead = (warp % WPS) == 0;
+  if (lead) {
+#pragma unroll
+    for (int p = 1; p < WPS; ++p) acc += part[warp + p][lane];
+  }
+  return lead;
+}
+
+// row sum (diag_i x_i + sum_j a_ij x_j) of the split layout; valid in lead
+// threads whose row exists (returned flag)
+template <typename T, int WPS, typename XF>
+__device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &ix, T xi, XF xf, T &out,
+                                          T (*part)[32]) {
+  T acc = (ix.q == 0 && ix.i < A.n) ? A.diag[ix.i] * xi : T(0);
+  acc = split_partial<T, WPS>(A, ix, acc, xf);
+  const bool lead = split_combine<T, WPS>(acc, part);
+  out = acc;
+  return lead && ix.i < A.n;
+}
+
 // T_1 = t(A) r with t(A) = sa*A - ca*I; x (=|+=) b0*r + b1*T_1
-template <typename T, bool ADD>
+template <typename T, bool ADD, int WPS>
 __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> A, const T *__restrict__ r,
                                                          T *__restrict__ T1, T *__restrict__ x, T sa,
                                                          T ca, T b0, T b1) {
   pdl_sync();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
+  int i;
+  T Ar;
+  if constexpr (WPS == 1) {
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    Ar = apply_row(A, r, i);
+  } else {
+    __shared__ T part[kThreads / 32][32];
+    const SplitIdx ix = split_index<WPS>(blockIdx.x);
+    i = ix.i;
+    const T xi = i < A.n ? r[i] : T(0);
+    if (!split_row<T, WPS>(A, ix, xi, [&](int j) { return r[j]; }, Ar, part)) return;
+  }
   const T ri = r[i];
-  const T Ar = apply_row(A, r, i);
   const T t1 = fma(sa, Ar, -ca * ri);
   T1[i] = t1;
   const T inc = fma(b1, t1, b0 * ri);
@@ -69,15 +146,25 @@ __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> A, const T 
 }
 
 // T_{j+1} = 2 t(A) T_j - T_{j-1}; x += bj * T_{j+1}.  Tn may alias Tp.
-template <typename T>
+template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> A, const T *__restrict__ Tc,
                                                         const T *Tp, T *Tn, T *__restrict__ x, T sa,
                                                         T ca, T bj) {
   pdl_sync();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
+  int i;
+  T At;
+  if constexpr (WPS == 1) {
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    At = apply_row(A, Tc, i);
+  } else {
+    __shared__ T part[kThreads / 32][32];
+    const SplitIdx ix = split_index<WPS>(blockIdx.x);
+    i = ix.i;
+    const T xi = i < A.n ? Tc[i] : T(0);
+    if (!split_row<T, WPS>(A, ix, xi, [&](int j) { return Tc[j]; }, At, part)) return;
+  }
   const T tc = Tc[i];
-  const T At = apply_row(A, Tc, i);
   const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[i];
   Tn[i] = tn;
   x[i] = fma(bj, tn, x[i]);
@@ -91,22 +178,38 @@ __global__ void k_scale(int n, const T *__restrict__ r, T *__restrict__ x, T b0)
   x[i] = ADD ? x[i] + b0 * r[i] : b0 * r[i];
 }
 
-template <typename T>
+template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *__restrict__ x,
                                                        const T *__restrict__ r, T *__restrict__ s) {
   pdl_sync();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
-  s[i] = r[i] - apply_row(A, x, i);
+  if constexpr (WPS == 1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    s[i] = r[i] - apply_row(A, x, i);
+  } else {
+    __shared__ T part[kThreads / 32][32];
+    const SplitIdx ix = split_index<WPS>(blockIdx.x);
+    const T xi = ix.i < A.n ? x[ix.i] : T(0);
+    T Ax;
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) s[ix.i] = r[ix.i] - Ax;
+  }
 }
 
-template <typename T>
+template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_spmv(SellView<T> A, const T *__restrict__ x,
                                                    T *__restrict__ y) {
   pdl_sync();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
-  y[i] = apply_row(A, x, i);
+  if constexpr (WPS == 1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    y[i] = apply_row(A, x, i);
+  } else {
+    __shared__ T part[kThreads / 32][32];
+    const SplitIdx ix = split_index<WPS>(blockIdx.x);
+    const T xi = ix.i < A.n ? x[ix.i] : T(0);
+    T Ax;
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) y[ix.i] = Ax;
+  }
 }
 
 // r_H = P^T s; `flag`, when given, is the next level's inner-CG stop flag,
@@ -119,6 +222,7 @@ __global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__res
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   T acc = T(0);
+#pragma unroll 4
   for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += s[mem[a]];
   rH[I] = acc;
 }
@@ -281,7 +385,7 @@ __global__ void __launch_bounds__(kThreads) k_dots(int64_t n, DotSpec<T> spec, d
 }
 
 // y = A x fused with ND dot products; a null operand pointer stands for y
-template <typename T, int ND>
+template <typename T, int ND, int WPS>
 __global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *__restrict__ x,
                                                         T *__restrict__ y, DotSpec<T> spec,
                                                         double *partial, unsigned *ticket, Fin fin) {
@@ -289,14 +393,27 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *
   double acc[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) acc[q] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
-    const T yi = apply_row(A, x, i);
+  auto accumulate = [&](int i, T yi) {
     y[i] = yi;
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
       const double a = spec.a[q] ? (double)spec.a[q][i] : (double)yi;
       const double b = spec.b[q] ? (double)spec.b[q][i] : (double)yi;
       acc[q] += a * b;
+    }
+  };
+  if constexpr (WPS == 1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+      accumulate(i, apply_row(A, x, i));
+  } else {
+    __shared__ T part[kThreads / 32][32];
+    const int groups = (((A.n + kSlice - 1) / kSlice) * WPS + kThreads / 32 - 1) / (kThreads / 32);
+    for (int g = blockIdx.x; g < groups; g += gridDim.x) {  // block-uniform trip count
+      const SplitIdx ix = split_index<WPS>(g);
+      const T xi = ix.i < A.n ? x[ix.i] : T(0);
+      T yi;
+      if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, yi, part)) accumulate(ix.i, yi);
+      __syncthreads();  // part is rewritten by the next group
     }
   }
   reduce_and_finalize<ND>(acc, partial, ticket, fin);
@@ -328,12 +445,23 @@ __global__ void __launch_bounds__(kThreads) k_orth_dots(int64_t n, T *D, T *W, D
 // x_out = u + P e_H and s = r - A x_out in one pass: neighbours' values are
 // formed on the fly as u_j + e_H[agg_j] (the same rounding as forming x_out
 // first), so x_out never needs a second read
-template <typename T>
+template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, const int *__restrict__ agg,
                                                                const T *__restrict__ eH,
                                                                const T *__restrict__ u, const T *__restrict__ r,
                                                                T *__restrict__ xout, T *__restrict__ s) {
   pdl_sync();
+  if constexpr (WPS > 1) {
+    __shared__ T part[kThreads / 32][32];
+    const SplitIdx ix = split_index<WPS>(blockIdx.x);
+    const T xi = ix.i < A.n ? u[ix.i] + eH[agg[ix.i]] : T(0);
+    T Ax;
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return u[j] + eH[agg[j]]; }, Ax, part)) {
+      xout[ix.i] = xi;
+      s[ix.i] = r[ix.i] - Ax;
+    }
+    return;
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const T xi = u[i] + eH[agg[i]];
@@ -413,6 +541,33 @@ static inline unsigned red_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kThreads - 1) / kThreads));
 }
 
+// blocks of the SELL kernels: (slices x WPS) warps, kThreads / 32 per block
+static inline unsigned sell_grid(int n, int wps) {
+  const int64_t warps = (int64_t)((n + kSlice - 1) / kSlice) * wps;
+  return (unsigned)std::max<int64_t>(1, (warps + kThreads / 32 - 1) / (kThreads / 32));
+}
+
+// Warps per slice for a level of n rows: the smallest of 1, 2, 4, 8 that
+// gives at least ~16 warps per SM (152 SMs), so that small levels spread
+// their FP64 work and their dependent loads over the whole GPU.
+int choose_wps(int n) {
+  const int64_t slices = (n + kSlice - 1) / kSlice;
+  int w = 1;
+  while (w < 8 && slices * w < 16 * 152) w *= 2;
+  return w;
+}
+
+// call f(std::integral_constant<int, WPS>) for the level's WPS
+template <typename F>
+static amg_status with_wps(int wps, F f) {
+  switch (wps) {
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    default: return f(std::integral_constant<int, 1>{});
+  }
+}
+
 template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
@@ -447,20 +602,30 @@ static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin f
 template <typename T>
 static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotSpec<T> &spec, Fin fin) {
   amg::Level &L = h->lv[k];
-  const unsigned g = red_grid(L.n);
   double *P = h->red.partial;
   unsigned *tk = h->red.ticket;
   cudaStream_t st = h->stream;
   const SellView<T> A = view<T>(L);
+  if (L.wps > 1 && spec.nd <= 2) {  // the inner solve's shapes (nu = 2) take the split form
+    const unsigned g = std::min<unsigned>(kRedBlocks, sell_grid(L.n, L.wps));
+    AMG_TRY(with_wps(L.wps, [&](auto W) {
+      constexpr int wp = decltype(W)::value;
+      if (spec.nd == 1) return plaunch(h, st, k_spmv_dots<T, 1, wp>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin);
+      return plaunch(h, st, k_spmv_dots<T, 2, wp>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin);
+    }));
+    SLAUNCH(h);
+    return AMG_OK;
+  }
+  const unsigned g = red_grid(L.n);
   switch (spec.nd) {
-    case 1: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    case 2: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 2>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    case 3: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 3>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    case 4: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 4>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    case 5: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 5>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    case 6: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 6>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    case 7: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 7>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
-    default: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 8>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 1: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 1, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 2: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 2, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 3: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 3, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 4: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 4, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 5: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 5, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 6: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 6, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    case 7: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 7, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
+    default: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 8, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
   }
   SLAUNCH(h);
   return AMG_OK;
@@ -516,8 +681,12 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     return AMG_OK;
   }
   T *Ta = (T *)L.Ta, *Tb = (T *)L.Tb;
-  if (add) AMG_TRY(plaunch(h, st, k_cheb_first<T, true>, dim3(nblk(L.n)), dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]));
-  else AMG_TRY(plaunch(h, st, k_cheb_first<T, false>, dim3(nblk(L.n)), dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]));
+  const dim3 grid(sell_grid(L.n, L.wps));
+  AMG_TRY(with_wps(L.wps, [&](auto W) {
+    constexpr int wp = decltype(W)::value;
+    if (add) return plaunch(h, st, k_cheb_first<T, true, wp>, grid, dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
+    return plaunch(h, st, k_cheb_first<T, false, wp>, grid, dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
+  }));
   SLAUNCH(h);
   const T *Tp = r;
   T *Tc = Ta;
@@ -526,7 +695,9 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     T *Tn = (j == 2) ? Tb : const_cast<T *>(Tp);
     cudaEvent_t e0, e1;
     if (timed) AMG_TRY(timing_record(h, &e0));
-    AMG_TRY(plaunch(h, st, k_cheb_step<T>, dim3(nblk(L.n)), dim3(kThreads), A, Tc, Tp, Tn, x, sa, ca, (T)L.coef[j]));
+    AMG_TRY(with_wps(L.wps, [&](auto W) {
+      return plaunch(h, st, k_cheb_step<T, decltype(W)::value>, grid, dim3(kThreads), A, Tc, Tp, Tn, x, sa, ca, (T)L.coef[j]);
+    }));
     SLAUNCH(h);
     if (timed) AMG_TRY(timing_record(h, &e1));
     Tp = Tc;
@@ -538,7 +709,10 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
 template <typename T>
 static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s) {
   amg::Level &L = h->lv[k];
-  AMG_TRY(plaunch(h, h->stream, k_residual<T>, dim3(nblk(L.n)), dim3(kThreads), view<T>(L), x, r, s));
+  AMG_TRY(with_wps(L.wps, [&](auto W) {
+    return plaunch(h, h->stream, k_residual<T, decltype(W)::value>, dim3(sell_grid(L.n, L.wps)), dim3(kThreads),
+                   view<T>(L), x, r, s);
+  }));
   SLAUNCH(h);
   return AMG_OK;
 }
@@ -657,7 +831,10 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else if (k + 1 == h->tail_k0) AMG_TRY(launch_tail(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
-  AMG_TRY(plaunch(h, st, k_prolong_residual<T>, dim3(nblk(L.n)), dim3(kThreads), view<T>(L), L.agg, (const T *)N.x, u, r, x, s));
+  AMG_TRY(with_wps(L.wps, [&](auto W) {
+    return plaunch(h, st, k_prolong_residual<T, decltype(W)::value>, dim3(sell_grid(L.n, L.wps)), dim3(kThreads),
+                   view<T>(L), L.agg, (const T *)N.x, u, r, x, s);
+  }));
   SLAUNCH(h);
   AMG_TRY(smooth<T>(h, k, s, x, true));
   return AMG_OK;
@@ -749,9 +926,13 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   const bool f32 = h->opt.precision == AMG_PREC_FP32;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   const int L = h->L, nu = h->opt.inner_iters;
+  // AMG_GB300_SPLIT=0 keeps one thread per row on every level
+  const char *split_env = getenv("AMG_GB300_SPLIT");
+  const bool split = !(split_env && split_env[0] == '0');
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     const size_t n = (size_t)std::max(V.n, 1);
+    V.wps = split ? choose_wps(V.n) : 1;
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1) {
       AMG_TRY(h->arena.alloc(&V.u, es * n));
@@ -946,7 +1127,9 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       AMG_TRY(plaunch(h, st, k_axpy_multi<double>, dim3(nblk(n)), dim3(kThreads), n, d, h->oz, vd, sc + 16));
       SLAUNCH(h);
     }
-    AMG_TRY(plaunch(h, st, k_spmv<double>, dim3(nblk(n)), dim3(kThreads), A0, d, q));
+    AMG_TRY(with_wps(L0.wps, [&](auto W) {
+      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, d, q);
+    }));
     SLAUNCH(h);
     {
       DotSpec<double> sp{};
@@ -991,7 +1174,10 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
   // true residual ||b - A x|| / ||b||
   double true_rel = 0.0;
   if (nb > 0.0) {
-    AMG_TRY(plaunch(h, st, k_residual<double>, dim3(nblk(n)), dim3(kThreads), A0, x_dev, h->ob, h->oz));
+    AMG_TRY(with_wps(L0.wps, [&](auto W) {
+      return plaunch(h, st, k_residual<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, x_dev,
+                     h->ob, h->oz);
+    }));
     SLAUNCH(h);
     DotSpec<double> sp{};
     sp.a[0] = h->oz;
@@ -1049,8 +1235,12 @@ static amg_status run_conv(amg_handle_s *h, const double *in, int64_t nin, doubl
 amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y) {
   amg::Level &L = h->lv[k];
   AMG_TRY(run_conv(h, x, L.n, y, L.n, false, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_spmv<float>, dim3(nblk(L.n)), dim3(kThreads), view<float>(L), (const float *)a, (float *)b));
-    else AMG_TRY(plaunch(h, h->stream, k_spmv<double>, dim3(nblk(L.n)), dim3(kThreads), view<double>(L), (const double *)a, (double *)b));
+    AMG_TRY(with_wps(L.wps, [&](auto W) {
+      constexpr int wp = decltype(W)::value;
+      const dim3 g(sell_grid(L.n, L.wps));
+      if (f32(h)) return plaunch(h, h->stream, k_spmv<float, wp>, g, dim3(kThreads), view<float>(L), (const float *)a, (float *)b);
+      return plaunch(h, h->stream, k_spmv<double, wp>, g, dim3(kThreads), view<double>(L), (const double *)a, (double *)b);
+    }));
     SLAUNCH(h);
     return AMG_OK;
   }));

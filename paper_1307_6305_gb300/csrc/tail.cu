@@ -71,7 +71,7 @@ struct TailCtx {
   unsigned *bar;        // [0] arrivals, [1] generation
   double *gpart;        // [2][gridDim][kMaxDots] partial sums
   int *err;             // set when a barrier wait runs out
-  long long spin_limit; // polls before a barrier wait gives up
+  long long wait_ns;    // how long a barrier wait may last before it gives up
   int test_stall;       // test hook: wait for a generation that never comes
   bool failed;
 };
@@ -92,6 +92,12 @@ __device__ __forceinline__ void tail_fail(TailCtx &c) {
   c.tid = 0x3fffffff;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // grid-wide barrier with a bounded wait (sense by generation counter)
 __device__ __noinline__ void gbar(TailCtx &c) {
   __shared__ int ok_s;
@@ -106,15 +112,17 @@ __device__ __noinline__ void gbar(TailCtx &c) {
       __threadfence();
       atomicAdd(c.bar + 1, 1u);
     }
+    // spin without sleeping (a wake-up adds latency to every phase); every
+    // 256 polls look at the clock and at the error flag another CTA may set
     int ok = 1;
-    long long it = 0;
+    unsigned it = 0;
+    const unsigned long long t0 = global_ns();
     while ((int)(*gen - target) < 0) {
-      if (++it > c.spin_limit || *(volatile int *)c.err) {
+      if ((++it & 255u) == 0 && (global_ns() - t0 > (unsigned long long)c.wait_ns || *(volatile int *)c.err)) {
         atomicExch(c.err, 1);
         ok = 0;
         break;
       }
-      __nanosleep(64);
     }
     __threadfence();
     ok_s = ok;
@@ -416,7 +424,7 @@ struct TailSync {
   unsigned *bar;
   double *gpart;
   int *err;
-  long long spin_limit;
+  long long wait_ns;
   int test_stall;
 };
 
@@ -435,7 +443,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailParams<T> *_
     for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
   }
   TailCtx c{cg::this_cluster(), MODE, 0, 1, 0, 0, slots, wred, bcast, 0,
-            sy.bar, sy.gpart, sy.err, sy.spin_limit, sy.test_stall, false};
+            sy.bar, sy.gpart, sy.err, sy.wait_ns, sy.test_stall, false};
   if (MODE == kModeCluster) {
     c.rank = (int)c.cl.block_rank();
     c.csize = (int)c.cl.num_blocks();
@@ -525,7 +533,12 @@ static amg_status prepare(amg_handle_s *h, int mode) {
     AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tail<T, kModeGrid>, kTailThreads, 0));
     if (per < 1) return fail(AMG_ERR_CUDA, "the grid tail kernel does not fit on an SM");
-    csize = sms;  // one CTA per SM: all co-resident, as a grid barrier needs
+    // At most one CTA per SM, so all are co-resident, as a grid barrier needs.
+    // 16 CTAs measured fastest on the 128^3 hierarchy (the barrier's cost
+    // grows with the CTA count faster than the tail levels' work shrinks);
+    // AMG_GB300_TAIL_CTAS overrides.
+    csize = std::min(sms, 16);
+    if (const char *env = getenv("AMG_GB300_TAIL_CTAS")) csize = std::max(1, std::min(sms, atoi(env)));
   }
   h->tail_csize = csize;
   h->tail_mode = mode;
@@ -583,9 +596,9 @@ static amg_status launch(amg_handle_s *h) {
   sy.bar = h->tail_bar;
   sy.gpart = h->tail_gpart;
   sy.err = h->tail_err;
-  // about 2^26 polls of >= 64 ns: seconds, far beyond any real wait; the
-  // test hook uses a few thousand polls
-  sy.spin_limit = h->tail_test_stall ? 4096 : (1LL << 26);
+  // a real barrier wait lasts microseconds: give up after 2 s (the test
+  // hook, whose barrier never opens, after 5 ms)
+  sy.wait_ns = h->tail_test_stall ? 5000000LL : 2000000000LL;
   sy.test_stall = h->tail_test_stall;
   const TailParams<T> *P = (const TailParams<T> *)h->tail_params;
   if (h->tail_mode == kModeCTA) {

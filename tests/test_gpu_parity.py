@@ -246,3 +246,32 @@ def test_full_size_grid3d_128(amg, orc):
     m = min(len(hist), len(ref.history))
     assert np.abs(hist[:m] - ref.history[:m]).max() <= 1e-10
     close(xd.cpu().numpy(), ref.x, 1e-7)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_rows_match_one_thread_per_row(amg, orc, precision, monkeypatch):
+    """Small levels run their SELL kernels with several warps per 32-row slice
+    (AMG_GB300_SPLIT=0 turns that off).  Both forms solve the same problem:
+    the same iteration count, residual histories within 1e-10 (fp64) and
+    solutions within 1e-7; and the split form still meets the oracle."""
+    g = gg.grid3d_7pt(24, 1.0)
+    opts = dict(degree=5, passes=3, precision=precision)
+    b = gg.rhs(g.n, 77, False)
+    runs = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("AMG_GB300_SPLIT", flag)
+        h = amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts)
+        x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        st, info, hist = h.solve(cuda(b), x, tol=1e-8)
+        assert st == amg.AMG_OK
+        runs[flag] = (x.cpu().numpy(), info.iterations, np.asarray(hist))
+        h.close()
+    (x0, i0, h0), (x1, i1, h1) = runs["0"], runs["1"]
+    assert i0 == i1
+    if precision == 0:
+        assert np.abs(h0 - h1).max() <= 1e-10
+        ref = orc.Hierarchy(g, degree=5, passes=3).solve(b, tol=1e-8)
+        assert abs(i1 - ref.iterations) <= 1
+        m = min(len(h1), len(ref.history))
+        assert np.abs(h1[:m] - ref.history[:m]).max() <= 1e-10
+    close(x1, x0, 1e-7)

@@ -7,6 +7,8 @@
 * Slots overlap (peak active > 1) and every solution meets its tolerance.
 * Under a memory cap that holds only a few hierarchies, idle hierarchies are
   evicted and re-built and every request still completes.
+* A hierarchy larger than the cap fails its request with AMG_ERR_OOM instead
+  of waiting forever.
 """
 import numpy as np
 import pytest
@@ -73,13 +75,43 @@ def test_same_result_alone_and_in_the_mix(amg, precision):
         assert np.linalg.norm(b - A @ xm) <= 1e-7 * np.linalg.norm(b)
 
 
+def hierarchy_bytes(amg, graphs):
+    """Arena bytes of each graph's hierarchy, read off the server's resident
+    total while the graphs are set up one at a time under an ample cap."""
+    srv = amg.Server(8 << 30, 1, degree=4, passes=3)
+    out, before = [], 0
+    for g in graphs:
+        gid = srv.add_graph(g)
+        assert srv.wait(srv.submit(gid, gg.rhs(g.n, 5, gg.is_pure_laplacian(g))))[0] == amg.AMG_OK
+        now = srv.stats().resident_bytes
+        out.append(now - before)
+        before = now
+    srv.close()
+    return out
+
+
 def test_memory_cap_evicts_idle_hierarchies(amg):
     graphs = pool()
+    sizes = hierarchy_bytes(amg, graphs)
+    cap = int(1.3 * max(sizes))
+    assert cap < sum(sizes)          # not every hierarchy fits at once
     reqs = requests(graphs, per=2)
-    res, stats = run(amg, graphs, reqs, 2, cap=160 << 20)
+    res, stats = run(amg, graphs, reqs, 2, cap=cap)
+    assert stats.peak_resident_bytes <= cap
     assert stats.evictions > 0 and stats.setups > len(graphs)
     for (gi, b), (st, x, info, lat) in zip(reqs, res):
         assert st == amg.AMG_OK
         A = sparse_laplacian(graphs[gi])
         assert np.linalg.norm(b - A @ x) <= 1e-7 * np.linalg.norm(b)
         assert lat > 0
+
+
+def test_hierarchy_larger_than_cap_fails_cleanly(amg):
+    g = gg.grid2d_5pt(150)
+    srv = amg.Server(1 << 20, 2, degree=4, passes=3)
+    gid = srv.add_graph(g)
+    st, x, info, lat = srv.wait(srv.submit(gid, gg.rhs(g.n, 3, gg.is_pure_laplacian(g))))
+    assert st == amg.AMG_ERR_OOM
+    stats = srv.stats()
+    assert stats.resident_bytes == 0 and stats.completed == 1
+    srv.close()
