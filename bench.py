@@ -138,7 +138,7 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    src = open(os.path.join(ROOT, "paper_1307_6305_gb300", "csrc", "solve.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_1307_6305_gb300", "csrc", "sell_kernels.cuh"), "rb").read()
     return hashlib.sha256(src).hexdigest()[:16]
 
 

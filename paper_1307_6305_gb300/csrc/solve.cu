@@ -5,7 +5,8 @@
 //   k_cheb_first / k_cheb_step : one SpMV on the SELL-32 operator fused with
 //       one step of the Chebyshev three-term recurrence for q_m(A) r and the
 //       accumulation x += c_j T_j (Sec. 3 smoother R = q_m(A));
-//   k_residual                 : s = r - A x;
+//   k_residual                 : s = r - A x
+//       (these two groups live in sell_kernels.cuh);
 //   k_restrict / k_prolong_add : r_H = P^T s (sum over aggregate members in
 //       ascending order) and x += P e_H (Eq. (coarse));
 //   k_dots                     : up to kMaxDots dot products in one pass,
@@ -23,6 +24,7 @@
 
 #include "common.cuh"
 #include "block_kernels.cuh"
+#include "sell_kernels.cuh"
 
 namespace amg {
 
@@ -33,184 +35,6 @@ namespace amg {
     if (e_ != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
   } while (0)
 
-
-// ---------------------------------------------------------------------------
-// SELL-32 row kernel: off-diagonal part of row `row` times x
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict__ x, int row, T acc) {
-  const int s = row >> 5, lane = row & 31;
-  const int64_t base = A.sptr[s];
-  const int w = (int)((A.sptr[s + 1] - base) >> 5);
-  const int32_t *__restrict__ c = A.scol + base + lane;
-  const T *__restrict__ v = A.val + base + lane;
-#pragma unroll 4
-  for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[c[k * kSlice]], acc);
-  return acc;
-}
-
-template <typename T>
-__device__ __forceinline__ T apply_row(const SellView<T> &A, const T *__restrict__ x, int row) {
-  return sell_row(A, x, row, A.diag[row] * x[row]);
-}
-
-// Split rows for small levels.  With one thread per row, a row of w stored
-// entries costs about w/4 dependent round trips to L2 (column index, then
-// x[col]), and a level of a few thousand rows keeps only a few SMs busy on
-// the slow FP64 pipe.  With WPS > 1 the stored positions of a 32-row slice
-// are dealt round-robin to WPS warps (warp q takes positions q, q + WPS, ...,
-// still coalesced across the slice's rows); the partial sums meet in shared
-// memory and the group's first warp adds them in warp order, so the result is
-// deterministic.  A block of kThreads threads holds kThreads / 32 / WPS
-// slices; `group` numbers those blocks of slices.
-struct SplitIdx {
-  int q, s, lane, i;
-};
-
-template <int WPS>
-__device__ __forceinline__ SplitIdx split_index(int group) {
-  const int warp = threadIdx.x >> 5;
-  SplitIdx ix;
-  ix.q = warp % WPS;
-  ix.lane = threadIdx.x & 31;
-  ix.s = group * (kThreads / 32 / WPS) + warp / WPS;
-  ix.i = ix.s * kSlice + ix.lane;
-  return ix;
-}
-
-// warp q's share of row ix.i's sum, accumulated onto acc; xf(j) gives x_j
-template <typename T, int WPS, typename XF>
-__device__ __forceinline__ T split_partial(const SellView<T> &A, const SplitIdx &ix, T acc, XF xf) {
-  if (ix.i < A.n) {
-    const int64_t base = A.sptr[ix.s];
-    const int w = (int)((A.sptr[ix.s + 1] - base) >> 5);
-    const int32_t *__restrict__ c = A.scol + base + ix.lane;
-    const T *__restrict__ v = A.val + base + ix.lane;
-#pragma unroll 2
-    for (int k = ix.q; k < w; k += WPS) acc = fma(v[k * kSlice], xf(c[k * kSlice]), acc);
-  }
-  return acc;
-}
-
-// meet in shared memory; true in the group's first warp, which then holds
-// the row's full sum in acc.  Block-uniform: every thread must call it.
-template <typename T, int WPS>
-__device__ __forceinline__ bool split_combine(T &acc, T (*part)[32]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  part[warp][lane] = acc;
-  __syncthreads();
-  const bool lead = (warp % WPS) == 0;
-  if (lead) {
-#pragma unroll
-    for (int p = 1; p < WPS; ++p) acc += part[warp + p][lane];
-  }
-  return lead;
-}
-
-// row sum (diag_i x_i + sum_j a_ij x_j) of the split layout; valid in lead
-// threads whose row exists (returned flag)
-template <typename T, int WPS, typename XF>
-__device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &ix, T xi, XF xf, T &out,
-                                          T (*part)[32]) {
-  T acc = (ix.q == 0 && ix.i < A.n) ? A.diag[ix.i] * xi : T(0);
-  acc = split_partial<T, WPS>(A, ix, acc, xf);
-  const bool lead = split_combine<T, WPS>(acc, part);
-  out = acc;
-  return lead && ix.i < A.n;
-}
-
-// T_1 = t(A) r with t(A) = sa*A - ca*I; x (=|+=) b0*r + b1*T_1
-template <typename T, bool ADD, int WPS>
-__global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> A, const T *__restrict__ r,
-                                                         T *__restrict__ T1, T *__restrict__ x, T sa,
-                                                         T ca, T b0, T b1) {
-  pdl_sync();
-  int i;
-  T Ar;
-  if constexpr (WPS == 1) {
-    i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    Ar = apply_row(A, r, i);
-  } else {
-    __shared__ T part[kThreads / 32][32];
-    const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    i = ix.i;
-    const T xi = i < A.n ? r[i] : T(0);
-    if (!split_row<T, WPS>(A, ix, xi, [&](int j) { return r[j]; }, Ar, part)) return;
-  }
-  const T ri = r[i];
-  const T t1 = fma(sa, Ar, -ca * ri);
-  T1[i] = t1;
-  const T inc = fma(b1, t1, b0 * ri);
-  x[i] = ADD ? x[i] + inc : inc;
-}
-
-// T_{j+1} = 2 t(A) T_j - T_{j-1}; x += bj * T_{j+1}.  Tn may alias Tp.
-template <typename T, int WPS>
-__global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> A, const T *__restrict__ Tc,
-                                                        const T *Tp, T *Tn, T *__restrict__ x, T sa,
-                                                        T ca, T bj) {
-  pdl_sync();
-  int i;
-  T At;
-  if constexpr (WPS == 1) {
-    i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    At = apply_row(A, Tc, i);
-  } else {
-    __shared__ T part[kThreads / 32][32];
-    const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    i = ix.i;
-    const T xi = i < A.n ? Tc[i] : T(0);
-    if (!split_row<T, WPS>(A, ix, xi, [&](int j) { return Tc[j]; }, At, part)) return;
-  }
-  const T tc = Tc[i];
-  const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[i];
-  Tn[i] = tn;
-  x[i] = fma(bj, tn, x[i]);
-}
-
-template <typename T, bool ADD>
-__global__ void k_scale(int n, const T *__restrict__ r, T *__restrict__ x, T b0) {
-  pdl_sync();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  x[i] = ADD ? x[i] + b0 * r[i] : b0 * r[i];
-}
-
-template <typename T, int WPS>
-__global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *__restrict__ x,
-                                                       const T *__restrict__ r, T *__restrict__ s) {
-  pdl_sync();
-  if constexpr (WPS == 1) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    s[i] = r[i] - apply_row(A, x, i);
-  } else {
-    __shared__ T part[kThreads / 32][32];
-    const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const T xi = ix.i < A.n ? x[ix.i] : T(0);
-    T Ax;
-    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) s[ix.i] = r[ix.i] - Ax;
-  }
-}
-
-template <typename T, int WPS>
-__global__ void __launch_bounds__(kThreads) k_spmv(SellView<T> A, const T *__restrict__ x,
-                                                   T *__restrict__ y) {
-  pdl_sync();
-  if constexpr (WPS == 1) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    y[i] = apply_row(A, x, i);
-  } else {
-    __shared__ T part[kThreads / 32][32];
-    const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const T xi = ix.i < A.n ? x[ix.i] : T(0);
-    T Ax;
-    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) y[ix.i] = Ax;
-  }
-}
 
 // r_H = P^T s; `flag`, when given, is the next level's inner-CG stop flag,
 // cleared here because the inner solve on r_H starts right after
