@@ -128,6 +128,7 @@ void destroy(amg_handle_s *h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   h->arena.release();
+  if (h->leaf_params && h->leaf_free) h->leaf_free(h->leaf_params);
   if (h->pre_exec) cudaGraphExecDestroy(h->pre_exec);
   if (h->bpre_exec) cudaGraphExecDestroy(h->bpre_exec);
   if (h->b_pinned) cudaFreeHost(h->b_pinned);
@@ -224,6 +225,7 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   if (!s) s = allocate_solve_buffers(h);
   if (!s) s = build_dense_two_level(h);
   if (!s) s = prepare_tail(h);
+  if (!s) s = prepare_leaf(h);
   if (!s) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = fail(AMG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e));

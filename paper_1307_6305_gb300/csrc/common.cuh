@@ -189,6 +189,12 @@ struct amg_handle_s {
   int Bk = -1;
   double *Bd = nullptr;
   double *bb64 = nullptr, *bx64 = nullptr;
+  // the inner solve at level leaf_k (= Bk - 1) as one cluster kernel whose
+  // vectors live in shared memory (leaf.cu); -1: multi-kernel path
+  int leaf_k = -1;
+  int leaf_csize = 0;
+  void *leaf_params = nullptr;             // host copy of the launch parameters
+  void (*leaf_free)(void *) = nullptr;
   // levels >= tail_k0 run as one persistent cluster kernel per inner solve
   int tail_k0 = -1;
   // batched path (batch.cu)
@@ -247,6 +253,8 @@ amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs
 // tail.cu
 amg_status prepare_tail(amg_handle_s *h);
 amg_status launch_tail(amg_handle_s *h);
+amg_status prepare_leaf(amg_handle_s *h);
+amg_status launch_leaf(amg_handle_s *h);
 amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol,
                      amg_info *info, int *iters, double *rel, double *true_rel, int *converged);
 amg_status apply_spmv(amg_handle_s *h, int k, const double *x, double *y);

@@ -1,0 +1,678 @@
+// leaf.cu -- the inner flexible-CG solve at the level just above the dense
+// two-level operator, as ONE thread-block-cluster kernel per call.
+//
+// Level k0 = Bk - 1 (a few hundred to two thousand rows) is visited 2^k0
+// times per outer iteration.  Issued as separate kernels, one inner solve
+// there is ~45 dependent launches whose cost is latency -- dependent L2
+// round trips inside each kernel plus the launch gaps -- not work.  Here one
+// launch runs the whole inner solve at k0 (nu flexible-CG steps, each
+// preconditioned by the K-cycle at k0: smoothing, restriction, the inner
+// solve at k0+1 preconditioned by the dense two-level operator B,
+// prolongation, smoothing; Sec. 3, Sec. 4) on one cluster of C CTAs:
+//   * CTA c owns a contiguous block of rows on both levels and keeps its rows
+//     of A_k0 and A_k0+1 (compact CSR, no slice padding) and of B in shared
+//     memory;
+//   * every vector that some phase reads at another CTA's rows is kept as a
+//     full copy in every CTA's shared memory; the phase that produces it
+//     writes each new entry into all C copies with distributed-shared-memory
+//     stores, so every later read is a local shared-memory load;
+//   * a hardware cluster barrier (release/acquire) ends each phase;
+//   * dot products: each CTA posts its partial sums into every CTA's slot
+//     table; after the barrier every CTA adds the C partials in rank order,
+//     so all CTAs hold bit-identical Krylov scalars (the stop/breakdown
+//     decisions are therefore uniform) and no global scalar traffic occurs.
+// Every cluster barrier sits in code whose trip counts come from the launch
+// parameters only, so all CTAs meet the same barriers.
+//
+// The arithmetic is that of the multi-kernel path (solve.cu) step for step:
+// the Chebyshev recurrence, the stop rule of the inner flexible CG and the
+// vector updates are the same expressions in the same precision; only the
+// summation order inside a row and inside a dot product differs.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace amg {
+
+constexpr int kLeafThreads = 256;
+constexpr int kLeafWarps = kLeafThreads / 32;
+constexpr int kLeafMaxC = 16;
+constexpr int kLeafMaxInner = 4;
+constexpr int kLeafMaxRows = 2048;    // rows of level k0
+constexpr int kLeafMaxCoarse = 1024;  // rows of level k0 + 1
+constexpr int kLeafSlot = 8;          // doubles per CTA in a slot table
+
+// shared-memory arrays, in layout order
+enum LeafArr : int {
+  // full copies, level k0 (n entries of T)
+  A_B = 0, A_R, A_TA, A_TB, A_U, A_S, A_D0,
+  // owned rows, level k0 (R entries of T)
+  A_W0 = A_D0 + kLeafMaxInner, A_XO = A_W0 + kLeafMaxInner,
+  // full copies, level k0+1 (nH entries of T)
+  A_HB, A_HR, A_HX, A_HD0,
+  // owned rows, level k0+1 (RH entries of T)
+  A_HW0 = A_HD0 + kLeafMaxInner,
+  // compact CSR of the owned rows of A_k0 (off-diagonal) and its diagonal
+  A_LRP = A_HW0 + kLeafMaxInner, A_LCOL, A_LVAL, A_LDIAG,
+  // aggregate id of every row of level k0
+  A_AGG,
+  // member lists of the owned aggregates
+  A_LAP, A_LAM,
+  // compact CSR of the owned rows of A_k0+1 and its diagonal
+  A_HRP, A_HCOL, A_HVAL, A_HDIAG,
+  // owned rows of B (fp64, nH columns)
+  A_BROWS,
+  // dot-product slot tables [2][C][kLeafSlot] and per-warp partials
+  A_SLOTS, A_WRED,
+  A_COUNT
+};
+
+template <typename T>
+struct LeafParams {
+  int n, nH, C, R, RH, m, nu, tpr, tprH;
+  int maxnz, maxnzH, maxmem;
+  T sa, ca;
+  T coef[kMaxDegree + 1];
+  const int64_t *rp;
+  const int32_t *col;
+  const double *val, *diag;
+  const int32_t *agg, *agg_ptr, *agg_mem;
+  const int64_t *rpH;
+  const int32_t *colH;
+  const double *valH, *diagH;
+  const double *B;
+  const T *b;
+  T *x;
+  unsigned off[A_COUNT];  // byte offsets into dynamic shared memory
+  unsigned smem;          // bytes
+};
+
+// byte offsets of every array (16-byte aligned); identical on host and device
+template <typename T>
+static unsigned leaf_layout(LeafParams<T> &P) {
+  size_t cnt[A_COUNT] = {};
+  size_t esz[A_COUNT] = {};
+  for (int a = 0; a < A_COUNT; ++a) esz[a] = sizeof(T);
+  for (int a = A_B; a <= A_S; ++a) cnt[a] = P.n;
+  for (int l = 0; l < P.nu; ++l) {
+    cnt[A_D0 + l] = P.n;
+    cnt[A_W0 + l] = P.R;
+    cnt[A_HD0 + l] = P.nH;
+    cnt[A_HW0 + l] = P.RH;
+  }
+  cnt[A_XO] = P.R;
+  cnt[A_HB] = cnt[A_HR] = cnt[A_HX] = P.nH;
+  cnt[A_LRP] = P.R + 1;
+  esz[A_LRP] = sizeof(int);
+  cnt[A_LCOL] = P.maxnz;
+  esz[A_LCOL] = sizeof(int);
+  cnt[A_LVAL] = P.maxnz;
+  cnt[A_LDIAG] = P.R;
+  cnt[A_AGG] = P.n;
+  esz[A_AGG] = sizeof(int);
+  cnt[A_LAP] = P.RH + 1;
+  esz[A_LAP] = sizeof(int);
+  cnt[A_LAM] = P.maxmem;
+  esz[A_LAM] = sizeof(int);
+  cnt[A_HRP] = P.RH + 1;
+  esz[A_HRP] = sizeof(int);
+  cnt[A_HCOL] = P.maxnzH;
+  esz[A_HCOL] = sizeof(int);
+  cnt[A_HVAL] = P.maxnzH;
+  cnt[A_HDIAG] = P.RH;
+  cnt[A_BROWS] = (size_t)P.RH * P.nH;
+  esz[A_BROWS] = sizeof(double);
+  cnt[A_SLOTS] = 2 * (size_t)P.C * kLeafSlot;
+  esz[A_SLOTS] = sizeof(double);
+  cnt[A_WRED] = kLeafWarps * kLeafSlot;
+  esz[A_WRED] = sizeof(double);
+  size_t o = 0;
+  for (int a = 0; a < A_COUNT; ++a) {
+    o = (o + 15) & ~(size_t)15;
+    P.off[a] = (unsigned)o;
+    o += cnt[a] * esz[a];
+  }
+  P.smem = (unsigned)((o + 15) & ~(size_t)15);
+  return P.smem;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ LeafParams<T> P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int C = P.C, n = P.n, nH = P.nH, nu = P.nu, m = P.m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // owned rows [r0, r0 + nloc) and [h0, h0 + nlocH); trailing CTAs may own
+  // none (r0 >= n), hence the clamped starts used for loads
+  const int r0 = rank * P.R, nloc = max(0, min(n, r0 + P.R) - r0), r0c = min(r0, n);
+  const int h0 = rank * P.RH, nlocH = max(0, min(nH, h0 + P.RH) - h0), h0c = min(h0, nH);
+
+  auto vec = [&](int a) { return reinterpret_cast<T *>(sm + P.off[a]); };
+  auto ivec = [&](int a) { return reinterpret_cast<int *>(sm + P.off[a]); };
+  T *vb = vec(A_B), *vr = vec(A_R), *vTa = vec(A_TA), *vTb = vec(A_TB), *vu = vec(A_U), *vs = vec(A_S);
+  T *xo = vec(A_XO);
+  T *hb = vec(A_HB), *hr = vec(A_HR), *hx = vec(A_HX);
+  int *lrp = ivec(A_LRP), *lcol = ivec(A_LCOL), *agg = ivec(A_AGG), *lap = ivec(A_LAP), *lam = ivec(A_LAM);
+  int *hrp = ivec(A_HRP), *hcol = ivec(A_HCOL);
+  T *lval = vec(A_LVAL), *ldiag = vec(A_LDIAG), *hval = vec(A_HVAL), *hdiag = vec(A_HDIAG);
+  double *brows = reinterpret_cast<double *>(sm + P.off[A_BROWS]);
+  double *slots = reinterpret_cast<double *>(sm + P.off[A_SLOTS]);
+  double *wred = reinterpret_cast<double *>(sm + P.off[A_WRED]);
+  __shared__ double s_sc[40];
+
+  // ---- load: b (all rows), the owned rows of both operators, B, maps ----
+  for (int i = tid; i < n; i += kLeafThreads) {
+    vb[i] = P.b[i];
+    agg[i] = P.agg[i];
+  }
+  const int64_t e0 = P.rp[r0c];
+  for (int li = tid; li <= nloc; li += kLeafThreads) lrp[li] = (int)(P.rp[r0c + li] - e0);
+  for (int li = tid; li < nloc; li += kLeafThreads) ldiag[li] = (T)P.diag[r0 + li];
+  {
+    const int cnt = (int)(P.rp[r0c + nloc] - e0);
+    for (int e = tid; e < cnt; e += kLeafThreads) {
+      lcol[e] = P.col[e0 + e];
+      lval[e] = (T)P.val[e0 + e];
+    }
+  }
+  const int64_t f0 = P.rpH[h0c];
+  const int a0 = P.agg_ptr[h0c];
+  for (int lI = tid; lI <= nlocH; lI += kLeafThreads) {
+    hrp[lI] = (int)(P.rpH[h0c + lI] - f0);
+    lap[lI] = P.agg_ptr[h0c + lI] - a0;
+  }
+  for (int lI = tid; lI < nlocH; lI += kLeafThreads) hdiag[lI] = (T)P.diagH[h0 + lI];
+  {
+    const int cnt = (int)(P.rpH[h0c + nlocH] - f0);
+    for (int e = tid; e < cnt; e += kLeafThreads) {
+      hcol[e] = P.colH[f0 + e];
+      hval[e] = (T)P.valH[f0 + e];
+    }
+    const int mc = P.agg_ptr[h0c + nlocH] - a0;
+    for (int e = tid; e < mc; e += kLeafThreads) lam[e] = P.agg_mem[a0 + e];
+  }
+  for (int e = tid; e < nlocH * nH; e += kLeafThreads) brows[e] = P.B[(size_t)h0c * nH + e];
+  cl.sync();  // every CTA has started and loaded before any remote store
+
+  // ---- building blocks ----
+  // write v into row i of `a` in every CTA's copy (fire-and-forget stores)
+  auto put = [&](T *a, int i, T v) {
+    for (int r = 0; r < C; ++r) *cl.map_shared_rank(a + i, (unsigned)r) = v;
+  };
+  // sweep over the owned rows of A_k0: epi(local row, row, sum_j a_ij x_j, q).
+  // The tpr lanes of a row share its entries; every lane gets the full sum,
+  // but only lane q == 0 may write (a row's vectors are read and written in
+  // place within one phase, e.g. x += c_j T_j, so a second writer could race
+  // with a slower reader of the same row).
+  auto sweep = [&](auto xf, auto epi) {
+    const int tpr = P.tpr, q = tid & (tpr - 1), per = kLeafThreads / tpr;
+    for (int base = 0; base < P.R; base += per) {
+      const int li = base + tid / tpr;
+      const bool ok = li < nloc;
+      T acc = T(0);
+      if (ok)
+        for (int e = lrp[li] + q; e < lrp[li + 1]; e += tpr) acc = fma(lval[e], xf(lcol[e]), acc);
+      for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (ok) epi(li, r0 + li, acc, q);
+    }
+  };
+  auto sweepH = [&](auto xf, auto epi) {
+    const int tpr = P.tprH, q = tid & (tpr - 1), per = kLeafThreads / tpr;
+    for (int base = 0; base < P.RH; base += per) {
+      const int lI = base + tid / tpr;
+      const bool ok = lI < nlocH;
+      T acc = T(0);
+      if (ok)
+        for (int e = hrp[lI] + q; e < hrp[lI + 1]; e += tpr) acc = fma(hval[e], xf(hcol[e]), acc);
+      for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (ok) epi(lI, h0 + lI, acc, q);
+    }
+  };
+  // dot products: post this CTA's nd partial sums (nd <= kLeafSlot, static
+  // register indices) to every CTA's slot table
+  int sb = 0;
+  auto post = [&](const double (&v)[kLeafSlot], int nd) {
+#pragma unroll
+    for (int q = 0; q < kLeafSlot; ++q) {
+      if (q < nd) {
+        double t = v[q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) wred[warp * kLeafSlot + q] = t;
+      }
+    }
+    __syncthreads();
+    if (tid < nd) {
+      double t = 0.0;
+      for (int w = 0; w < kLeafWarps; ++w) t += wred[w * kLeafSlot + tid];
+      for (int r = 0; r < C; ++r)
+        *cl.map_shared_rank(slots + (sb * C + rank) * kLeafSlot + tid, (unsigned)r) = t;
+    }
+  };
+  // after the barrier: the cluster-wide sums, added in rank order by nd
+  // threads (the FP64 pipe runs 2 lanes per clock: scalar work is done once
+  // per CTA, not once per thread) into shared out[0, nd); then a CTA barrier
+  auto fold = [&](double *out, int nd) {
+    if (tid < nd) {
+      double t = 0.0;
+      for (int c = 0; c < C; ++c) t += slots[(sb * C + c) * kLeafSlot + tid];
+      out[tid] = t;
+    }
+    sb ^= 1;
+    __syncthreads();
+  };
+  // Krylov scalars of one inner flexible CG, in shared memory: rho[4],
+  // alpha[4], beta[4], stop flag; sums[8] holds folded dot products
+  double *const scT = s_sc, *const scH = s_sc + 16, *const sums = s_sc + 32;
+  // rho_it = s0; alpha_it = s1 / rho_it unless the solve has stopped or
+  // rho_it is not a positive finite number (then the stop flag is set and
+  // alpha_it = 0): the rule of the multi-kernel path.  Thread 0 only.
+  auto fin_alpha = [&](double *sc, int it) {
+    const double r = sums[0], sg = sums[1];
+    sc[it] = r;
+    if (sc[12] != 0.0 || !(r > 0.0) || !isfinite(r)) {
+      sc[12] = 1.0;
+      sc[4 + it] = 0.0;
+    } else {
+      sc[4 + it] = sg / r;
+    }
+  };
+
+  // x (=|+=) q_m(A) r on level k0; r is a full copy, x a full copy whose
+  // owned rows are updated and which is broadcast by the last step
+  auto smooth = [&](const T *r, T *x, bool add) {
+    if (m == 0) {
+      for (int li = tid; li < nloc; li += kLeafThreads) {
+        const int i = r0 + li;
+        const T inc = P.coef[0] * r[i];
+        const T v = add ? x[i] + inc : inc;
+        put(x, i, v);
+      }
+      cl.sync();
+      return;
+    }
+    const T sa = P.sa, ca = P.ca, b0 = P.coef[0], b1 = P.coef[1];
+    sweep([&](int j) { return r[j]; },
+          [&](int li, int i, T acc, int q) {
+            if (q != 0) return;
+            const T ri = r[i];
+            const T Ar = fma(ldiag[li], ri, acc);
+            const T t1 = fma(sa, Ar, -ca * ri);
+            if (m > 1) put(vTa, i, t1);
+            const T inc = fma(b1, t1, b0 * ri);
+            const T v = add ? x[i] + inc : inc;
+            if (m == 1) put(x, i, v);
+            else x[i] = v;
+          });
+    cl.sync();
+    const T *Tp = r;
+    T *Tc = vTa;
+    for (int j = 2; j <= m; ++j) {
+      T *Tn = (j == 2) ? vTb : const_cast<T *>(Tp);
+      const T bj = P.coef[j];
+      const bool last = (j == m);
+      sweep([&](int jj) { return Tc[jj]; },
+            [&](int li, int i, T acc, int q) {
+              if (q != 0) return;
+              const T tc = Tc[i];
+              const T At = fma(ldiag[li], tc, acc);
+              const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[i];  // Tp[i] read before Tn[i] (may alias) is written
+              const T v = fma(bj, tn, x[i]);
+              if (!last) put(Tn, i, tn);
+              if (last) put(x, i, v);
+              else x[i] = v;
+            });
+      cl.sync();
+      Tp = Tc;
+      Tc = Tn;
+    }
+  };
+
+  // the inner flexible CG at level k0+1 (nu steps, preconditioner B) on
+  // hb; result in hx (full copy)
+  auto inner_coarse = [&]() {
+    if (tid == 0) scH[12] = 0.0;  // stop flag (read after the next barrier)
+    for (int it = 0; it < nu; ++it) {
+      const T *rin = (it == 0) ? hb : hr;
+      T *D = vec(A_HD0 + it), *W = vec(A_HW0 + it);
+      // D = B rin (fp64), one warp per owned row
+      for (int base = 0; base < P.RH; base += kLeafWarps) {
+        const int lI = base + warp;
+        const bool ok = lI < nlocH;
+        double acc = 0.0;
+        if (ok)
+          for (int j = lane; j < nH; j += 32) acc = fma(brows[(size_t)lI * nH + j], (double)rin[j], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (ok && lane < C) *cl.map_shared_rank(D + h0 + lI, (unsigned)lane) = (T)acc;
+      }
+      cl.sync();
+      double dv[kLeafSlot] = {};
+      // W = A D with rho = D.W, sigma = rin.D (step 0) or D_l.W (step > 0)
+      sweepH([&](int j) { return D[j]; },
+             [&](int lI, int I, T acc, int q) {
+               if (q != 0) return;
+               const T w = fma(hdiag[lI], D[I], acc);
+               W[lI] = w;
+               if (it == 0) {
+                 dv[0] += (double)D[I] * (double)w;
+                 dv[1] += (double)rin[I] * (double)D[I];
+               } else {
+#pragma unroll
+                 for (int l = 0; l < kLeafMaxInner; ++l)
+                   if (l < it) dv[l] += (double)vec(A_HD0 + l)[I] * (double)w;
+               }
+             });
+      post(dv, it == 0 ? 2 : it);
+      cl.sync();
+      fold(sums, it == 0 ? 2 : it);
+      if (it == 0) {
+        if (tid == 0) fin_alpha(scH, 0);
+      } else {
+        if (tid < it) scH[8 + tid] = sums[tid] / scH[tid];  // beta_l
+        __syncthreads();
+        // D -= sum beta_l D_l, W -= sum beta_l W_l; rho = D.W, sigma = D.rin
+        double ev[kLeafSlot] = {};
+        for (int lI = tid; lI < nlocH; lI += kLeafThreads) {
+          const int I = h0 + lI;
+          T d = D[I], w = W[lI];
+#pragma unroll
+          for (int l = 0; l < kLeafMaxInner; ++l) {
+            if (l < it) {
+              const T bl = (T)scH[8 + l];
+              d -= bl * vec(A_HD0 + l)[I];
+              w -= bl * vec(A_HW0 + l)[lI];
+            }
+          }
+          D[I] = d;
+          W[lI] = w;
+          ev[0] += (double)d * (double)w;
+          ev[1] += (double)d * (double)rin[I];
+        }
+        post(ev, 2);
+        cl.sync();
+        fold(sums, 2);
+        if (tid == 0) fin_alpha(scH, it);
+      }
+      __syncthreads();
+      // x = alpha D (it 0) or x += alpha D; r = rin - alpha W before another step
+      const bool here = scH[12] != 0.0 && scH[4 + it] == 0.0;
+      const T a = (T)scH[4 + it];
+      const bool upd_r = it + 1 < nu, last = it + 1 == nu;
+      for (int lI = tid; lI < nlocH; lI += kLeafThreads) {
+        const int I = h0 + lI;
+        T xv;
+        if (it == 0) xv = here ? T(0) : a * D[I];
+        else xv = here ? hx[I] : fma(a, D[I], hx[I]);
+        if (last) put(hx, I, xv);
+        else hx[I] = xv;
+        if (upd_r) put(hr, I, here ? rin[I] : rin[I] - a * W[lI]);
+      }
+      cl.sync();
+    }
+  };
+
+  // x = K_k0(r): the W(1,1) cycle at level k0; r, x full copies
+  auto kcycle = [&](const T *r, T *x) {
+    smooth(r, vu, false);  // u = q_m(A) r
+    // s = r - A u
+    sweep([&](int j) { return vu[j]; },
+          [&](int li, int i, T acc, int q) {
+            if (q == 0) put(vs, i, r[i] - fma(ldiag[li], vu[i], acc));
+          });
+    cl.sync();
+    // r_H = P^T s over the owned aggregates (members in ascending order)
+    for (int lI = tid; lI < nlocH; lI += kLeafThreads) {
+      T acc = T(0);
+      for (int a = lap[lI]; a < lap[lI + 1]; ++a) acc += vs[lam[a]];
+      put(hb, h0 + lI, acc);
+    }
+    cl.sync();
+    inner_coarse();
+    // x = u + P e_H and s = r - A x (neighbours formed on the fly)
+    sweep([&](int j) { return vu[j] + hx[agg[j]]; },
+          [&](int li, int i, T acc, int q) {
+            if (q != 0) return;
+            const T xi = vu[i] + hx[agg[i]];
+            x[i] = xi;
+            put(vs, i, r[i] - fma(ldiag[li], xi, acc));
+          });
+    cl.sync();
+    smooth(vs, x, true);  // x += q_m(A) s, broadcast by its last step
+  };
+
+  // ---- the inner flexible CG at level k0 ----
+  if (tid == 0) scT[12] = 0.0;
+  for (int it = 0; it < nu; ++it) {
+    const T *rin = (it == 0) ? vb : vr;
+    T *D = vec(A_D0 + it), *W = vec(A_W0 + it);
+    kcycle(rin, D);
+    double dv[kLeafSlot] = {};
+    sweep([&](int j) { return D[j]; },
+          [&](int li, int i, T acc, int q) {
+            if (q != 0) return;
+            const T w = fma(ldiag[li], D[i], acc);
+            W[li] = w;
+            if (it == 0) {
+              dv[0] += (double)D[i] * (double)w;
+              dv[1] += (double)rin[i] * (double)D[i];
+            } else {
+#pragma unroll
+              for (int l = 0; l < kLeafMaxInner; ++l)
+                if (l < it) dv[l] += (double)vec(A_D0 + l)[i] * (double)w;
+            }
+          });
+    post(dv, it == 0 ? 2 : it);
+    cl.sync();
+    fold(sums, it == 0 ? 2 : it);
+    if (it == 0) {
+      if (tid == 0) fin_alpha(scT, 0);
+    } else {
+      if (tid < it) scT[8 + tid] = sums[tid] / scT[tid];  // beta_l
+      __syncthreads();
+      double ev[kLeafSlot] = {};
+      for (int li = tid; li < nloc; li += kLeafThreads) {
+        const int i = r0 + li;
+        T d = D[i], w = W[li];
+#pragma unroll
+        for (int l = 0; l < kLeafMaxInner; ++l) {
+          if (l < it) {
+            const T bl = (T)scT[8 + l];
+            d -= bl * vec(A_D0 + l)[i];
+            w -= bl * vec(A_W0 + l)[li];
+          }
+        }
+        D[i] = d;
+        W[li] = w;
+        ev[0] += (double)d * (double)w;
+        ev[1] += (double)d * (double)rin[i];
+      }
+      post(ev, 2);
+      cl.sync();
+      fold(sums, 2);
+      if (tid == 0) fin_alpha(scT, it);
+    }
+    __syncthreads();
+    const bool here = scT[12] != 0.0 && scT[4 + it] == 0.0;
+    const T a = (T)scT[4 + it];
+    const bool upd_r = it + 1 < nu, last = it + 1 == nu;
+    for (int li = tid; li < nloc; li += kLeafThreads) {
+      const int i = r0 + li;
+      T xv;
+      if (it == 0) xv = here ? T(0) : a * D[i];
+      else xv = here ? xo[li] : fma(a, D[i], xo[li]);
+      xo[li] = xv;
+      if (last) P.x[i] = xv;
+      if (upd_r) put(vr, i, here ? rin[i] : rin[i] - a * W[li]);
+    }
+    cl.sync();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename T>
+static void *kernel_ptr() {
+  return (void *)k_leaf<T>;
+}
+
+// The kernel attributes are process-wide state of the function: set them
+// once per device, to the largest shared-memory size the device allows, so
+// that handles set up concurrently (the server's slots) never lower the
+// limit under another handle's launch.
+template <typename T>
+static amg_status leaf_attrs(int device, int optin, bool *nonportable, int *max_dynamic) {
+  static std::mutex mu;
+  static bool done[64], np_ok[64];
+  static int dyn[64];
+  if (device < 0 || device >= 64) return fail(AMG_ERR_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done[device]) {
+    void *kern = kernel_ptr<T>();
+    cudaFuncAttributes fa{};
+    AMG_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    dyn[device] = optin - (int)fa.sharedSizeBytes;  // the kernel's static shared memory counts too
+    AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn[device]));
+    np_ok[device] = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    if (!np_ok[device]) cudaGetLastError();
+    done[device] = true;
+  }
+  *nonportable = np_ok[device];
+  *max_dynamic = dyn[device];
+  return AMG_OK;
+}
+
+template <typename T>
+static amg_status prepare_t(amg_handle_s *h, int k0) {
+  const Level &L = h->lv[k0];
+  const Level &N = h->lv[k0 + 1];
+  const int n = L.n, nH = N.n;
+  std::vector<int64_t> rp(n + 1), rpH(nH + 1);
+  std::vector<int32_t> ap(nH + 1);
+  AMG_CUDA_TRY(cudaMemcpyAsync(rp.data(), L.A.rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(rpH.data(), N.A.rowptr, sizeof(int64_t) * (nH + 1), cudaMemcpyDeviceToHost, h->stream));
+  AMG_CUDA_TRY(cudaMemcpyAsync(ap.data(), L.agg_ptr, sizeof(int32_t) * (nH + 1), cudaMemcpyDeviceToHost, h->stream));
+  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  int optin = 0;
+  AMG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  void *kern = kernel_ptr<T>();
+  bool nonportable = false;
+  int max_dynamic = 0;
+  AMG_TRY(leaf_attrs<T>(h->device, optin, &nonportable, &max_dynamic));
+  for (int C : {kLeafMaxC, 8, 4, 2, 1}) {
+    LeafParams<T> P{};
+    P.n = n;
+    P.nH = nH;
+    P.C = C;
+    P.R = (n + C - 1) / C;
+    P.RH = (nH + C - 1) / C;
+    P.m = h->opt.degree;
+    P.nu = h->opt.inner_iters;
+    int tpr = 8;
+    while (tpr > 1 && P.R * tpr > kLeafThreads) tpr >>= 1;
+    int tprH = 8;
+    while (tprH > 1 && P.RH * tprH > kLeafThreads) tprH >>= 1;
+    P.tpr = tpr;
+    P.tprH = tprH;
+    for (int c = 0; c < C; ++c) {
+      const int a = std::min(n, c * P.R), b = std::min(n, (c + 1) * P.R);
+      const int aH = std::min(nH, c * P.RH), bH = std::min(nH, (c + 1) * P.RH);
+      P.maxnz = std::max(P.maxnz, (int)(rp[b] - rp[a]));
+      P.maxnzH = std::max(P.maxnzH, (int)(rpH[bH] - rpH[aH]));
+      P.maxmem = std::max(P.maxmem, ap[bH] - ap[aH]);
+    }
+    if (leaf_layout(P) > (unsigned)max_dynamic) continue;
+    if (C > 8 && !nonportable) continue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kLeafThreads);
+    cfg.dynamicSmemBytes = P.smem;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    P.sa = (T)(2.0 / (L.lam1 - L.lam0));
+    P.ca = (T)((L.lam1 + L.lam0) / (L.lam1 - L.lam0));
+    for (int j = 0; j <= P.m; ++j) P.coef[j] = (T)L.coef[j];
+    P.rp = L.A.rowptr;
+    P.col = L.A.col;
+    P.val = L.A.val;
+    P.diag = L.diag;
+    P.agg = L.agg;
+    P.agg_ptr = L.agg_ptr;
+    P.agg_mem = L.agg_mem;
+    P.rpH = N.A.rowptr;
+    P.colH = N.A.col;
+    P.valH = N.A.val;
+    P.diagH = N.diag;
+    P.B = h->Bd;
+    P.b = (const T *)L.b;
+    P.x = (T *)L.x;
+    LeafParams<T> *hp = new LeafParams<T>(P);
+    h->leaf_params = hp;
+    h->leaf_free = [](void *p) { delete static_cast<LeafParams<T> *>(p); };
+    h->leaf_k = k0;
+    h->leaf_csize = C;
+    return AMG_OK;
+  }
+  return AMG_OK;  // nothing fits: the multi-kernel path stays in use
+}
+
+// Use the leaf kernel for the inner solve at level Bk - 1 when the level is
+// small enough for every CTA to hold its vectors in shared memory.
+// AMG_GB300_LEAF=0 keeps the multi-kernel path.
+amg_status prepare_leaf(amg_handle_s *h) {
+  h->leaf_k = -1;
+  const char *env = getenv("AMG_GB300_LEAF");
+  if (env && env[0] == '0') return AMG_OK;
+  const int k0 = h->Bk - 1;
+  if (h->Bk < 0 || k0 < 1 || h->tail_k0 >= 0) return AMG_OK;
+  if (h->opt.inner_iters > kLeafMaxInner || h->opt.degree > kMaxDegree) return AMG_OK;
+  if (h->lv[k0].n > kLeafMaxRows || h->lv[k0 + 1].n > kLeafMaxCoarse) return AMG_OK;
+  if (h->opt.precision == AMG_PREC_FP32) return prepare_t<float>(h, k0);
+  return prepare_t<double>(h, k0);
+}
+
+template <typename T>
+static amg_status launch_t(amg_handle_s *h) {
+  const LeafParams<T> &P = *static_cast<const LeafParams<T> *>(h->leaf_params);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3(P.C);
+  cfg.blockDim = dim3(kLeafThreads);
+  cfg.dynamicSmemBytes = P.smem;
+  cfg.stream = h->stream;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = P.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_leaf<T>, P);
+  ++h->launches;
+  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("leaf kernel launch: ") + cudaGetErrorString(e));
+  return AMG_OK;
+}
+
+amg_status launch_leaf(amg_handle_s *h) {
+  if (h->opt.precision == AMG_PREC_FP32) return launch_t<float>(h);
+  return launch_t<double>(h);
+}
+
+}  // namespace amg

@@ -653,6 +653,7 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
                   N.scal + 24));
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
+  else if (k + 1 == h->leaf_k) AMG_TRY(launch_leaf(h));
   else if (k + 1 == h->tail_k0) AMG_TRY(launch_tail(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
   AMG_TRY(with_wps(L.wps, [&](auto W) {
