@@ -99,6 +99,10 @@ struct Sell {  // SELL-32 off-diagonal part + diagonal
   float *val32 = nullptr;
   double *diag64 = nullptr;
   float *diag32 = nullptr;
+  // the smoother's operator 2 t(A) = 2 sa A - 2 ca I on the same pattern:
+  // off-diagonal values times 2 sa, diagonal 2 sa a_ii - 2 ca
+  double *sval64 = nullptr, *sdiag64 = nullptr;
+  float *sval32 = nullptr, *sdiag32 = nullptr;
 };
 
 template <typename T>

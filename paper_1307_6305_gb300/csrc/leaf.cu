@@ -580,6 +580,11 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     while (tpr > 1 && P.R * tpr > kLeafThreads) tpr >>= 1;
     int tprH = 8;
     while (tprH > 1 && P.RH * tprH > kLeafThreads) tprH >>= 1;
+    // AMG_GB300_LEAF_TPR=1|2|4|8 overrides the lanes per row on level k0
+    if (const char *e = getenv("AMG_GB300_LEAF_TPR")) {
+      const int v = atoi(e);
+      if (v == 1 || v == 2 || v == 4 || v == 8) tpr = v;
+    }
     P.tpr = tpr;
     P.tprH = tprH;
     for (int c = 0; c < C; ++c) {

@@ -95,55 +95,66 @@ __device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &
   return lead && ix.i < A.n;
 }
 
-// T_1 = t(A) r with t(A) = sa*A - ca*I; x (=|+=) b0*r + b1*T_1
+// The Chebyshev kernels take the smoother form S = 2 t(A) = 2 sa A - 2 ca I
+// (stored once per level), so that a recurrence step is one SpMV and one
+// subtraction: T_{j+1} = S T_j - T_{j-1}, and T_1 = S r / 2 (exact halving).
+
+// T_1 = t(A) r; x (=|+=) b0*r + b1*T_1
 template <typename T, bool ADD, int WPS>
-__global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> A, const T *__restrict__ r,
-                                                         T *__restrict__ T1, T *__restrict__ x, T sa,
-                                                         T ca, T b0, T b1) {
+__global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> S, const T *__restrict__ r,
+                                                         T *__restrict__ T1, T *__restrict__ x, T b0, T b1) {
   pdl_sync();
   int i;
-  T Ar;
+  T Sr;
   if constexpr (WPS == 1) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    Ar = apply_row(A, r, i);
+    if (i >= S.n) return;
+    Sr = apply_row(S, r, i);
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
     i = ix.i;
-    const T xi = i < A.n ? r[i] : T(0);
-    if (!split_row<T, WPS>(A, ix, xi, [&](int j) { return r[j]; }, Ar, part)) return;
+    const T xi = i < S.n ? r[i] : T(0);
+    if (!split_row<T, WPS>(S, ix, xi, [&](int j) { return r[j]; }, Sr, part)) return;
   }
   const T ri = r[i];
-  const T t1 = fma(sa, Ar, -ca * ri);
+  const T t1 = T(0.5) * Sr;
   T1[i] = t1;
   const T inc = fma(b1, t1, b0 * ri);
   x[i] = ADD ? x[i] + inc : inc;
 }
 
-// T_{j+1} = 2 t(A) T_j - T_{j-1}; x += bj * T_{j+1}.  Tn may alias Tp.
+// T_{j+1} = S T_j - T_{j-1}; x += bj * T_{j+1}.  Tn may alias Tp.
 template <typename T, int WPS>
-__global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> A, const T *__restrict__ Tc,
-                                                        const T *Tp, T *Tn, T *__restrict__ x, T sa,
-                                                        T ca, T bj) {
+__global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> S, const T *__restrict__ Tc,
+                                                        const T *Tp, T *Tn, T *__restrict__ x, T bj) {
   pdl_sync();
   int i;
-  T At;
+  T St;
   if constexpr (WPS == 1) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    At = apply_row(A, Tc, i);
+    if (i >= S.n) return;
+    St = apply_row(S, Tc, i);
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
     i = ix.i;
-    const T xi = i < A.n ? Tc[i] : T(0);
-    if (!split_row<T, WPS>(A, ix, xi, [&](int j) { return Tc[j]; }, At, part)) return;
+    const T xi = i < S.n ? Tc[i] : T(0);
+    if (!split_row<T, WPS>(S, ix, xi, [&](int j) { return Tc[j]; }, St, part)) return;
   }
-  const T tc = Tc[i];
-  const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[i];
+  const T tn = St - Tp[i];
   Tn[i] = tn;
   x[i] = fma(bj, tn, x[i]);
+}
+
+// smoother form of one level: sval = 2 sa val, sdiag = 2 sa diag - 2 ca
+template <typename T>
+__global__ void k_smoother_form(int64_t stored, int n, const double *__restrict__ val,
+                                const double *__restrict__ diag, double two_sa, double two_ca,
+                                T *__restrict__ sval, T *__restrict__ sdiag) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < stored) sval[e] = (T)(two_sa * val[e]);
+  if (e < n) sdiag[e] = (T)(two_sa * diag[e] - two_ca);
 }
 
 template <typename T, bool ADD>

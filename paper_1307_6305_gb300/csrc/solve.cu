@@ -404,6 +404,17 @@ SellView<float> view<float>(const amg::Level &L) {
 }
 
 template <typename T>
+static SellView<T> smoother_view(const amg::Level &L);
+template <>
+SellView<double> smoother_view<double>(const amg::Level &L) {
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64};
+}
+template <>
+SellView<float> smoother_view<float>(const amg::Level &L) {
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32};
+}
+
+template <typename T>
 static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin fin) {
   const unsigned g = red_grid(n);
   double *P = h->red.partial;
@@ -494,9 +505,7 @@ template <typename T>
 static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
   amg::Level &L = h->lv[k];
   const int m = h->opt.degree;
-  const SellView<T> A = view<T>(L);
-  const T sa = (T)(2.0 / (L.lam1 - L.lam0));
-  const T ca = (T)((L.lam1 + L.lam0) / (L.lam1 - L.lam0));
+  const SellView<T> S = smoother_view<T>(L);  // 2 t(A) = 2 sa A - 2 ca I
   cudaStream_t st = h->stream;
   if (m == 0) {
     if (add) AMG_TRY(plaunch(h, st, k_scale<T, true>, dim3(nblk(L.n)), dim3(kThreads), L.n, r, x, (T)L.coef[0]));
@@ -508,8 +517,8 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
   const dim3 grid(sell_grid(L.n, L.wps));
   AMG_TRY(with_wps(L.wps, [&](auto W) {
     constexpr int wp = decltype(W)::value;
-    if (add) return plaunch(h, st, k_cheb_first<T, true, wp>, grid, dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
-    return plaunch(h, st, k_cheb_first<T, false, wp>, grid, dim3(kThreads), A, r, Ta, x, sa, ca, (T)L.coef[0], (T)L.coef[1]);
+    if (add) return plaunch(h, st, k_cheb_first<T, true, wp>, grid, dim3(kThreads), S, r, Ta, x, (T)L.coef[0], (T)L.coef[1]);
+    return plaunch(h, st, k_cheb_first<T, false, wp>, grid, dim3(kThreads), S, r, Ta, x, (T)L.coef[0], (T)L.coef[1]);
   }));
   SLAUNCH(h);
   const T *Tp = r;
@@ -520,7 +529,7 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     cudaEvent_t e0, e1;
     if (timed) AMG_TRY(timing_record(h, &e0));
     AMG_TRY(with_wps(L.wps, [&](auto W) {
-      return plaunch(h, st, k_cheb_step<T, decltype(W)::value>, grid, dim3(kThreads), A, Tc, Tp, Tn, x, sa, ca, (T)L.coef[j]);
+      return plaunch(h, st, k_cheb_step<T, decltype(W)::value>, grid, dim3(kThreads), S, Tc, Tp, Tn, x, (T)L.coef[j]);
     }));
     SLAUNCH(h);
     if (timed) AMG_TRY(timing_record(h, &e1));
@@ -759,6 +768,24 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     const size_t n = (size_t)std::max(V.n, 1);
     V.wps = split ? choose_wps(V.n) : 1;
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
+    if (k < L - 1 && h->opt.degree > 0) {
+      // the smoother form 2 t(A) of this level (Chebyshev kernels)
+      amg::Sell &S = V.S;
+      const double two_sa = 4.0 / (V.lam1 - V.lam0), two_ca = 2.0 * (V.lam1 + V.lam0) / (V.lam1 - V.lam0);
+      const int64_t stored = std::max<int64_t>(S.stored, 1), cnt = std::max<int64_t>(S.stored, V.n);
+      if (f32) {
+        AMG_TRY(h->arena.alloc((void **)&S.sval32, sizeof(float) * stored));
+        AMG_TRY(h->arena.alloc((void **)&S.sdiag32, sizeof(float) * n));
+        k_smoother_form<float><<<nblk(cnt), kThreads, 0, h->stream>>>(S.stored, V.n, S.val64, V.diag, two_sa, two_ca,
+                                                                        S.sval32, S.sdiag32);
+      } else {
+        AMG_TRY(h->arena.alloc((void **)&S.sval64, sizeof(double) * stored));
+        AMG_TRY(h->arena.alloc((void **)&S.sdiag64, sizeof(double) * n));
+        k_smoother_form<double><<<nblk(cnt), kThreads, 0, h->stream>>>(S.stored, V.n, S.val64, V.diag, two_sa, two_ca,
+                                                                         S.sval64, S.sdiag64);
+      }
+      SLAUNCH(h);
+    }
     if (k < L - 1) {
       AMG_TRY(h->arena.alloc(&V.u, es * n));
       AMG_TRY(h->arena.alloc(&V.s, es * n));
