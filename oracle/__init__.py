@@ -43,7 +43,8 @@ class Options(C.Structure):
     _fields_ = [("degree", C.c_int), ("passes", C.c_int), ("coarse_max", C.c_int),
                 ("max_levels", C.c_int), ("inner_iters", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precond", C.c_int), ("lambda0_ratio", C.c_double),
-                ("hash_salt", C.c_uint64)]
+                ("hash_salt", C.c_uint64), ("cycle", C.c_int), ("amli_alpha", C.c_double),
+                ("rho", C.c_double)]
 
 
 class Info(C.Structure):
@@ -79,8 +80,11 @@ def lib():
             L.orc_level_pass_agg.argtypes = [C.c_void_p, C.c_int, C.c_int, P]
             L.orc_level_lambda.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.orc_level_cheb.argtypes = [C.c_void_p, C.c_int, P]
+            L.orc_amli_coef.argtypes = [C.c_void_p, P]
+            L.orc_degree_for.argtypes = [C.c_double, C.c_double]
+            L.orc_degree_for.restype = C.c_int
             for name in ("orc_spmv", "orc_smooth", "orc_restrict", "orc_prolong_add", "orc_kcycle",
-                         "orc_inner_fcg"):
+                         "orc_inner_fcg", "orc_amli_cycle"):
                 getattr(L, name).argtypes = [C.c_void_p, C.c_int, P, P]
             L.orc_coarse_solve.argtypes = [C.c_void_p, P, P]
             _lib = L
@@ -110,6 +114,11 @@ def match(rowptr, col, w, salt: int = 0):
     rounds = C.c_int(0)
     nH = lib().orc_match(n, _p(rowptr), _p(col), _p(w), C.c_uint64(salt), _p(mate), _p(agg), C.byref(rounds))
     return mate, agg, nH, rounds.value
+
+
+def degree_for(rho: float, lambda0_ratio: float = 0.1) -> int:
+    """Smoother degree from Eq. (bound-on-m): smallest m with E_m <= rho and E_m < 1 (-1: none)."""
+    return lib().orc_degree_for(rho, lambda0_ratio)
 
 
 def remez_inverse(m: int, l0: float, l1: float):
@@ -160,6 +169,8 @@ class Hierarchy:
                                       C.byref(self.opts), C.byref(h))
         self.h = h if self.status == 0 else None
         self.n = g.n
+        if self.status == 0 and self.opts.rho > 0:  # the degree the hierarchy uses
+            self.opts.degree = degree_for(self.opts.rho, self.opts.lambda0_ratio)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -248,6 +259,16 @@ class Hierarchy:
 
     def kcycle(self, k, r):
         return self._op("orc_kcycle", k, r, self.level_n(k))
+
+    def amli_cycle(self, k, r):
+        """x = B_k r, the stationary AMLI W-cycle (cycle=1 hierarchies)."""
+        return self._op("orc_amli_cycle", k, r, self.level_n(k))
+
+    def amli_coef(self) -> np.ndarray:
+        c = np.zeros(self.opts.inner_iters)
+        if lib().orc_amli_coef(self.h, _p(c)):
+            raise RuntimeError("not an AMLI-cycle hierarchy")
+        return c
 
     def inner_fcg(self, k, b):
         return self._op("orc_inner_fcg", k, b, self.level_n(k))

@@ -61,6 +61,8 @@ struct orc_hier {
   /* dense eigen-decomposition of A_0 for ORC_PREC_EXACT */
   double *x_ev;
   double *x_U;
+  /* stationary AMLI cycle: Chebyshev coefficients of q_{nu-1} on [alpha, 1] */
+  double amli_cheb[64];
 };
 
 void orc_default_options(orc_options *o) {
@@ -74,6 +76,9 @@ void orc_default_options(orc_options *o) {
   o->precond = ORC_PREC_KCYCLE;
   o->lambda0_ratio = 0.1;
   o->hash_salt = 0;
+  o->cycle = ORC_CYCLE_K;
+  o->amli_alpha = 0.25;
+  o->rho = 0.0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -552,8 +557,16 @@ int orc_setup(int64_t n, const int64_t *rowptr, const int32_t *col, const double
   *out = NULL;
   orc_options opt;
   if (optin) opt = *optin; else orc_default_options(&opt);
+  if (!(opt.rho >= 0.0) || !isfinite(opt.rho) || (opt.cycle != ORC_CYCLE_K && opt.cycle != ORC_CYCLE_AMLI) ||
+      !(opt.amli_alpha > 0.0 && opt.amli_alpha < 1.0))
+    return ORC_ERR_INVALID_ARG;
+  if (opt.rho > 0.0) {
+    if (!(opt.lambda0_ratio > 0.0 && opt.lambda0_ratio < 1.0)) return ORC_ERR_INVALID_ARG;
+    opt.degree = orc_degree_for(opt.rho, opt.lambda0_ratio);
+    if (opt.degree < 0) return ORC_ERR_INVALID_ARG;
+  }
   if (opt.degree < 0 || opt.degree > 30 || opt.passes < 1 || opt.passes > 16 || opt.coarse_max < 1 ||
-      opt.max_levels < 1 || opt.inner_iters < 1 || opt.restart < 1 || opt.max_iters < 0 ||
+      opt.max_levels < 1 || opt.inner_iters < 1 || opt.inner_iters > 60 || opt.restart < 1 || opt.max_iters < 0 ||
       !(opt.lambda0_ratio > 0.0 && opt.lambda0_ratio < 1.0))
     return ORC_ERR_INVALID_ARG;
   if (n > 2147483647LL) return ORC_ERR_INVALID_ARG;
@@ -568,6 +581,22 @@ int orc_setup(int64_t n, const int64_t *rowptr, const int32_t *col, const double
   orc_hier *h = (orc_hier *)calloc(1, sizeof(orc_hier));
   h->opt = opt;
   h->pure = pure;
+  /* the AMLI polynomial q_{nu-1}: best uniform approximation to 1/t on
+   * [alpha, 1] (Sec. 4 with the construction of Sec. 3 applied to the
+   * preconditioned coarse operator) */
+  if (opt.cycle == ORC_CYCLE_AMLI) {
+    /* E = delta^(nu-1) (kappa - 1)/2, kappa = 1/alpha, bounds |1 - t q(t)| on
+     * [alpha, 1] (Sec. 3 with lambda1 = 1).  E < 1 (the positivity condition)
+     * and the scaling q / (1 + E) give 0 < t q(t) <= 1 there, so that by
+     * induction every B_k is SPD with the spectrum of B_k A_k in (0, 1] */
+    double kap = 1.0 / opt.amli_alpha, del = (sqrt(kap) - 1.0) / (sqrt(kap) + 1.0);
+    double E = pow(del, (double)(opt.inner_iters - 1)) * (kap - 1.0) / 2.0;
+    if (!(E < 1.0) || orc_remez_inverse(opt.inner_iters - 1, opt.amli_alpha, 1.0, h->amli_cheb, NULL, NULL)) {
+      free(h);
+      return ORC_ERR_INVALID_ARG;
+    }
+    for (int p = 0; p < opt.inner_iters; ++p) h->amli_cheb[p] /= 1.0 + E;
+  }
   /* level 0: assemble A from (w, d), Eq. (1) */
   orc_mat *A0 = &h->lv[0].A;
   int64_t nnz = rowptr[n];
@@ -864,6 +893,80 @@ int orc_inner_fcg(const orc_hier *h, int k, const double *b, double *x) {
   return ORC_OK;
 }
 
+/* Stationary AMLI W-cycle at level k < L-1 (Sec. 4: "AMLI-cycle"): the
+ * two-level steps of orc_kcycle with the coarse problem solved by a fixed
+ * polynomial instead of inner flexible CG:
+ *   e_H = q(B_{k+1} A_{k+1}) B_{k+1} r_H   (k+1 < L-1),  e_H = A_c^+ r_H (k+1 = L-1),
+ * q = q_{nu-1} / (1 + E), q_{nu-1} the best uniform approximation to 1/t on
+ * [alpha, 1] and E its error bound (see orc_setup), in the Chebyshev basis of
+ * tau(t) = (2t - 1 - alpha)/(1 - alpha), evaluated by the
+ * forward recurrence T_0 = B r_H, T_1 = tau(BA) T_0,
+ * T_{p+1} = 2 tau(BA) T_p - T_{p-1}; each tau(BA) costs one SpMV with A_{k+1}
+ * and one application of B_{k+1} (nu applications of B_{k+1} in all: a
+ * W-cycle for nu = 2).  B_k is linear and symmetric. */
+static void amli_coarse(const orc_hier *h, int j, const double *rH, double *eH) {
+  const orc_level *lv = &h->lv[j];
+  int64_t n = lv->A.n;
+  int deg = h->opt.inner_iters - 1;
+  double a = h->opt.amli_alpha;
+  double *Tp = vnew(n), *Tc = vnew(n), *Tn = vnew(n), *v = vnew(n), *w = vnew(n);
+  orc_amli_cycle(h, j, rH, Tc); /* T_0 = B r_H */
+  for (int64_t i = 0; i < n; ++i) eH[i] = h->amli_cheb[0] * Tc[i];
+  for (int p = 1; p <= deg; ++p) {
+    /* w = B A T_{p-1}; tau(BA) T_{p-1} = (2 w - (1 + a) T_{p-1}) / (1 - a) */
+    mat_spmv(&lv->A, Tc, v);
+    orc_amli_cycle(h, j, v, w);
+    for (int64_t i = 0; i < n; ++i) {
+      double t = (2.0 * w[i] - (1.0 + a) * Tc[i]) / (1.0 - a);
+      Tn[i] = (p == 1) ? t : 2.0 * t - Tp[i];
+    }
+    for (int64_t i = 0; i < n; ++i) eH[i] += h->amli_cheb[p] * Tn[i];
+    double *t = Tp; Tp = Tc; Tc = Tn; Tn = t;
+  }
+  free(Tp); free(Tc); free(Tn); free(v); free(w);
+}
+
+int orc_amli_cycle(const orc_hier *h, int k, const double *r, double *x) {
+  if (!h || k < 0 || k >= h->L) return ORC_ERR_INVALID_ARG;
+  if (k == h->L - 1) return orc_coarse_solve(h, r, x);
+  const orc_level *lv = &h->lv[k];
+  int64_t n = lv->A.n, nH = lv->nH;
+  double *s = vnew(n), *y = vnew(n), *rH = vnew(nH), *eH = vnew(nH);
+  orc_smooth(h, k, r, x);
+  mat_spmv(&lv->A, x, s);
+  for (int64_t i = 0; i < n; ++i) s[i] = r[i] - s[i];
+  orc_restrict(h, k, s, rH);
+  if (k + 1 == h->L - 1) orc_coarse_solve(h, rH, eH);
+  else amli_coarse(h, k + 1, rH, eH);
+  orc_prolong_add(h, k, eH, x);
+  mat_spmv(&lv->A, x, s);
+  for (int64_t i = 0; i < n; ++i) s[i] = r[i] - s[i];
+  orc_smooth(h, k, s, y);
+  for (int64_t i = 0; i < n; ++i) x[i] += y[i];
+  free(s); free(y); free(rH); free(eH);
+  return ORC_OK;
+}
+
+int orc_amli_coef(const orc_hier *h, double *coef) {
+  if (!h || !coef || h->opt.cycle != ORC_CYCLE_AMLI) return ORC_ERR_INVALID_ARG;
+  for (int p = 0; p < h->opt.inner_iters; ++p) coef[p] = h->amli_cheb[p];
+  return ORC_OK;
+}
+
+/* Eq. (bound-on-m) read as: the smallest m whose error E_m = delta^m
+ * (kappa - 1)/2 of the smoother polynomial (Sec. 3) is at most rho and
+ * below 1 (the positivity condition), kappa = lambda1/lambda0 */
+int orc_degree_for(double rho, double lambda0_ratio) {
+  if (!(rho > 0.0) || !(lambda0_ratio > 0.0 && lambda0_ratio < 1.0)) return -1;
+  double kappa = 1.0 / lambda0_ratio;
+  double delta = (sqrt(kappa) - 1.0) / (sqrt(kappa) + 1.0);
+  for (int m = 0; m <= 30; ++m) {
+    double e = pow(delta, (double)m) * (kappa - 1.0) / 2.0;
+    if (e <= rho && e < 1.0) return m;
+  }
+  return -1;
+}
+
 /* ------------------------------------------------------------------ */
 /* outer flexible CG (Sec. 4: the N-AMLI cycle preconditions NPCG on the */
 /* finest level, restarted every five iterations).  Iteration k:         */
@@ -905,6 +1008,7 @@ int orc_solve(orc_hier *h, const double *bin, double *x, double tol, orc_info *i
     double *d = D[nwin], *q = Q[nwin];
     if (h->opt.precond == ORC_PREC_IDENTITY) memcpy(z, r, sizeof(double) * (size_t)n);
     else if (h->opt.precond == ORC_PREC_EXACT) eig_pinv_apply(n, h->x_ev, h->x_U, r, z);
+    else if (h->opt.cycle == ORC_CYCLE_AMLI) orc_amli_cycle(h, 0, r, z);
     else orc_kcycle(h, 0, r, z);
     for (int j = 0; j < nwin; ++j) beta[j] = dot(n, Q[j], z) / rho[j];
     memcpy(d, z, sizeof(double) * (size_t)n);

@@ -38,6 +38,10 @@ enum {
 
 /* preconditioner choices for the outer flexible CG */
 enum { ORC_PREC_KCYCLE = 0, ORC_PREC_IDENTITY = 1, ORC_PREC_EXACT = 2 };
+/* multilevel cycle behind ORC_PREC_KCYCLE: the nonlinear AMLI cycle (K-cycle,
+ * inner flexible CG on coarse levels) or the stationary AMLI W-cycle (a fixed
+ * polynomial in B_{k+1} A_{k+1} on coarse levels), Sec. 4 */
+enum { ORC_CYCLE_K = 0, ORC_CYCLE_AMLI = 1 };
 
 typedef struct {
   int degree;          /* m, degree of the smoothing polynomial q_m          */
@@ -50,6 +54,12 @@ typedef struct {
   int precond;         /* ORC_PREC_*                                          */
   double lambda0_ratio;/* lambda0 = ratio * lambda1                           */
   uint64_t hash_salt;  /* salt of the matching tie-break hash                 */
+  int cycle;           /* ORC_CYCLE_K or ORC_CYCLE_AMLI                       */
+  double amli_alpha;   /* AMLI polynomial: best approximation to 1/t on
+                          [amli_alpha, 1], degree nu - 1; its error
+                          delta^(nu-1) (1/alpha - 1)/2 must be < 1 (0.25)     */
+  double rho;          /* > 0: degree m from Eq. (bound-on-m) for damping rho;
+                          `degree` is then ignored                            */
 } orc_options;
 
 typedef struct {
@@ -118,6 +128,12 @@ int orc_restrict(const orc_hier *h, int k, const double *s, double *rH);   /* rH
 int orc_prolong_add(const orc_hier *h, int k, const double *eH, double *x);/* x += P eH      */
 int orc_coarse_solve(const orc_hier *h, const double *b, double *x);       /* x = A_c^+ b    */
 int orc_kcycle(const orc_hier *h, int k, const double *r, double *x);      /* x = K_k(r)     */
+int orc_amli_cycle(const orc_hier *h, int k, const double *r, double *x);  /* x = B_k r      */
+/* Chebyshev coefficients (nu entries) of the AMLI polynomial on [alpha, 1] */
+int orc_amli_coef(const orc_hier *h, double *coef);
+/* smallest m with E_m = delta^m (kappa - 1)/2 <= rho and E_m < 1,
+ * kappa = 1 / lambda0_ratio (Eq. bound-on-m); -1 if none up to 30 */
+int orc_degree_for(double rho, double lambda0_ratio);
 int orc_inner_fcg(const orc_hier *h, int k, const double *b, double *x);   /* nu steps       */
 
 #ifdef __cplusplus
