@@ -210,14 +210,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_oracle_step(g, p, b, ncols=None):
+def run_oracle_step(g, p, b, ncols=None, cycle=0):
     """Oracle setup + solve of the first `ncols` right-hand sides (all by default)."""
     import oracle
 
     nr = b.size // g.n
     ncols = nr if ncols is None else min(ncols, nr)
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"])
+    h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"], cycle=cycle)
     for j in range(ncols):
         r = h.solve(b[j * g.n:(j + 1) * g.n], tol=1e-8)
         assert r.status == 0, r.status
@@ -238,7 +238,10 @@ def main():
     ap.add_argument("--workload", default="grid3d_128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32: the whole preconditioner in fp32 inside the fp64 outer CG")
+    ap.add_argument("--cycle", default="k", choices=["k", "amli"],
+                    help="k: nonlinear AMLI cycle (K-cycle, default); amli: stationary AMLI W-cycle")
     args = ap.parse_args()
+    CYCLE = 1 if args.cycle == "amli" else 0
     rank, world, local = dist_env()
     if args.workload == "serve":
         return serve_bench(args) if args.impl == "ours" and rank == 0 else 0
@@ -254,14 +257,15 @@ def main():
             return 0
         ncols = 1 if nrhs == 1 else 2          # bounded sample: two of the 32 columns
         for _ in range(args.warmup):
-            run_oracle_step(g, p, b, ncols)
-        times = [run_oracle_step(g, p, b, ncols)[0] for _ in range(args.steps)]
+            run_oracle_step(g, p, b, ncols, CYCLE)
+        times = [run_oracle_step(g, p, b, ncols, CYCLE)[0] for _ in range(args.steps)]
         ms = 1e3 * sum(times) / len(times)
         value = g.n * ncols / (ms / 1e3)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": nrhs},
+                "config": {"workload": WORKLOAD_DESC + ("" if CYCLE == 0 else "; stationary AMLI W-cycle"),
+                           "n": g.n, "nrhs": nrhs},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                                  "sample": f"oracle setup + {ncols} of {nrhs} right-hand sides per step, single thread"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -288,7 +292,7 @@ def main():
     xd = torch.zeros_like(bd)
     in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + b.nbytes
     prec = amg.AMG_PREC_FP32 if args.precision == "fp32" else amg.AMG_PREC_FP64
-    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=prec)
+    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=prec, cycle=CYCLE)
     state = {"launches": 0, "iters": [], "setup_ms": [], "solve_ms": [], "kt": [0, 0.0, 0.0]}
 
     def step(timed_kernel: bool):
@@ -348,7 +352,8 @@ def main():
     # the fp32-preconditioner form on the same workload (the metric compares both)
     variant = None
     if args.precision == "fp64" and nrhs == 1 and not args.no_variant:
-        opts32 = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=amg.AMG_PREC_FP32)
+        opts32 = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=amg.AMG_PREC_FP32,
+                                         cycle=CYCLE)
         its = []
 
         def step32():
@@ -428,7 +433,7 @@ def main():
                  "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": flops})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        dt, r, nc = run_oracle_step(g, p, b, 1 if nrhs == 1 else 2)
+        dt, r, nc = run_oracle_step(g, p, b, 1 if nrhs == 1 else 2, CYCLE)
         cpu = {"value": g.n * nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle setup + {nc} of {nrhs} right-hand sides ({r.iterations} iterations), "
                          f"{dt:.1f} s single thread"}
@@ -437,7 +442,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 preconditioner / f64 outer",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "n": g.n, "nrhs": nrhs, "nnz_offdiag": g.nnz,
+        "config": {"workload": WORKLOAD_DESC + ("" if CYCLE == 0 else "; stationary AMLI W-cycle instead of the K-cycle"),
+                   "n": g.n, "nrhs": nrhs, "nnz_offdiag": g.nnz,
                    "l2": f"inputs {in_bytes / 2**20:.0f} MiB > 129 MiB L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "iterations": state["iters"][-1], "setup_ms_host": statistics.median(state["setup_ms"]),

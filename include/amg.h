@@ -74,7 +74,20 @@ typedef struct {
                           solve stay fp64                                          */
   double lambda0_ratio;/* lambda0 = ratio * ||A_k||_inf (Sec. 4: 1/10)             */
   uint64_t hash_salt;  /* salt of the matching tie-break hash                      */
+  int cycle;           /* AMG_CYCLE_K: nonlinear AMLI cycle (K-cycle), inner
+                          flexible CG on coarse levels.  AMG_CYCLE_AMLI:
+                          stationary AMLI W-cycle (Sec. 4), a fixed polynomial
+                          in B_{k+1} A_{k+1} on coarse levels: e_H =
+                          q(B_{k+1} A_{k+1}) B_{k+1} r_H, q = q_{nu-1}/(1+E) with
+                          q_{nu-1} the best uniform approximation to 1/t on
+                          [amli_alpha, 1] and E = delta^(nu-1)(1/amli_alpha-1)/2
+                          its error bound (Sec. 3), which must be < 1            */
+  double amli_alpha;   /* left end of the AMLI polynomial's interval, (0, 1)     */
+  double rho;          /* > 0: choose m from Eq. (bound-on-m), see
+                          amg_degree_for; `degree` is then ignored              */
 } amg_options;
+
+enum { AMG_CYCLE_K = 0, AMG_CYCLE_AMLI = 1 };
 
 /* Per-solve report (Sec. 4 reports iterations and grid/operator complexity). */
 typedef struct {
@@ -94,8 +107,17 @@ typedef struct {
 } amg_info;
 
 /* Fill *opt with defaults: degree 4, passes 3, coarse_max 64, max_levels 30,
- * inner_iters 2, restart 5, max_iters 500, FP64, lambda0_ratio 0.1, salt 0. */
+ * inner_iters 2, restart 5, max_iters 500, FP64, lambda0_ratio 0.1, salt 0,
+ * AMG_CYCLE_K, amli_alpha 0.25, rho 0. */
 void amg_default_options(amg_options *opt);
+
+/* Smoother degree from Eq. (bound-on-m) (Sec. 3): the smallest m with
+ * E_m = delta^m (kappa - 1)/2 <= rho and E_m < 1, where kappa =
+ * 1/lambda0_ratio and delta = (sqrt(kappa) - 1)/(sqrt(kappa) + 1): the
+ * smoother then damps [lambda0, lambda1] by at least rho and q_m stays
+ * positive.  Returns -1 if rho <= 0, lambda0_ratio is outside (0, 1) or no
+ * m <= 16 suffices.  Host only; needs no GPU. */
+int amg_degree_for(double rho, double lambda0_ratio);
 
 /*
  * Build the hierarchy on the device (Sec. 2-3; setup steps all run in CUDA
@@ -168,7 +190,8 @@ amg_status amg_level_csr(amg_handle h, int k, int64_t *rowptr, int32_t *col, dou
  * Coarse ids rank the aggregates' smallest members.  Host buffer. */
 amg_status amg_level_agg(amg_handle h, int k, int32_t *agg);
 /* Smoother data of level k < levels-1: lambda0, lambda1 = ||A_k||_inf and the
- * degree+1 Chebyshev coefficients of q_m in t = (2x - l1 - l0)/(l1 - l0).
+ * m+1 Chebyshev coefficients of q_m in t = (2x - l1 - l0)/(l1 - l0), m the
+ * handle's degree (amg_degree_for(rho, lambda0_ratio) when rho > 0).
  * Any output pointer may be NULL. */
 amg_status amg_level_smoother(amg_handle h, int k, double *lam0, double *lam1, double *coef);
 
@@ -191,9 +214,10 @@ amg_status amg_apply_restrict(amg_handle h, int k, const double *s, double *rH);
 amg_status amg_apply_prolong_add(amg_handle h, int k, const double *eH, double *x);
 /* x = A_c^+ b on the coarsest level (Sec. 3: pseudo-inverse), fp64. */
 amg_status amg_apply_coarse_solve(amg_handle h, const double *b, double *x);
-/* z = K_k(r): one nonlinear AMLI (K-cycle) application at level k
- * (pre-smooth, residual, restriction, nu inner flexible-CG steps or the
- * coarsest solve, prolongation, residual, post-smooth). */
+/* z = K_k(r): one application of the handle's cycle at level k (pre-smooth,
+ * residual, restriction, then nu inner flexible-CG steps (AMG_CYCLE_K) or
+ * the AMLI polynomial (AMG_CYCLE_AMLI) or the coarsest solve, prolongation,
+ * residual, post-smooth). */
 amg_status amg_apply_kcycle(amg_handle h, int k, const double *r, double *z);
 
 /* One handshake matching pass (Sec. 2) on a device CSR graph whose entries

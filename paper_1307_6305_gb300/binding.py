@@ -32,10 +32,12 @@ AMG_MEM_HOST = 0
 AMG_MEM_DEVICE = 1
 AMG_PREC_FP64 = 0
 AMG_PREC_FP32 = 1
+AMG_CYCLE_K = 0
+AMG_CYCLE_AMLI = 1
 
 # every symbol declared in include/amg.h
 SYMBOLS = [
-    "amg_default_options", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
+    "amg_default_options", "amg_degree_for", "amg_setup", "amg_solve", "amg_free", "amg_last_error",
     "amg_num_levels", "amg_level_n", "amg_level_nnz", "amg_level_csr", "amg_level_agg",
     "amg_level_smoother", "amg_apply_spmv", "amg_apply_smoother", "amg_apply_restrict",
     "amg_apply_prolong_add", "amg_apply_coarse_solve", "amg_apply_kcycle", "amg_match", "amg_match_noalloc",
@@ -49,7 +51,8 @@ class amg_options(C.Structure):
     _fields_ = [("degree", C.c_int), ("passes", C.c_int), ("coarse_max", C.c_int),
                 ("max_levels", C.c_int), ("inner_iters", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precision", C.c_int), ("lambda0_ratio", C.c_double),
-                ("hash_salt", C.c_uint64)]
+                ("hash_salt", C.c_uint64), ("cycle", C.c_int), ("amli_alpha", C.c_double),
+                ("rho", C.c_double)]
 
 
 class amg_info(C.Structure):
@@ -90,6 +93,8 @@ def lib(build_if_missing: bool = True):
             P, I64, I = C.c_void_p, C.c_int64, C.c_int
             L.amg_default_options.argtypes = [C.POINTER(amg_options)]
             L.amg_default_options.restype = None
+            L.amg_degree_for.argtypes = [C.c_double, C.c_double]
+            L.amg_degree_for.restype = C.c_int
             L.amg_setup.argtypes = [I64, P, P, P, P, C.POINTER(amg_options), I, P, C.POINTER(C.c_void_p)]
             L.amg_solve.argtypes = [P, P, P, I, I64, C.c_double, C.POINTER(amg_info)]
             L.amg_free.argtypes = [P]
@@ -150,6 +155,11 @@ class AmgError(RuntimeError):
 
 
 # ---- thin wrappers with the C names ----------------------------------------
+def amg_degree_for(rho: float, lambda0_ratio: float = 0.1) -> int:
+    """Smoother degree of Eq. (bound-on-m) for damping rho (-1: none <= 16)."""
+    return lib().amg_degree_for(rho, lambda0_ratio)
+
+
 def amg_default_options(**overrides) -> amg_options:
     o = amg_options()
     lib().amg_default_options(C.byref(o))
@@ -207,6 +217,8 @@ class Hierarchy:
         self.n = n
         if self.status != AMG_OK:
             self.h = None
+        elif self.opt.rho > 0:  # the degree the handle derived from rho
+            self.opt.degree = amg_degree_for(self.opt.rho, self.opt.lambda0_ratio)
 
     @classmethod
     def from_graph(cls, g, mem_space=AMG_MEM_HOST, stream=None, device="cuda", **opts):

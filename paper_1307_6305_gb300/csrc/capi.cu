@@ -7,6 +7,8 @@
 #include <chrono>
 #include <mutex>
 
+#include <math.h>
+
 #include "common.cuh"
 
 namespace amg {
@@ -83,6 +85,13 @@ using namespace amg;
 
 namespace {
 
+// error bound delta^m (kappa - 1)/2 of the best degree-m approximation to
+// 1/t on [alpha, 1], kappa = 1/alpha (Sec. 3 with lambda1 = 1)
+double amli_error(int m, double alpha) {
+  const double kappa = 1.0 / alpha, delta = (sqrt(kappa) - 1.0) / (sqrt(kappa) + 1.0);
+  return pow(delta, (double)m) * (kappa - 1.0) / 2.0;
+}
+
 amg_status check_options(const amg_options &o) {
   if (o.degree < 0 || o.degree > kMaxDegree) return fail(AMG_ERR_INVALID_ARG, "degree must be in [0, 16]");
   if (o.passes < 1 || o.passes > 16) return fail(AMG_ERR_INVALID_ARG, "passes must be in [1, 16]");
@@ -96,6 +105,18 @@ amg_status check_options(const amg_options &o) {
     return fail(AMG_ERR_INVALID_ARG, "precision must be AMG_PREC_FP64 or AMG_PREC_FP32");
   if (!(o.lambda0_ratio > 0.0 && o.lambda0_ratio < 1.0))
     return fail(AMG_ERR_INVALID_ARG, "lambda0_ratio must be in (0, 1)");
+  if (o.cycle != AMG_CYCLE_K && o.cycle != AMG_CYCLE_AMLI)
+    return fail(AMG_ERR_INVALID_ARG, "cycle must be AMG_CYCLE_K or AMG_CYCLE_AMLI");
+  if (!(o.rho >= 0.0) || !std::isfinite(o.rho)) return fail(AMG_ERR_INVALID_ARG, "rho must be >= 0");
+  if (o.rho > 0.0 && amg_degree_for(o.rho, o.lambda0_ratio) < 0)
+    return fail(AMG_ERR_INVALID_ARG, "no smoother degree <= 16 reaches the damping rho");
+  if (o.cycle == AMG_CYCLE_AMLI) {
+    if (!(o.amli_alpha > 0.0 && o.amli_alpha < 1.0))
+      return fail(AMG_ERR_INVALID_ARG, "amli_alpha must be in (0, 1)");
+    if (!(amli_error(o.inner_iters - 1, o.amli_alpha) < 1.0))
+      return fail(AMG_ERR_INVALID_ARG,
+                  "the AMLI polynomial's error on [amli_alpha, 1] is >= 1: raise amli_alpha or inner_iters");
+  }
   return AMG_OK;
 }
 
@@ -155,6 +176,25 @@ void amg_default_options(amg_options *o) {
   o->precision = AMG_PREC_FP64;
   o->lambda0_ratio = 0.1;
   o->hash_salt = 0;
+  o->cycle = AMG_CYCLE_K;
+  o->amli_alpha = 0.25;
+  o->rho = 0.0;
+}
+
+int amg_degree_for(double rho, double lambda0_ratio) {
+  if (!(rho > 0.0) || !(lambda0_ratio > 0.0 && lambda0_ratio < 1.0)) return -1;
+  const double kappa = 1.0 / lambda0_ratio, delta = (sqrt(kappa) - 1.0) / (sqrt(kappa) + 1.0);
+  auto ok = [&](int m) {
+    const double e = pow(delta, (double)m) * (kappa - 1.0) / 2.0;
+    return e <= rho && e < 1.0;
+  };
+  // E_m <= min(rho, 1): m >= log(2 min(rho, 1) / (kappa - 1)) / log(delta);
+  // then settle the rounding of the logarithms on the condition itself
+  const double x = log(2.0 * std::min(rho, 1.0) / (kappa - 1.0)) / log(delta);
+  int m = x > 0.0 ? (int)std::min(ceil(x), (double)kMaxDegree + 1) : 0;
+  while (m > 0 && ok(m - 1)) --m;
+  while (m <= kMaxDegree && !ok(m)) ++m;
+  return m <= kMaxDegree ? m : -1;
 }
 
 amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *w,
@@ -169,6 +209,7 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   amg_options o;
   if (opt) o = *opt; else amg_default_options(&o);
   AMG_TRY(check_options(o));
+  if (o.rho > 0.0) o.degree = amg_degree_for(o.rho, o.lambda0_ratio);  // Eq. (bound-on-m)
   if (mem_space == AMG_MEM_HOST) {
     if (row_ptr[0] != 0 || row_ptr[n] < 0) return fail(AMG_ERR_INVALID_ARG, "row_ptr must start at 0 and be non-decreasing");
     if (row_ptr[n] > 0 && (!col_idx || !w)) return fail(AMG_ERR_INVALID_ARG, "col_idx and w must be non-NULL");
@@ -254,7 +295,8 @@ amg_status amg_solve(amg_handle h, const double *rhs, double *x, int nrhs, int64
   double *bstage = nullptr, *xstage = nullptr;
   amg_status s = AMG_OK;
   const char *benv = getenv("AMG_GB300_BATCHED");
-  if (nrhs >= 2 && !(benv && benv[0] == '0')) {
+  // the block path implements the K-cycle; AMLI-cycle handles solve column by column
+  if (nrhs >= 2 && !(benv && benv[0] == '0') && h->opt.cycle == AMG_CYCLE_K) {
     // all right-hand sides together (block kernels, per-column scalars)
     const double *bd = rhs;
     double *xd = x;

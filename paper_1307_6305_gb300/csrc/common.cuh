@@ -193,6 +193,10 @@ struct amg_handle_s {
   int Bk = -1;
   double *Bd = nullptr;
   double *bb64 = nullptr, *bx64 = nullptr;
+  // stationary AMLI cycle: Chebyshev coefficients of q = q_{nu-1}/(1+E) on
+  // [alpha, 1] and tau(t) = sA t - sB, sA = 2/(1-alpha), sB = (1+alpha)/(1-alpha)
+  double amli_coef[amg::kMaxInner] = {};
+  double amli_sA = 0.0, amli_sB = 0.0;
   // the inner solve at level leaf_k (= Bk - 1) as one cluster kernel whose
   // vectors live in shared memory (leaf.cu); -1: multi-kernel path
   int leaf_k = -1;

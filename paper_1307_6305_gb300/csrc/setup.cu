@@ -1114,6 +1114,18 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     closed_form_coefficients(h->opt.degree, L.lam0, L.lam1, L.coef);
   }
   pool_free(nrm, st);
+  if (h->opt.cycle == AMG_CYCLE_AMLI) {
+    // the AMLI polynomial: best approximation of degree nu-1 to 1/t on
+    // [alpha, 1], divided by 1 + E (E its error bound) so that 0 < t q(t) <= 1
+    const int dg = h->opt.inner_iters - 1;
+    const double al = h->opt.amli_alpha, kappa = 1.0 / al;
+    const double delta = (sqrt(kappa) - 1.0) / (sqrt(kappa) + 1.0);
+    const double E = pow(delta, (double)dg) * (kappa - 1.0) / 2.0;
+    closed_form_coefficients(dg, al, 1.0, h->amli_coef);
+    for (int p = 0; p <= dg; ++p) h->amli_coef[p] /= 1.0 + E;
+    h->amli_sA = 2.0 / (1.0 - al);
+    h->amli_sB = (1.0 + al) / (1.0 - al);
+  }
   // ---- solve layouts ----
   const bool want32 = h->opt.precision == AMG_PREC_FP32;
   for (int k = 0; k < h->L; ++k) AMG_TRY(build_sell(h, h->lv[k], want32));

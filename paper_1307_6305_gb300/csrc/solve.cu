@@ -346,6 +346,30 @@ __global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const doub
   reduce_and_finalize<1>(acc, partial, ticket, fin);
 }
 
+// stationary AMLI coarse correction e = sum_p c_p T_p(tau(BA)) B r:
+// e = c_0 T_0 (first term)
+template <typename T>
+__global__ void k_amli_first(int64_t n, const T *__restrict__ T0, T *__restrict__ e, T c0) {
+  pdl_sync();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) e[i] = c0 * T0[i];
+}
+
+// one recurrence step: t = tau(BA) T_{p-1} = sA w - sB T_{p-1} with w = B A T_{p-1};
+// T_p = t (p = 1) or 2 t - T_{p-2}; e += c_p T_p
+template <typename T>
+__global__ void k_amli_step(int64_t n, const T *__restrict__ w, const T *__restrict__ Tc,
+                            const T *__restrict__ Tp, T *__restrict__ Tn, T *__restrict__ e, T sA, T sB,
+                            T cp, int first) {
+  pdl_sync();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T t = fma(sA, w[i], -sB * Tc[i]);
+  const T tn = first ? t : T(2) * t - Tp[i];
+  Tn[i] = tn;
+  e[i] = fma(cp, tn, e[i]);
+}
+
 __global__ void k_shift(int64_t n, const double *src, double *dst, const double *mean) {
   pdl_sync();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -674,6 +698,73 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   return AMG_OK;
 }
 
+// x = B_k r: the stationary AMLI W-cycle (Sec. 4).  The two-level steps of
+// the K-cycle, with the coarse problem solved by the fixed polynomial
+// e_H = q(B_{k+1} A_{k+1}) B_{k+1} r_H (amli_coarse) instead of inner flexible CG.
+template <typename T>
+static amg_status amli_coarse(amg_handle_s *h, int j);
+
+template <typename T>
+static amg_status amli_cycle(amg_handle_s *h, int k, const T *r, T *x) {
+  if (k == h->L - 1) return coarse_solve<T>(h, r, x);
+  if (k == h->Bk) return dense_two_level<T>(h, r, x);  // exact coarse solve below: linear, = B
+  amg::Level &L = h->lv[k];
+  amg::Level &N = h->lv[k + 1];
+  cudaStream_t st = h->stream;
+  T *s = (T *)L.s, *u = (T *)L.u;
+  AMG_TRY(smooth<T>(h, k, r, u, false));
+  AMG_TRY(residual<T>(h, k, u, r, s));
+  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b,
+                  (double *)nullptr));
+  SLAUNCH(h);
+  if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
+  else AMG_TRY(amli_coarse<T>(h, k + 1));
+  AMG_TRY(with_wps(L.wps, [&](auto W) {
+    return plaunch(h, st, k_prolong_residual<T, decltype(W)::value>, dim3(sell_grid(L.n, L.wps)), dim3(kThreads),
+                   view<T>(L), L.agg, (const T *)N.x, u, r, x, s);
+  }));
+  SLAUNCH(h);
+  AMG_TRY(smooth<T>(h, k, s, x, true));
+  return AMG_OK;
+}
+
+// level j's x = q(B_j A_j) B_j b with the Chebyshev recurrence in
+// tau(BA) = (2 BA - (1 + alpha) I)/(1 - alpha): T_0 = B b, T_1 = tau T_0,
+// T_{p+1} = 2 tau T_p - T_{p-1}; T_p rotates through D[p mod 3], W[0] holds
+// A T, W[1] holds B A T
+template <typename T>
+static amg_status amli_coarse(amg_handle_s *h, int j) {
+  amg::Level &L = h->lv[j];
+  const int64_t n = L.n;
+  const int deg = h->opt.inner_iters - 1;
+  cudaStream_t st = h->stream;
+  T *e = (T *)L.x, *v = (T *)L.W[0], *w = (T *)L.W[1];
+  auto Tb = [&](int p) { return (T *)L.D[p % 3]; };
+  AMG_TRY(amli_cycle<T>(h, j, (const T *)L.b, Tb(0)));
+  AMG_TRY(plaunch(h, st, k_amli_first<T>, dim3(nblk(n)), dim3(kThreads), n, Tb(0), e, (T)h->amli_coef[0]));
+  SLAUNCH(h);
+  for (int p = 1; p <= deg; ++p) {
+    AMG_TRY(with_wps(L.wps, [&](auto W) {
+      return plaunch(h, st, k_spmv<T, decltype(W)::value>, dim3(sell_grid(L.n, L.wps)), dim3(kThreads), view<T>(L),
+                     Tb(p - 1), v);
+    }));
+    SLAUNCH(h);
+    AMG_TRY(amli_cycle<T>(h, j, v, w));
+    T *Tp = p >= 2 ? Tb(p - 2) : Tb(p - 1);  // unused when p == 1
+    AMG_TRY(plaunch(h, st, k_amli_step<T>, dim3(nblk(n)), dim3(kThreads), n, w, Tb(p - 1), Tp, Tb(p), e,
+                    (T)h->amli_sA, (T)h->amli_sB, (T)h->amli_coef[p], p == 1 ? 1 : 0));
+    SLAUNCH(h);
+  }
+  return AMG_OK;
+}
+
+// the handle's cycle at level k
+template <typename T>
+static amg_status cycle(amg_handle_s *h, int k, const T *r, T *x) {
+  if (h->opt.cycle == AMG_CYCLE_AMLI) return amli_cycle<T>(h, k, r, x);
+  return kcycle<T>(h, k, r, x);
+}
+
 // ---------------------------------------------------------------------------
 // the level above the coarsest as one dense operator
 //
@@ -838,12 +929,12 @@ static amg_status precondition(amg_handle_s *h, const double *r, double *z) {
     const int64_t n = h->n;
     AMG_TRY(plaunch(h, h->stream, k_convert<double, float>, dim3(nblk(n)), dim3(kThreads), n, r, h->r32));
     SLAUNCH(h);
-    AMG_TRY(kcycle<float>(h, 0, h->r32, h->z32));
+    AMG_TRY(cycle<float>(h, 0, h->r32, h->z32));
     AMG_TRY(plaunch(h, h->stream, k_convert<float, double>, dim3(nblk(n)), dim3(kThreads), n, h->z32, z));
     SLAUNCH(h);
     return AMG_OK;
   }
-  return kcycle<double>(h, 0, r, z);
+  return cycle<double>(h, 0, r, z);
 }
 
 // Capture z = K_0(r) on the fixed buffers (or_, oz) as a CUDA graph.  All
@@ -1145,8 +1236,8 @@ amg_status apply_kcycle(amg_handle_s *h, int k, const double *r, double *z) {
   // level k >= 1 reads its input from the level's b buffer when it recurses,
   // so use dedicated copies
   AMG_TRY(run_conv(h, r, L.n, z, L.n, false, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) return kcycle<float>(h, k, (const float *)a, (float *)b);
-    return kcycle<double>(h, k, (const double *)a, (double *)b);
+    if (f32(h)) return cycle<float>(h, k, (const float *)a, (float *)b);
+    return cycle<double>(h, k, (const double *)a, (double *)b);
   }));
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
   return check_tail(h);

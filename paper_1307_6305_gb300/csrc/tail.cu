@@ -576,7 +576,7 @@ amg_status prepare_tail(amg_handle_s *h) {
   }
   h->tail_test_stall = 0;
   if (const char *env = getenv("AMG_GB300_TAIL_TEST_STALL")) h->tail_test_stall = atoi(env);
-  if (max_rows <= 0 || h->L < 3) return AMG_OK;
+  if (max_rows <= 0 || h->L < 3 || h->opt.cycle != AMG_CYCLE_K) return AMG_OK;
   int k0 = -1;
   for (int k = 1; k + 1 < h->L; ++k)
     if (h->lv[k].n <= max_rows) {

@@ -42,6 +42,20 @@ def test_default_options(amg):
     o = amg.amg_default_options()
     assert (o.degree, o.passes, o.coarse_max, o.max_levels, o.inner_iters, o.restart) == (4, 3, 64, 30, 2, 5)
     assert o.precision == amg.AMG_PREC_FP64 and o.lambda0_ratio == 0.1
+    assert o.cycle == amg.AMG_CYCLE_K and o.amli_alpha == 0.25 and o.rho == 0.0
+
+
+def test_degree_for_matches_oracle(amg, orc):
+    """amg_degree_for (library) and the oracle's reading of Eq. (bound-on-m)
+    are separate implementations; they agree wherever m <= 16."""
+    for ratio in (0.02, 0.05, 0.1, 0.2, 0.5):
+        for rho in np.geomspace(1e-4, 2.0, 37):
+            m = orc.degree_for(rho, ratio)
+            want = m if 0 <= m <= 16 else -1
+            assert amg.amg_degree_for(rho, ratio) == want, (rho, ratio)
+    assert amg.amg_degree_for(1 / 3, 0.1) == 4
+    for bad in ((0.0, 0.1), (-1.0, 0.1), (0.3, 0.0), (0.3, 1.0)):
+        assert amg.amg_degree_for(*bad) == -1
 
 
 def test_argument_errors_before_device(amg):
@@ -52,7 +66,9 @@ def test_argument_errors_before_device(amg):
     st, h = amg.amg_setup(g.n, None, col, w)
     assert st == amg.AMG_ERR_INVALID_ARG
     for bad in (dict(degree=-1), dict(degree=17), dict(passes=0), dict(inner_iters=9), dict(restart=0),
-                dict(precision=3), dict(lambda0_ratio=1.5), dict(coarse_max=0)):
+                dict(precision=3), dict(lambda0_ratio=1.5), dict(coarse_max=0), dict(cycle=2), dict(rho=-1.0),
+                dict(rho=1e-12), dict(cycle=1, amli_alpha=0.0), dict(cycle=1, amli_alpha=0.1),
+                dict(cycle=1, inner_iters=1)):
         st, h = amg.amg_setup(g.n, rp, col, w, None, amg.amg_default_options(**bad))
         assert st == amg.AMG_ERR_INVALID_ARG, bad
         assert amg.amg_last_error(None)
