@@ -44,7 +44,7 @@ class Options(C.Structure):
                 ("max_levels", C.c_int), ("inner_iters", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precond", C.c_int), ("lambda0_ratio", C.c_double),
                 ("hash_salt", C.c_uint64), ("cycle", C.c_int), ("amli_alpha", C.c_double),
-                ("rho", C.c_double)]
+                ("rho", C.c_double), ("aggregation", C.c_int), ("mis_k", C.c_int)]
 
 
 class Info(C.Structure):
@@ -81,6 +81,8 @@ def lib():
             L.orc_level_lambda.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.orc_level_cheb.argtypes = [C.c_void_p, C.c_int, P]
             L.orc_amli_coef.argtypes = [C.c_void_p, P]
+            L.orc_mis_aggregate.argtypes = [C.c_int, P, P, C.c_int, C.c_uint64, P, P]
+            L.orc_mis_aggregate.restype = C.c_int
             L.orc_degree_for.argtypes = [C.c_double, C.c_double]
             L.orc_degree_for.restype = C.c_int
             for name in ("orc_spmv", "orc_smooth", "orc_restrict", "orc_prolong_add", "orc_kcycle",
@@ -114,6 +116,17 @@ def match(rowptr, col, w, salt: int = 0):
     rounds = C.c_int(0)
     nH = lib().orc_match(n, _p(rowptr), _p(col), _p(w), C.c_uint64(salt), _p(mate), _p(agg), C.byref(rounds))
     return mate, agg, nH, rounds.value
+
+
+def mis_aggregate(rowptr, col, k: int = 4, salt: int = 0):
+    """Sec. 2 aggregation: (agg, is_root, n_aggregates) from the MIS of the graph of A^k."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = rowptr.size - 1
+    agg = np.empty(n, np.int32)
+    root = np.empty(n, np.int32)
+    nH = lib().orc_mis_aggregate(n, _p(rowptr), _p(col), k, C.c_uint64(salt), _p(agg), _p(root))
+    return agg, root.astype(bool), nH
 
 
 def degree_for(rho: float, lambda0_ratio: float = 0.1) -> int:

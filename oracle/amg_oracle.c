@@ -79,6 +79,8 @@ void orc_default_options(orc_options *o) {
   o->cycle = ORC_CYCLE_K;
   o->amli_alpha = 0.25;
   o->rho = 0.0;
+  o->aggregation = ORC_AGG_MATCHING;
+  o->mis_k = 4;
 }
 
 /* ------------------------------------------------------------------ */
@@ -257,6 +259,89 @@ int orc_match(int n, const int64_t *rowptr, const int32_t *col, const double *w,
   for (int i = 0; i < n; ++i)
     if (mate[i] >= 0 && mate[i] < i) agg[i] = agg[mate[i]];
   return nH;
+}
+
+/* ------------------------------------------------------------------ */
+/* Aggregation by a maximal independent set of the graph of A^k (Sec. 2, */
+/* steps (A) and (B); Sec. 4 applies it with k = 4).                     */
+/* ------------------------------------------------------------------ */
+static uint64_t mis_key(uint64_t salt, int v) {
+  return (((splitmix64(salt ^ (uint64_t)v) >> 33) + 1) << 32) | (uint64_t)(uint32_t)v;
+}
+
+/* breadth-first distances from src, up to depth k (-1: farther) */
+static void bfs_limited(int n, const int64_t *rowptr, const int32_t *col, int src, int k, int *dist,
+                        int *queue, int *visited, int *nvis) {
+  int head = 0, tail = 0;
+  dist[src] = 0;
+  queue[tail++] = src;
+  visited[(*nvis)++] = src;
+  while (head < tail) {
+    int u = queue[head++];
+    if (dist[u] == k) continue;
+    for (int64_t p = rowptr[u]; p < rowptr[u + 1]; ++p) {
+      int v = col[p];
+      if (dist[v] < 0) {
+        dist[v] = dist[u] + 1;
+        queue[tail++] = v;
+        visited[(*nvis)++] = v;
+      }
+    }
+  }
+  (void)n;
+}
+
+static int cmp_key_desc(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x < y) - (x > y);
+}
+
+int orc_mis_aggregate(int n, const int64_t *rowptr, const int32_t *col, int k, uint64_t salt,
+                      int32_t *agg, int32_t *root) {
+  if (n < 1 || k < 1) return -1;
+  uint64_t *order = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+  int *dist = (int *)malloc(sizeof(int) * (size_t)n), *queue = (int *)malloc(sizeof(int) * (size_t)n);
+  int *vis = (int *)malloc(sizeof(int) * (size_t)n);
+  char *blocked = (char *)calloc((size_t)n, 1);
+  for (int v = 0; v < n; ++v) { order[v] = mis_key(salt, v); dist[v] = -1; root[v] = 0; }
+  qsort(order, (size_t)n, sizeof(uint64_t), cmp_key_desc);
+  /* (A) greedy: a vertex not within distance k of an earlier root becomes one */
+  for (int a = 0; a < n; ++a) {
+    int v = (int)(uint32_t)order[a];
+    if (blocked[v]) continue;
+    root[v] = 1;
+    int nvis = 0;
+    bfs_limited(n, rowptr, col, v, k, dist, queue, vis, &nvis);
+    for (int t = 0; t < nvis; ++t) { blocked[vis[t]] = 1; dist[vis[t]] = -1; }
+  }
+  /* (B) nearest root, ties to the larger key: grow all roots together one
+   * layer at a time; a vertex reached in layer t takes the largest label
+   * among its neighbours labelled in earlier layers */
+  uint64_t *lab = (uint64_t *)calloc((size_t)n, sizeof(uint64_t));
+  uint64_t *nxt = (uint64_t *)calloc((size_t)n, sizeof(uint64_t));
+  for (int v = 0; v < n; ++v) if (root[v]) lab[v] = mis_key(salt, v);
+  for (int layer = 1; layer <= k; ++layer) {
+    memcpy(nxt, lab, sizeof(uint64_t) * (size_t)n);
+    for (int v = 0; v < n; ++v) {
+      if (lab[v]) continue;
+      uint64_t best = 0;
+      for (int64_t p = rowptr[v]; p < rowptr[v + 1]; ++p)
+        if (lab[col[p]] > best) best = lab[col[p]];
+      nxt[v] = best;
+    }
+    memcpy(lab, nxt, sizeof(uint64_t) * (size_t)n);
+  }
+  /* aggregate ids: roots ranked by vertex index */
+  int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int nH = 0;
+  for (int v = 0; v < n; ++v) rank[v] = root[v] ? nH++ : -1;
+  int ok = 1;
+  for (int v = 0; v < n; ++v) {
+    if (!lab[v]) { ok = 0; break; } /* cannot happen: S is maximal */
+    agg[v] = rank[(int)(uint32_t)lab[v]];
+  }
+  free(order); free(dist); free(queue); free(vis); free(blocked); free(lab); free(nxt); free(rank);
+  return ok ? nH : -1;
 }
 
 /* ------------------------------------------------------------------ */
@@ -557,6 +642,9 @@ int orc_setup(int64_t n, const int64_t *rowptr, const int32_t *col, const double
   *out = NULL;
   orc_options opt;
   if (optin) opt = *optin; else orc_default_options(&opt);
+  if ((opt.aggregation != ORC_AGG_MATCHING && opt.aggregation != ORC_AGG_MIS) || opt.mis_k < 1 ||
+      opt.mis_k > 16)
+    return ORC_ERR_INVALID_ARG;
   if (!(opt.rho >= 0.0) || !isfinite(opt.rho) || (opt.cycle != ORC_CYCLE_K && opt.cycle != ORC_CYCLE_AMLI) ||
       !(opt.amli_alpha > 0.0 && opt.amli_alpha < 1.0))
     return ORC_ERR_INVALID_ARG;
@@ -624,19 +712,27 @@ int orc_setup(int64_t n, const int64_t *rowptr, const int32_t *col, const double
     orc_mat next;
     int owns = 0;
     int64_t ncur = nk;
-    lv->npass = opt.passes;
-    for (int p = 0; p < opt.passes; ++p) {
+    const int npass = opt.aggregation == ORC_AGG_MIS ? 1 : opt.passes;
+    lv->npass = npass;
+    for (int p = 0; p < npass; ++p) {
       int64_t nc = cur.n, nzc = cur.rowptr[nc];
-      /* matching weight of edge (i,j): strength |a_ij| / sqrt(a_ii a_jj) */
-      double *wp = vnew(nzc);
-      for (int64_t i = 0; i < nc; ++i)
-        for (int64_t q = cur.rowptr[i]; q < cur.rowptr[i + 1]; ++q)
-          wp[q] = -cur.val[q] / sqrt(cur.diag[i] * cur.diag[cur.col[q]]);
-      int32_t *mate = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
       int32_t *agg = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
-      int nH = orc_match((int)nc, cur.rowptr, cur.col, wp, opt.hash_salt, mate, agg, NULL);
-      free(wp);
-      free(mate);
+      int nH;
+      if (opt.aggregation == ORC_AGG_MIS) {
+        int32_t *isroot = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
+        nH = orc_mis_aggregate((int)nc, cur.rowptr, cur.col, opt.mis_k, opt.hash_salt, agg, isroot);
+        free(isroot);
+      } else {
+        /* matching weight of edge (i,j): strength |a_ij| / sqrt(a_ii a_jj) */
+        double *wp = vnew(nzc);
+        for (int64_t i = 0; i < nc; ++i)
+          for (int64_t q = cur.rowptr[i]; q < cur.rowptr[i + 1]; ++q)
+            wp[q] = -cur.val[q] / sqrt(cur.diag[i] * cur.diag[cur.col[q]]);
+        int32_t *mate = (int32_t *)malloc(sizeof(int32_t) * (size_t)nc);
+        nH = orc_match((int)nc, cur.rowptr, cur.col, wp, opt.hash_salt, mate, agg, NULL);
+        free(wp);
+        free(mate);
+      }
       memset(&next, 0, sizeof(next));
       st = galerkin(&cur, agg, nH, &next);
       if (st) return st;

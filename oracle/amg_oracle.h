@@ -60,7 +60,13 @@ typedef struct {
                           delta^(nu-1) (1/alpha - 1)/2 must be < 1 (0.25)     */
   double rho;          /* > 0: degree m from Eq. (bound-on-m) for damping rho;
                           `degree` is then ignored                            */
+  int aggregation;     /* ORC_AGG_MATCHING (`passes` handshake matchings per
+                          level) or ORC_AGG_MIS (Sec. 2: maximal independent
+                          set of the graph of A^k, one pass per level)        */
+  int mis_k;           /* k of A^k for ORC_AGG_MIS (Sec. 4 uses 4)            */
 } orc_options;
+
+enum { ORC_AGG_MATCHING = 0, ORC_AGG_MIS = 1 };
 
 typedef struct {
   int iterations;
@@ -85,6 +91,14 @@ void orc_default_options(orc_options *o);
  * CSR with positive weights w.  Outputs mate[n] (-1 = unmatched), agg[n]
  * (coarse id of each vertex), returns the number of coarse vertices; *rounds
  * receives the number of proposal rounds executed (last one adds nothing). */
+/* Aggregation of Sec. 2 (steps A and B): S = the maximal independent set of
+ * the graph of A^k (vertices at graph distance <= k adjacent) taken greedily
+ * in decreasing key order, key(v) = ((splitmix64(salt ^ v) >> 33) + 1) << 32
+ * | v; then every vertex joins its nearest root (graph distance, ties to the
+ * larger root key).  Aggregates are numbered by their roots' vertex order.
+ * Writes agg[n] and root[n] (1 for roots); returns the number of aggregates. */
+int orc_mis_aggregate(int n, const int64_t *rowptr, const int32_t *col, int k, uint64_t salt,
+                      int32_t *agg, int32_t *root);
 int orc_match(int n, const int64_t *rowptr, const int32_t *col, const double *w,
               uint64_t salt, int32_t *mate, int32_t *agg, int *rounds);
 
