@@ -37,6 +37,10 @@ import graphgen as gg  # noqa: E402
 WORKLOADS = {
     "grid3d_128": ("128^3 7-point graph Laplacian, w=1, d=1 on boundary faces; degree-5 polynomial "
                    "smoother, 3 matching passes/level, K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64)"),
+    "grid3d_128_neumann_mis": ("128^3 7-point pure (Neumann) graph Laplacian; degree-4 polynomial smoother, "
+                               "aggregation by the maximal independent set of the graph of A^4 (one pass per "
+                               "level), K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64): the setting of the paper's "
+                               "Table (matrix and right-hand side synthetic)"),
     "grid3d_96x32": ("96^3 7-point graph Laplacian, d=1 on boundary faces, 32 right-hand sides solved in one "
                      "batched call; degree-5 smoother, 3 passes/level, fp32 preconditioner / fp64 FCG, tol 1e-8"),
     "serve": ("continuous-batching server: pool of 16 graphs (8 random geometric, 4 2D and 4 3D grids), sizes "
@@ -217,7 +221,8 @@ def run_oracle_step(g, p, b, ncols=None, cycle=0):
     nr = b.size // g.n
     ncols = nr if ncols is None else min(ncols, nr)
     t0 = time.perf_counter()
-    h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"], cycle=cycle)
+    h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"], cycle=cycle,
+                         aggregation=p.get("aggregation", 0))
     for j in range(ncols):
         r = h.solve(b[j * g.n:(j + 1) * g.n], tol=1e-8)
         assert r.status == 0, r.status
@@ -292,7 +297,8 @@ def main():
     xd = torch.zeros_like(bd)
     in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + b.nbytes
     prec = amg.AMG_PREC_FP32 if args.precision == "fp32" else amg.AMG_PREC_FP64
-    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=prec, cycle=CYCLE)
+    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=prec, cycle=CYCLE,
+                                   aggregation=p.get("aggregation", 0))
     state = {"launches": 0, "iters": [], "setup_ms": [], "solve_ms": [], "kt": [0, 0.0, 0.0]}
 
     def step(timed_kernel: bool):
@@ -353,7 +359,7 @@ def main():
     variant = None
     if args.precision == "fp64" and nrhs == 1 and not args.no_variant:
         opts32 = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=amg.AMG_PREC_FP32,
-                                         cycle=CYCLE)
+                                         cycle=CYCLE, aggregation=p.get("aggregation", 0))
         its = []
 
         def step32():

@@ -241,6 +241,9 @@ def workload(name: str) -> tuple[Graph, dict]:
                     matrix seed 3, RHS seed 1003, fp32 preconditioner
     grid3d_96x32  : 96^3 7-point, d=1 on boundary, 32 RHS seeds 4000..4031,
                     degree 5, 3 passes, fp32 preconditioner
+    grid3d_128_neumann_mis : 128^3 7-point, pure (Neumann) Laplacian, degree 4,
+                    aggregation by the independent set of the graph of A^4
+                    (the setting of the paper's Table), RHS seed 2
     """
     if name == "grid2d_64":
         g = grid2d_5pt(64)
@@ -251,6 +254,9 @@ def workload(name: str) -> tuple[Graph, dict]:
     if name == "rdiag2d_2048":
         g = grid2d_random_diag(2048, 3)
         return g, dict(degree=4, passes=3, rhs_seeds=[1003], precision=1)
+    if name == "grid3d_128_neumann_mis":
+        g = grid3d_7pt(128, None)
+        return g, dict(degree=4, passes=1, rhs_seeds=[2], precision=0, aggregation=1)
     if name == "grid3d_96x32":
         g = grid3d_7pt(96, 1.0)
         return g, dict(degree=5, passes=3, rhs_seeds=list(range(4000, 4032)), precision=1)

@@ -85,9 +85,18 @@ typedef struct {
   double amli_alpha;   /* left end of the AMLI polynomial's interval, (0, 1)     */
   double rho;          /* > 0: choose m from Eq. (bound-on-m), see
                           amg_degree_for; `degree` is then ignored              */
+  int aggregation;     /* AMG_AGG_MATCHING: `passes` handshake matchings per
+                          level.  AMG_AGG_MIS: Sec. 2 steps (A)-(B), one pass per
+                          level: S = maximal independent set of the graph of
+                          A^mis_k taken greedily in decreasing key order, key(v)
+                          = ((splitmix64(salt ^ v) >> 33) + 1) << 32 | v; every
+                          vertex joins its nearest root (graph distance, ties to
+                          the larger key); aggregates numbered by root index   */
+  int mis_k;           /* k of A^k for AMG_AGG_MIS, 1..16 (Sec. 4: 4)           */
 } amg_options;
 
 enum { AMG_CYCLE_K = 0, AMG_CYCLE_AMLI = 1 };
+enum { AMG_AGG_MATCHING = 0, AMG_AGG_MIS = 1 };
 
 /* Per-solve report (Sec. 4 reports iterations and grid/operator complexity). */
 typedef struct {
@@ -108,7 +117,7 @@ typedef struct {
 
 /* Fill *opt with defaults: degree 4, passes 3, coarse_max 64, max_levels 30,
  * inner_iters 2, restart 5, max_iters 500, FP64, lambda0_ratio 0.1, salt 0,
- * AMG_CYCLE_K, amli_alpha 0.25, rho 0. */
+ * AMG_CYCLE_K, amli_alpha 0.25, rho 0, AMG_AGG_MATCHING, mis_k 4. */
 void amg_default_options(amg_options *opt);
 
 /* Smoother degree from Eq. (bound-on-m) (Sec. 3): the smallest m with

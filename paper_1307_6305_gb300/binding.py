@@ -34,6 +34,8 @@ AMG_PREC_FP64 = 0
 AMG_PREC_FP32 = 1
 AMG_CYCLE_K = 0
 AMG_CYCLE_AMLI = 1
+AMG_AGG_MATCHING = 0
+AMG_AGG_MIS = 1
 
 # every symbol declared in include/amg.h
 SYMBOLS = [
@@ -52,7 +54,7 @@ class amg_options(C.Structure):
                 ("max_levels", C.c_int), ("inner_iters", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precision", C.c_int), ("lambda0_ratio", C.c_double),
                 ("hash_salt", C.c_uint64), ("cycle", C.c_int), ("amli_alpha", C.c_double),
-                ("rho", C.c_double)]
+                ("rho", C.c_double), ("aggregation", C.c_int), ("mis_k", C.c_int)]
 
 
 class amg_info(C.Structure):

@@ -105,6 +105,9 @@ amg_status check_options(const amg_options &o) {
     return fail(AMG_ERR_INVALID_ARG, "precision must be AMG_PREC_FP64 or AMG_PREC_FP32");
   if (!(o.lambda0_ratio > 0.0 && o.lambda0_ratio < 1.0))
     return fail(AMG_ERR_INVALID_ARG, "lambda0_ratio must be in (0, 1)");
+  if (o.aggregation != AMG_AGG_MATCHING && o.aggregation != AMG_AGG_MIS)
+    return fail(AMG_ERR_INVALID_ARG, "aggregation must be AMG_AGG_MATCHING or AMG_AGG_MIS");
+  if (o.mis_k < 1 || o.mis_k > 16) return fail(AMG_ERR_INVALID_ARG, "mis_k must be in [1, 16]");
   if (o.cycle != AMG_CYCLE_K && o.cycle != AMG_CYCLE_AMLI)
     return fail(AMG_ERR_INVALID_ARG, "cycle must be AMG_CYCLE_K or AMG_CYCLE_AMLI");
   if (!(o.rho >= 0.0) || !std::isfinite(o.rho)) return fail(AMG_ERR_INVALID_ARG, "rho must be >= 0");
@@ -179,6 +182,8 @@ void amg_default_options(amg_options *o) {
   o->cycle = AMG_CYCLE_K;
   o->amli_alpha = 0.25;
   o->rho = 0.0;
+  o->aggregation = AMG_AGG_MATCHING;
+  o->mis_k = 4;
 }
 
 int amg_degree_for(double rho, double lambda0_ratio) {

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -442,32 +443,45 @@ __global__ void k_max_abs(int n, const double *a, unsigned long long *out) {
 // in order (m0's row, then m1's row, CSR order), diag_I = sum_J W_IJ (J
 // ascending) + d_I, d_I = d_m0 + d_m1.
 // ---------------------------------------------------------------------------
-__global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, const int *__restrict__ m0,
-                              const int *__restrict__ m1, int64_t *__restrict__ len) {
+// Members of a coarse row: the pair (m0, m1) of a matching pass (m1 = -1 for
+// a singleton) or an ascending member list (ptr, mem) of an aggregation pass.
+struct PairMembers {
+  const int *m0, *m1;
+  __device__ int count(int I) const { return m1[I] >= 0 ? 2 : 1; }
+  __device__ int get(int I, int q) const { return q == 0 ? m0[I] : m1[I]; }
+};
+struct ListMembers {
+  const int *ptr, *mem;
+  __device__ int count(int I) const { return ptr[I + 1] - ptr[I]; }
+  __device__ int get(int I, int q) const { return mem[ptr[I] + q]; }
+};
+
+template <typename M>
+__global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, M mb, int64_t *__restrict__ len) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
-  int a = m0[I], b = m1[I];
-  int64_t l = rp[a + 1] - rp[a];
-  if (b >= 0) l += rp[b + 1] - rp[b];
+  int64_t l = 0;
+  for (int q = 0; q < mb.count(I); ++q) {
+    const int v = mb.get(I, q);
+    l += rp[v + 1] - rp[v];
+  }
   len[I] = l;
 }
-
 // gather mapped entries of the coarse row into its segment, stable-sort by J,
 // count distinct J != I
 constexpr int kLocalSort = 64;
+constexpr int kBlockSort = 8192;  // longest row sorted in shared memory (128 KB)
+template <typename M>
 __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                              const double *__restrict__ val, const int *__restrict__ agg,
-                              const int *__restrict__ m0, const int *__restrict__ m1,
+                              const double *__restrict__ val, const int *__restrict__ agg, M mb,
                               const int64_t *__restrict__ seg, int *__restrict__ keyJ,
-                              double *__restrict__ kval, int *__restrict__ count) {
+                              double *__restrict__ kval, int *__restrict__ count, int *longrows) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   const int64_t s0 = seg[I];
   int64_t t = s0;
-  const int mem[2] = {m0[I], m1[I]};
-  for (int q = 0; q < 2; ++q) {
-    const int v = mem[q];
-    if (v < 0) continue;
+  for (int q = 0; q < mb.count(I); ++q) {
+    const int v = mb.get(I, q);
     for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
       keyJ[t] = agg[col[p]];
       kval[t] = val[p];
@@ -504,7 +518,13 @@ __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int3
     count[I] = c;
     return;
   }
-  for (int64_t a = 1; a < len; ++a) {  // stable insertion sort by J
+  if (longrows && len <= kBlockSort) {
+    // long row: sorted by k_gal_sort_long, one block per row
+    longrows[1 + atomicAdd(longrows, 1)] = I;
+    count[I] = 0;
+    return;
+  }
+  for (int64_t a = 1; a < len; ++a) {  // stable insertion sort by J (very long rows only)
     const int kj = keyJ[s0 + a];
     const double kv = kval[s0 + a];
     int64_t b = a - 1;
@@ -524,10 +544,75 @@ __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int3
   count[I] = c;
 }
 
+// Rows with kLocalSort < len <= kBlockSort entries (large aggregates): one
+// block per row sorts (J, gather position) with a bitonic network in shared
+// memory -- the position makes the order stable, as the summation order of
+// the Galerkin sums requires -- then writes the row back and counts its
+// distinct J != I.  Rows come from the list filled by k_pair_gather.
+constexpr int kSortThreads = 128;
+constexpr int kGalSortSmem = (int)(sizeof(unsigned long long) + sizeof(double)) * kBlockSort;
+__global__ void __launch_bounds__(kSortThreads) k_gal_sort_long(const int64_t *__restrict__ seg,
+                                                                int *__restrict__ keyJ, double *__restrict__ kval,
+                                                                int *__restrict__ count, const int *longrows) {
+  extern __shared__ __align__(16) unsigned char sort_smem[];
+  unsigned long long *key = reinterpret_cast<unsigned long long *>(sort_smem);
+  double *v = reinterpret_cast<double *>(sort_smem + sizeof(unsigned long long) * kBlockSort);
+  __shared__ int cnt;
+  const int nlong = longrows[0];
+  for (int r = blockIdx.x; r < nlong; r += gridDim.x) {
+    const int I = longrows[1 + r];
+    const int64_t s0 = seg[I];
+    const int len = (int)(seg[I + 1] - s0);
+    int p2 = 1;
+    while (p2 < len) p2 <<= 1;
+    for (int a = threadIdx.x; a < p2; a += kSortThreads) {
+      if (a < len) {
+        key[a] = ((unsigned long long)(unsigned)keyJ[s0 + a] << 32) | (unsigned)a;
+        v[a] = kval[s0 + a];
+      } else {
+        key[a] = ~0ull;
+        v[a] = 0.0;
+      }
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int a = threadIdx.x; a < p2; a += kSortThreads) {
+          const int b = a ^ stride;
+          if (b > a) {
+            const bool up = (a & size) == 0;
+            if ((key[a] > key[b]) == up) {
+              const unsigned long long tk = key[a];
+              key[a] = key[b];
+              key[b] = tk;
+              const double tv = v[a];
+              v[a] = v[b];
+              v[b] = tv;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    int c = 0;
+    for (int a = threadIdx.x; a < len; a += kSortThreads) {
+      const int J = (int)(key[a] >> 32);
+      keyJ[s0 + a] = J;
+      kval[s0 + a] = v[a];
+      if (J != I && (a == 0 || (int)(key[a - 1] >> 32) != J)) ++c;
+    }
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) count[I] = cnt;
+    __syncthreads();  // key, v and cnt are reused by the next row
+  }
+}
+
+template <typename M>
 __global__ void k_pair_emit(int nH, const int64_t *__restrict__ seg, const int *__restrict__ keyJ,
                             const double *__restrict__ kval, const int64_t *__restrict__ rpH,
-                            const double *__restrict__ dlow, const int *__restrict__ m0,
-                            const int *__restrict__ m1, int32_t *__restrict__ colH,
+                            const double *__restrict__ dlow, M mb, int32_t *__restrict__ colH,
                             double *__restrict__ valH, double *__restrict__ diagH,
                             double *__restrict__ dlowH) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -550,8 +635,7 @@ __global__ void k_pair_emit(int nH, const int64_t *__restrict__ seg, const int *
     a = b;
   }
   double dI = 0.0;
-  dI += dlow[m0[I]];
-  if (m1[I] >= 0) dI += dlow[m1[I]];
+  for (int q = 0; q < mb.count(I); ++q) dI += dlow[mb.get(I, q)];
   dlowH[I] = dI;
   diagH[I] = wsum + dI;
 }
@@ -574,15 +658,67 @@ __global__ void k_agg_place(int n, const int *__restrict__ agg, const int *__res
   const int I = agg[i];
   mem[ptr[I] + atomicAdd(&fill[I], 1)] = i;
 }
-__global__ void k_agg_sort(int nH, const int *__restrict__ ptr, int *__restrict__ mem) {
+// members of each aggregate in ascending order: insertion sort by one
+// thread for short lists; lists of kAggShort < len <= kBlockSort members go
+// to `longlist` for k_agg_sort_long (longer ones stay with the thread)
+constexpr int kAggShort = 64;
+__global__ void k_agg_sort(int nH, const int *__restrict__ ptr, int *__restrict__ mem, int *longlist) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   const int a0 = ptr[I], a1 = ptr[I + 1];
+  if (longlist && a1 - a0 > kAggShort && a1 - a0 <= 8192) {
+    longlist[1 + atomicAdd(longlist, 1)] = I;
+    return;
+  }
   for (int a = a0 + 1; a < a1; ++a) {
     int v = mem[a], b = a - 1;
     while (b >= a0 && mem[b] > v) { mem[b + 1] = mem[b]; --b; }
     mem[b + 1] = v;
   }
+}
+
+// one block per long member list: bitonic sort of the (distinct) vertex ids
+__global__ void __launch_bounds__(128) k_agg_sort_long(const int *__restrict__ ptr, int *__restrict__ mem,
+                                                        const int *longlist) {
+  __shared__ int key[8192];
+  const int nlong = longlist[0];
+  for (int r = blockIdx.x; r < nlong; r += gridDim.x) {
+    const int I = longlist[1 + r];
+    const int a0 = ptr[I], len = ptr[I + 1] - a0;
+    int p2 = 1;
+    while (p2 < len) p2 <<= 1;
+    for (int a = threadIdx.x; a < p2; a += blockDim.x) key[a] = a < len ? mem[a0 + a] : 0x7fffffff;
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int a = threadIdx.x; a < p2; a += blockDim.x) {
+          const int b = a ^ stride;
+          if (b > a && ((key[a] > key[b]) == ((a & size) == 0))) {
+            const int t = key[a];
+            key[a] = key[b];
+            key[b] = t;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int a = threadIdx.x; a < len; a += blockDim.x) mem[a0 + a] = key[a];
+    __syncthreads();
+  }
+}
+
+// sort member lists (ptr, mem) of nH aggregates in ascending order
+static amg_status sort_members(amg_handle_s *h, int nH, const int *ptr, int *mem) {
+  cudaStream_t st = h->stream;
+  int *longlist = nullptr;
+  AMG_TRY(pool_alloc((void **)&longlist, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(longlist, 0, sizeof(int), st));
+  k_agg_sort<<<blocks_for(nH, 128), 128, 0, st>>>(nH, ptr, mem, longlist);
+  LAUNCH_CHECK(&h->launches);
+  k_agg_sort_long<<<std::max(1, std::min(nH, 4 * 152)), 128, 0, st>>>(ptr, mem, longlist);
+  LAUNCH_CHECK(&h->launches);
+  pool_free(longlist, st);
+  return AMG_OK;
 }
 
 // lambda1 = ||A||_inf = max_i (|a_ii| + sum_j |a_ij|), summed in row order
@@ -729,6 +865,80 @@ static amg_status alloc_persist(amg_handle_s *h, void **p, size_t bytes) {
   return h->arena.alloc(p, bytes);
 }
 
+// Galerkin A_H = P^T A P on `cur` for the aggregates given by agg and their
+// members (owned temporaries in `next`); sums as documented at k_pair_gather
+// the long-row sort needs 128 KB of dynamic shared memory: allowed once per
+// device (function attributes are process-wide; set under a lock)
+static amg_status sort_kernels_ready() {
+  static std::mutex mu;
+  static bool done[64];
+  int dev = 0;
+  AMG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(AMG_ERR_CUDA, "device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done[dev]) {
+    AMG_CUDA_TRY(cudaFuncSetAttribute(k_gal_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, kGalSortSmem));
+    done[dev] = true;
+  }
+  return AMG_OK;
+}
+
+template <typename M>
+static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *aggp, M mb, int nH,
+                           LevelBuild &next) {
+  cudaStream_t st = h->stream;
+  const unsigned nbH = blocks_for(nH, 256);
+  int64_t *seglen = nullptr, *seg = nullptr;
+  AMG_TRY(pool_alloc((void **)&seglen, sizeof(int64_t) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&seg, sizeof(int64_t) * (size_t)(nH + 1), st));
+  k_pair_seglen<<<nbH, 256, 0, st>>>(nH, cur.A.rowptr, mb, seglen);
+  LAUNCH_CHECK(&h->launches);
+  AMG_CUDA_TRY(cudaMemsetAsync(seglen + nH, 0, sizeof(int64_t), st));
+  int64_t segtot = 0;
+  AMG_TRY(exclusive_scan_i64(seglen, seg, nH + 1, st, &segtot));
+  int *keyJ = nullptr, *count = nullptr;
+  double *kval = nullptr;
+  AMG_TRY(pool_alloc((void **)&keyJ, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
+  AMG_TRY(pool_alloc((void **)&kval, sizeof(double) * (size_t)std::max<int64_t>(segtot, 1), st));
+  AMG_TRY(pool_alloc((void **)&count, sizeof(int64_t) * (size_t)(nH + 1), st));
+  int *longrows = nullptr;  // [0]: count, then the long rows
+  AMG_TRY(pool_alloc((void **)&longrows, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(longrows, 0, sizeof(int), st));
+  k_pair_gather<<<blocks_for(nH, 128), 128, 0, st>>>(nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, mb, seg, keyJ,
+                                                     kval, count, longrows);
+  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(sort_kernels_ready());
+  k_gal_sort_long<<<std::max(1, std::min(nH, 4 * 152)), kSortThreads, kGalSortSmem, st>>>(seg, keyJ, kval, count,
+                                                                                          longrows);
+  LAUNCH_CHECK(&h->launches);
+  pool_free(longrows, st);
+  // widen counts to int64 for the row-offset scan
+  int64_t *cnt64 = nullptr;
+  AMG_TRY(pool_alloc((void **)&cnt64, sizeof(int64_t) * (size_t)(nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt64, 0, sizeof(int64_t) * (size_t)(nH + 1), st));
+  k_widen<<<nbH, 256, 0, st>>>(nH, count, cnt64);
+  LAUNCH_CHECK(&h->launches);
+  next.A.n = nH;
+  AMG_TRY(pool_alloc((void **)&next.A.rowptr, sizeof(int64_t) * (size_t)(nH + 1), st));
+  int64_t nnzH = 0;
+  AMG_TRY(exclusive_scan_i64(cnt64, next.A.rowptr, nH + 1, st, &nnzH));
+  next.A.nnz = nnzH;
+  AMG_TRY(pool_alloc((void **)&next.A.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnzH, 1), st));
+  AMG_TRY(pool_alloc((void **)&next.A.val, sizeof(double) * (size_t)std::max<int64_t>(nnzH, 1), st));
+  AMG_TRY(pool_alloc((void **)&next.diag, sizeof(double) * (size_t)std::max(nH, 1), st));
+  AMG_TRY(pool_alloc((void **)&next.dlow, sizeof(double) * (size_t)std::max(nH, 1), st));
+  k_pair_emit<<<nbH, 256, 0, st>>>(nH, seg, keyJ, kval, next.A.rowptr, cur.dlow, mb, next.A.col, next.A.val,
+                                   next.diag, next.dlow);
+  LAUNCH_CHECK(&h->launches);
+  pool_free(seglen, st);
+  pool_free(seg, st);
+  pool_free(keyJ, st);
+  pool_free(kval, st);
+  pool_free(count, st);
+  pool_free(cnt64, st);
+  return AMG_OK;
+}
+
 // one matching pass + Galerkin on `cur` (owned temporaries in `next`)
 static amg_status coarsen_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuild &next, int *aggp,
                                int *nH_out) {
@@ -749,50 +959,178 @@ static amg_status coarsen_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuil
                      &rounds, &h->launches));
   pool_free(s, st);
   pool_free(mate, st);
-  // Galerkin
-  const unsigned nbH = blocks_for(nH, 256);
-  int64_t *seglen = nullptr, *seg = nullptr;
-  AMG_TRY(pool_alloc((void **)&seglen, sizeof(int64_t) * (size_t)(nH + 1), st));
-  AMG_TRY(pool_alloc((void **)&seg, sizeof(int64_t) * (size_t)(nH + 1), st));
-  k_pair_seglen<<<nbH, 256, 0, st>>>(nH, cur.A.rowptr, m0, m1, seglen);
-  LAUNCH_CHECK(&h->launches);
-  AMG_CUDA_TRY(cudaMemsetAsync(seglen + nH, 0, sizeof(int64_t), st));
-  int64_t segtot = 0;
-  AMG_TRY(exclusive_scan_i64(seglen, seg, nH + 1, st, &segtot));
-  int *keyJ = nullptr, *count = nullptr;
-  double *kval = nullptr;
-  AMG_TRY(pool_alloc((void **)&keyJ, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
-  AMG_TRY(pool_alloc((void **)&kval, sizeof(double) * (size_t)std::max<int64_t>(segtot, 1), st));
-  AMG_TRY(pool_alloc((void **)&count, sizeof(int64_t) * (size_t)(nH + 1), st));
-  k_pair_gather<<<blocks_for(nH, 128), 128, 0, st>>>(nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, m0, m1, seg, keyJ,
-                                      kval, count);
-  LAUNCH_CHECK(&h->launches);
-  // widen counts to int64 for the row-offset scan
-  int64_t *cnt64 = nullptr;
-  AMG_TRY(pool_alloc((void **)&cnt64, sizeof(int64_t) * (size_t)(nH + 1), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(cnt64, 0, sizeof(int64_t) * (size_t)(nH + 1), st));
-  k_widen<<<nbH, 256, 0, st>>>(nH, count, cnt64);
-  LAUNCH_CHECK(&h->launches);
-  next.A.n = nH;
-  AMG_TRY(pool_alloc((void **)&next.A.rowptr, sizeof(int64_t) * (size_t)(nH + 1), st));
-  int64_t nnzH = 0;
-  AMG_TRY(exclusive_scan_i64(cnt64, next.A.rowptr, nH + 1, st, &nnzH));
-  next.A.nnz = nnzH;
-  AMG_TRY(pool_alloc((void **)&next.A.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnzH, 1), st));
-  AMG_TRY(pool_alloc((void **)&next.A.val, sizeof(double) * (size_t)std::max<int64_t>(nnzH, 1), st));
-  AMG_TRY(pool_alloc((void **)&next.diag, sizeof(double) * (size_t)std::max(nH, 1), st));
-  AMG_TRY(pool_alloc((void **)&next.dlow, sizeof(double) * (size_t)std::max(nH, 1), st));
-  k_pair_emit<<<nbH, 256, 0, st>>>(nH, seg, keyJ, kval, next.A.rowptr, cur.dlow, m0, m1, next.A.col,
-                                    next.A.val, next.diag, next.dlow);
-  LAUNCH_CHECK(&h->launches);
-  pool_free(seglen, st);
-  pool_free(seg, st);
-  pool_free(keyJ, st);
-  pool_free(kval, st);
-  pool_free(count, st);
-  pool_free(cnt64, st);
+  AMG_TRY(galerkin(h, cur, aggp, PairMembers{m0, m1}, nH, next));
   pool_free(m0, st);
   pool_free(m1, st);
+  *nH_out = nH;
+  return AMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// aggregation by a maximal independent set of the graph of A^k (Sec. 2 steps
+// (A) and (B); Sec. 4: k = 4).  Keys ((splitmix64(salt ^ v) >> 33) + 1) << 32
+// | v are distinct and nonzero.  (A) Luby's rule with fixed keys -- an
+// undecided vertex whose key is the largest among undecided vertices within
+// distance k joins S, then every vertex within distance k of a new root
+// leaves the undecided set -- gives the greedy set in decreasing key order.
+// (B) every vertex joins its nearest root, ties to the larger key: labels
+// spread one layer per round, each new vertex taking its neighbours' largest
+// label.  Distances come from k rounds of pull-style propagation over the
+// whole graph (no atomics, deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mis_key(uint64_t salt, int v) {
+  return (((splitmix64(salt ^ (uint64_t)v) >> 33) + 1) << 32) | (uint64_t)(uint32_t)v;
+}
+
+// state: 0 undecided, 1 root, 2 covered
+__global__ void k_mis_seed(int n, const int *__restrict__ state, uint64_t salt, uint64_t *__restrict__ m) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) m[v] = state[v] == 0 ? mis_key(salt, v) : 0ull;
+}
+
+// out[v] = max(in[v], max_{u in N(v)} in[u]); with keep, a nonzero in[v] stays
+__global__ void k_max_spread(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const uint64_t *__restrict__ in, uint64_t *__restrict__ out, int keep) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint64_t b = in[v];
+  if (keep && b) {
+    out[v] = b;
+    return;
+  }
+  for (int64_t p = rp[v]; p < rp[v + 1]; ++p) b = max(b, in[col[p]]);
+  out[v] = b;
+}
+
+__global__ void k_mis_pick(int n, int *__restrict__ state, uint64_t salt, const uint64_t *__restrict__ m,
+                           uint64_t *__restrict__ c) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const bool pick = state[v] == 0 && m[v] == mis_key(salt, v);
+  if (pick) state[v] = 1;
+  c[v] = pick ? 1ull : 0ull;
+}
+
+__global__ void k_mis_cover(int n, int *__restrict__ state, const uint64_t *__restrict__ c, int *left) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  if (state[v] == 0) {
+    if (c[v]) state[v] = 2;
+    else atomicAdd(left, 1);
+  }
+}
+
+__global__ void k_mis_label(int n, const int *__restrict__ state, uint64_t salt, uint64_t *__restrict__ lab,
+                            int *__restrict__ isroot) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  lab[v] = state[v] == 1 ? mis_key(salt, v) : 0ull;
+  isroot[v] = state[v] == 1;
+}
+
+__global__ void k_mis_agg(int n, const uint64_t *__restrict__ lab, const int *__restrict__ rank,
+                          int *__restrict__ agg, int *bad) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  if (!lab[v]) {  // unreachable: S is maximal
+    atomicExch(bad, 1);
+    agg[v] = 0;
+    return;
+  }
+  agg[v] = rank[(uint32_t)(lab[v] & 0xffffffffull)];
+}
+
+static amg_status mis_aggregate(amg_handle_s *h, int n, const int64_t *rp, const int32_t *col, int k, int *aggp,
+                                int *nH_out) {
+  cudaStream_t st = h->stream;
+  const unsigned nb = blocks_for(n, 256);
+  const uint64_t salt = h->opt.hash_salt;
+  int *state = nullptr, *isroot = nullptr, *rank = nullptr, *flag = nullptr;
+  uint64_t *a = nullptr, *b = nullptr;
+  AMG_TRY(pool_alloc((void **)&state, sizeof(int) * (size_t)n, st));
+  AMG_TRY(pool_alloc((void **)&isroot, sizeof(int) * (size_t)n, st));
+  AMG_TRY(pool_alloc((void **)&rank, sizeof(int) * (size_t)n, st));
+  AMG_TRY(pool_alloc((void **)&a, sizeof(uint64_t) * (size_t)n, st));
+  AMG_TRY(pool_alloc((void **)&b, sizeof(uint64_t) * (size_t)n, st));
+  AMG_TRY(pool_alloc((void **)&flag, sizeof(int) * 2, st));
+  AMG_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(int) * (size_t)n, st));
+  // k spreading rounds ping-pong between a and b; the result is in *res
+  auto spread = [&](uint64_t **res, int keep) -> amg_status {
+    uint64_t *src = *res, *dst = (src == a) ? b : a;
+    for (int r = 0; r < k; ++r) {
+      k_max_spread<<<nb, 256, 0, st>>>(n, rp, col, src, dst, keep);
+      LAUNCH_CHECK(&h->launches);
+      std::swap(src, dst);
+    }
+    *res = src;
+    return AMG_OK;
+  };
+  // (A) every round picks at least the largest undecided key, so at most n rounds
+  for (int round = 0;; ++round) {
+    if (round > n) return fail(AMG_ERR_CUDA, "independent-set selection did not terminate");
+    uint64_t *m = a;
+    k_mis_seed<<<nb, 256, 0, st>>>(n, state, salt, m);
+    LAUNCH_CHECK(&h->launches);
+    AMG_TRY(spread(&m, 0));
+    uint64_t *c = (m == a) ? b : a;
+    k_mis_pick<<<nb, 256, 0, st>>>(n, state, salt, m, c);
+    LAUNCH_CHECK(&h->launches);
+    AMG_TRY(spread(&c, 0));
+    AMG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    k_mis_cover<<<nb, 256, 0, st>>>(n, state, c, flag);
+    LAUNCH_CHECK(&h->launches);
+    int left = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&left, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (left == 0) break;
+  }
+  // (B) nearest root, ties to the larger key
+  uint64_t *lab = a;
+  k_mis_label<<<nb, 256, 0, st>>>(n, state, salt, lab, isroot);
+  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(spread(&lab, 1));
+  int nH = 0;
+  {
+    int64_t tot = 0;
+    AMG_TRY(exclusive_scan_i32(isroot, rank, n, st, &tot));
+    nH = (int)tot;
+  }
+  AMG_CUDA_TRY(cudaMemsetAsync(flag + 1, 0, sizeof(int), st));
+  k_mis_agg<<<nb, 256, 0, st>>>(n, lab, rank, aggp, flag + 1);
+  LAUNCH_CHECK(&h->launches);
+  int bad = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&bad, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  for (void *p : {(void *)state, (void *)isroot, (void *)rank, (void *)a, (void *)b, (void *)flag}) pool_free(p, st);
+  if (bad) return fail(AMG_ERR_CUDA, "a vertex farther than k from every root");
+  *nH_out = nH;
+  return AMG_OK;
+}
+
+// one aggregation pass by a maximal independent set + Galerkin on `cur`
+static amg_status coarsen_mis_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuild &next, int *aggp,
+                                   int *nH_out) {
+  cudaStream_t st = h->stream;
+  const int n = cur.A.n;
+  int nH = 0;
+  AMG_TRY(mis_aggregate(h, n, cur.A.rowptr, cur.A.col, h->opt.mis_k, aggp, &nH));
+  // member lists, ascending
+  int *cnt = nullptr, *fill = nullptr, *ptr = nullptr, *mem = nullptr;
+  AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&fill, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&ptr, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&mem, sizeof(int) * (size_t)std::max(n, 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)(nH + 1), st));
+  k_agg_count<<<blocks_for(n, 256), 256, 0, st>>>(n, aggp, cnt);
+  LAUNCH_CHECK(&h->launches);
+  int64_t tot = 0;
+  AMG_TRY(exclusive_scan_i32(cnt, ptr, nH + 1, st, &tot));
+  k_agg_place<<<blocks_for(n, 256), 256, 0, st>>>(n, aggp, ptr, fill, mem);
+  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(sort_members(h, nH, ptr, mem));
+  AMG_TRY(galerkin(h, cur, aggp, ListMembers{ptr, mem}, nH, next));
+  for (void *p : {(void *)cnt, (void *)fill, (void *)ptr, (void *)mem}) pool_free(p, st);
   *nH_out = nH;
   return AMG_OK;
 }
@@ -879,8 +1217,7 @@ static amg_status build_agg_lists(amg_handle_s *h, amg::Level &L) {
   AMG_TRY(exclusive_scan_i32(cnt, L.agg_ptr, L.nH + 1, st, &tot));
   k_agg_place<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.agg, L.agg_ptr, fill, L.agg_mem);
   LAUNCH_CHECK(&h->launches);
-  k_agg_sort<<<blocks_for(L.nH, 128), 128, 0, st>>>(L.nH, L.agg_ptr, L.agg_mem);
-  LAUNCH_CHECK(&h->launches);
+  AMG_TRY(sort_members(h, L.nH, L.agg_ptr, L.agg_mem));
   pool_free(cnt, st);
   pool_free(fill, st);
   return AMG_OK;
@@ -1050,7 +1387,8 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     LAUNCH_CHECK(&h->launches);
   }
   // ---- coarsening ----
-  const int passes = h->opt.passes;
+  const bool mis = h->opt.aggregation == AMG_AGG_MIS;
+  const int passes = mis ? 1 : h->opt.passes;
   while (h->lv.back().n > h->opt.coarse_max && (int)h->lv.size() < h->opt.max_levels) {
     const int k = (int)h->lv.size() - 1;
     const int nk = h->lv[k].n;
@@ -1066,7 +1404,8 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
       int *aggp = nullptr;
       AMG_TRY(pool_alloc((void **)&aggp, sizeof(int) * (size_t)std::max(cur.A.n, 1), st));
       LevelBuild next;
-      AMG_TRY(coarsen_pass(h, cur, next, aggp, &nH));
+      if (mis) AMG_TRY(coarsen_mis_pass(h, cur, next, aggp, &nH));
+      else AMG_TRY(coarsen_pass(h, cur, next, aggp, &nH));
       if (p == 0) {
         AMG_CUDA_TRY(cudaMemcpyAsync(comp, aggp, sizeof(int) * (size_t)nk, cudaMemcpyDeviceToDevice, st));
       } else {

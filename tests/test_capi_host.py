@@ -43,6 +43,7 @@ def test_default_options(amg):
     assert (o.degree, o.passes, o.coarse_max, o.max_levels, o.inner_iters, o.restart) == (4, 3, 64, 30, 2, 5)
     assert o.precision == amg.AMG_PREC_FP64 and o.lambda0_ratio == 0.1
     assert o.cycle == amg.AMG_CYCLE_K and o.amli_alpha == 0.25 and o.rho == 0.0
+    assert o.aggregation == amg.AMG_AGG_MATCHING and o.mis_k == 4
 
 
 def test_degree_for_matches_oracle(amg, orc):
@@ -68,7 +69,8 @@ def test_argument_errors_before_device(amg):
     for bad in (dict(degree=-1), dict(degree=17), dict(passes=0), dict(inner_iters=9), dict(restart=0),
                 dict(precision=3), dict(lambda0_ratio=1.5), dict(coarse_max=0), dict(cycle=2), dict(rho=-1.0),
                 dict(rho=1e-12), dict(cycle=1, amli_alpha=0.0), dict(cycle=1, amli_alpha=0.1),
-                dict(cycle=1, inner_iters=1)):
+                dict(cycle=1, inner_iters=1), dict(aggregation=2), dict(aggregation=1, mis_k=0),
+                dict(aggregation=1, mis_k=17)):
         st, h = amg.amg_setup(g.n, rp, col, w, None, amg.amg_default_options(**bad))
         assert st == amg.AMG_ERR_INVALID_ARG, bad
         assert amg.amg_last_error(None)
