@@ -396,12 +396,14 @@ static inline unsigned sell_grid(int n, int wps) {
 }
 
 // Warps per slice for a level of n rows: the smallest of 1, 2, 4, 8 that
-// gives at least ~16 warps per SM (152 SMs), so that small levels spread
-// their FP64 work and their dependent loads over the whole GPU.
-int choose_wps(int n) {
+// gives at least `per_sm` warps per SM (152 SMs; 32 unless
+// AMG_GB300_WPS_WARPS overrides -- measured on the 128^3 hierarchy: 16 / 32
+// / 64 / 128 give 36.5 / 36.2 / 37.8 / 37.7 ms per solve), so that small
+// levels spread their FP64 work and their dependent loads over the GPU.
+int choose_wps(int n, int per_sm) {
   const int64_t slices = (n + kSlice - 1) / kSlice;
   int w = 1;
-  while (w < 8 && slices * w < 16 * 152) w *= 2;
+  while (w < 8 && slices * w < (int64_t)per_sm * 152) w *= 2;
   return w;
 }
 
@@ -854,10 +856,12 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // AMG_GB300_SPLIT=0 keeps one thread per row on every level
   const char *split_env = getenv("AMG_GB300_SPLIT");
   const bool split = !(split_env && split_env[0] == '0');
+  int per_sm = 32;
+  if (const char *e = getenv("AMG_GB300_WPS_WARPS")) per_sm = std::max(1, std::min(2048, atoi(e)));
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     const size_t n = (size_t)std::max(V.n, 1);
-    V.wps = split ? choose_wps(V.n) : 1;
+    V.wps = split ? choose_wps(V.n, per_sm) : 1;
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1 && h->opt.degree > 0) {
       // the smoother form 2 t(A) of this level (Chebyshev kernels)
