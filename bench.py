@@ -41,6 +41,10 @@ WORKLOADS = {
                                "aggregation by the maximal independent set of the graph of A^4 (one pass per "
                                "level), K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64): the setting of the paper's "
                                "Table (matrix and right-hand side synthetic)"),
+    "delaunay3d_64_mis": ("64^3-vertex unstructured tetrahedral mesh of the unit cube (grid vertices moved by "
+                          "random vectors of length h/2, then Delaunay), pure Laplacian of the mesh graph; "
+                          "degree-4 smoother, aggregation by the maximal independent set of the graph of A^4, "
+                          "K-cycle nu=2, tol 1e-8 (fp64): the paper's unstructured setting (synthetic mesh)"),
     "grid3d_96x32": ("96^3 7-point graph Laplacian, d=1 on boundary faces, 32 right-hand sides solved in one "
                      "batched call; degree-5 smoother, 3 passes/level, fp32 preconditioner / fp64 FCG, tol 1e-8"),
     "serve": ("continuous-batching server: pool of 16 graphs (8 random geometric, 4 2D and 4 3D grids), sizes "

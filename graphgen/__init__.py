@@ -7,7 +7,8 @@ the CPU oracle.  It holds no arithmetic of the solver: it only builds graphs
 Graphs stand in for the paper's workloads (Sec. 4): graph Laplacians of linear
 finite elements for the Poisson problem on structured 2D/3D meshes, plus a
 randomly triangulated 2D mesh and random geometric graphs for unstructured
-cases.  Every CSR produced here is symmetric, has no self loops and has
+cases, and Delaunay tetrahedralisations of perturbed 3D grids.  Every CSR
+produced here is symmetric, has no self loops and has
 strictly increasing column indices in each row.
 
 Random numbers come from splitmix64 (S. Vigna's published finaliser of the
@@ -231,6 +232,31 @@ def random_geometric(n: int, seed: int, mean_degree: float = 8.0) -> Graph:
     return csr_from_edges(int(keepv.sum()), newid[u[ke]], newid[v[ke]], name=f"rgg_{n}_s{seed}")
 
 
+def delaunay3d(N: int, seed: int) -> Graph:
+    """Graph of an unstructured tetrahedral mesh of the unit cube, built as in
+    the paper's unstructured test (Sec. 4): the N^3 vertices of a structured
+    grid of spacing h = 1/(N-1) are each moved by a random vector of length
+    h/2 (direction: the normalised vector (2u-1, 2u-1, 2u-1) with u from
+    seed, seed + 1, seed + 2), then Delaunay-tetrahedralised (Qhull, through
+    scipy.spatial).  The graph has the mesh's edges with unit weights and no
+    lower-order term (the pure Laplacian of the mesh graph)."""
+    from scipy.spatial import Delaunay
+
+    n = N * N * N
+    h = 1.0 / (N - 1)
+    ax = np.linspace(0.0, 1.0, N)
+    pts = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    dirs = np.stack([2.0 * uniform01(seed + c, n) - 1.0 for c in range(3)], -1)
+    nrm = np.linalg.norm(dirs, axis=1, keepdims=True)
+    nrm[nrm == 0.0] = 1.0
+    pts = pts + dirs / nrm * (h / 2.0)
+    tets = Delaunay(pts).simplices.astype(np.int64)
+    e = np.concatenate([tets[:, [a, b]] for a in range(4) for b in range(a + 1, 4)])
+    e.sort(axis=1)
+    e = np.unique(e[:, 0] * n + e[:, 1])
+    return csr_from_edges(n, e // n, e % n, name=f"delaunay3d_{N}_s{seed}")
+
+
 # Named workloads (sizes and seeds of the benchmark configurations).
 def workload(name: str) -> tuple[Graph, dict]:
     """Return (graph, solver parameters) for a named workload.
@@ -244,6 +270,9 @@ def workload(name: str) -> tuple[Graph, dict]:
     grid3d_128_neumann_mis : 128^3 7-point, pure (Neumann) Laplacian, degree 4,
                     aggregation by the independent set of the graph of A^4
                     (the setting of the paper's Table), RHS seed 2
+    delaunay3d_64_mis : 64^3 unstructured tetrahedral mesh (perturbed grid +
+                    Delaunay, seed 5), pure Laplacian of the mesh graph, degree
+                    4, the same aggregation (the paper's unstructured column)
     """
     if name == "grid2d_64":
         g = grid2d_5pt(64)
@@ -257,6 +286,9 @@ def workload(name: str) -> tuple[Graph, dict]:
     if name == "grid3d_128_neumann_mis":
         g = grid3d_7pt(128, None)
         return g, dict(degree=4, passes=1, rhs_seeds=[2], precision=0, aggregation=1)
+    if name == "delaunay3d_64_mis":
+        g = delaunay3d(64, 5)
+        return g, dict(degree=4, passes=1, rhs_seeds=[5], precision=0, aggregation=1)
     if name == "grid3d_96x32":
         g = grid3d_7pt(96, 1.0)
         return g, dict(degree=5, passes=3, rhs_seeds=list(range(4000, 4032)), precision=1)

@@ -39,6 +39,7 @@ CASES = {
     "grid2d_96_k4": (lambda: gg.grid2d_5pt(96), dict(degree=4, mis_k=4)),
     "rand_k3": (lambda: random_graph(3000, 0.002, 8, wmax=5, d_frac=0.02), dict(degree=4, mis_k=3)),
     "rgg_k4": (lambda: gg.random_geometric(20000, 61), dict(degree=4, mis_k=4)),
+    "delaunay_16_k2": (lambda: gg.delaunay3d(16, 5), dict(degree=4, mis_k=2)),
 }
 
 
@@ -61,7 +62,7 @@ def test_mis_hierarchy_bit_exact(amg, orc, name):
 
 
 @pytest.mark.parametrize("cycle", [0, 1])
-@pytest.mark.parametrize("name", ["grid3d_24_pure_k4", "rand_k3", "rgg_k4"])
+@pytest.mark.parametrize("name", ["grid3d_24_pure_k4", "rand_k3", "rgg_k4", "delaunay_16_k2"])
 def test_mis_solve_matches_oracle(amg, orc, name, cycle):
     make, opts = CASES[name]
     g = make()

@@ -58,6 +58,7 @@ GRAPHS = {
     "grid3d_20_d": (lambda: gg.grid3d_7pt(20, 1.0), dict(degree=5, passes=3)),
     "rdiag_48": (lambda: gg.grid2d_random_diag(48, 3), dict(degree=4, passes=3)),
     "rand_w": (lambda: random_graph(700, 0.006, 3, wmax=4, d_frac=0.05), dict(degree=4, passes=2)),
+    "delaunay_14": (lambda: gg.delaunay3d(14, 5), dict(degree=4, passes=3)),
     "rgg_3000": (lambda: gg.random_geometric(3000, 5), dict(degree=4, passes=3)),
 }
 
