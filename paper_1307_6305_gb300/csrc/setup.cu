@@ -475,7 +475,8 @@ template <typename M>
 __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                               const double *__restrict__ val, const int *__restrict__ agg, M mb,
                               const int64_t *__restrict__ seg, int *__restrict__ keyJ,
-                              double *__restrict__ kval, int *__restrict__ count, int *longrows) {
+                              double *__restrict__ kval, int *__restrict__ count, int *longrows, int *huge,
+                              unsigned long long *hugeoff) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   const int64_t s0 = seg[I];
@@ -524,7 +525,15 @@ __global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int3
     count[I] = 0;
     return;
   }
-  for (int64_t a = 1; a < len; ++a) {  // stable insertion sort by J (very long rows only)
+  if (huge) {
+    // very long row: stable radix sort by k_gal_sort_huge through scratch
+    const int r = atomicAdd(huge, 1);
+    huge[1 + r] = I;
+    hugeoff[1 + r] = atomicAdd(hugeoff, (unsigned long long)len);
+    count[I] = 0;
+    return;
+  }
+  for (int64_t a = 1; a < len; ++a) {  // stable insertion sort by J (no scratch given)
     const int kj = keyJ[s0 + a];
     const double kv = kval[s0 + a];
     int64_t b = a - 1;
@@ -609,6 +618,99 @@ __global__ void __launch_bounds__(kSortThreads) k_gal_sort_long(const int64_t *_
   }
 }
 
+// Stable LSD radix sort, 4-bit digits, of key[0, len) (keys in [0, 2^bits))
+// with an optional payload, by one block of kRadixThreads threads, through
+// global scratch of the same length.  Thread t owns the t-th contiguous chunk
+// and scatters it in order, so equal keys keep their order.  Ends with the
+// result in key/val and a block barrier.
+constexpr int kRadixThreads = 256;
+__device__ void block_radix_sort(int *key, double *val, int *tk, double *tv, int len, int bits, int *cnt) {
+  const int t = threadIdx.x, T = kRadixThreads;
+  const int chunk = (len + T - 1) / T;
+  const int a0 = min(len, t * chunk), a1 = min(len, a0 + chunk);
+  int *src = key, *dst = tk;
+  double *vs = val, *vd = tv;
+  for (int shift = 0; shift < bits; shift += 4) {
+    for (int d = 0; d < 16; ++d) cnt[d * T + t] = 0;
+    for (int a = a0; a < a1; ++a) ++cnt[((src[a] >> shift) & 15) * T + t];
+    __syncthreads();
+    if (t < 16) {  // exclusive scan of digit t over the threads
+      int run = 0;
+      for (int u = 0; u < T; ++u) {
+        const int c = cnt[t * T + u];
+        cnt[t * T + u] = run;
+        run += c;
+      }
+      cnt[16 * T + t] = run;  // digit total
+    }
+    __syncthreads();
+    if (t == 0) {  // digit bases
+      int run = 0;
+      for (int d = 0; d < 16; ++d) {
+        const int c = cnt[16 * T + d];
+        cnt[16 * T + d] = run;
+        run += c;
+      }
+    }
+    __syncthreads();
+    for (int a = a0; a < a1; ++a) {
+      const int d = (src[a] >> shift) & 15;
+      const int pos = cnt[16 * T + d] + cnt[d * T + t]++;
+      dst[pos] = src[a];
+      if (vs) vd[pos] = vs[a];
+    }
+    __syncthreads();
+    int *ts = src;
+    src = dst;
+    dst = ts;
+    double *tvv = vs;
+    vs = vd;
+    vd = tvv;
+  }
+  if (src != key) {
+    for (int a = t; a < len; a += T) {
+      key[a] = src[a];
+      if (val) val[a] = vs[a];
+    }
+  }
+  __syncthreads();
+}
+
+// Galerkin rows of more than kBlockSort entries (a few coarse rows of a small,
+// dense level): one block per row, radix sort by J (J < nH: `bits` bits),
+// then the count of distinct J != I
+__global__ void __launch_bounds__(kRadixThreads) k_gal_sort_huge(const int64_t *__restrict__ seg, int *keyJ,
+                                                                 double *kval, int *__restrict__ count,
+                                                                 const int *huge, const unsigned long long *hugeoff,
+                                                                 int *skey, double *sval, int bits) {
+  __shared__ int cnt[17 * kRadixThreads];
+  __shared__ int tot;
+  const int nh = huge[0];
+  for (int r = blockIdx.x; r < nh; r += gridDim.x) {
+    const int I = huge[1 + r];
+    const int64_t s0 = seg[I];
+    const int len = (int)(seg[I + 1] - s0);
+    int *key = keyJ + s0;
+    double *val = kval + s0;
+    block_radix_sort(key, val, skey + hugeoff[1 + r], sval + hugeoff[1 + r], len, bits, cnt);
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    int c = 0;
+    for (int a = threadIdx.x; a < len; a += kRadixThreads)
+      if (key[a] != I && (a == 0 || key[a - 1] != key[a])) ++c;
+    atomicAdd(&tot, c);
+    __syncthreads();
+    if (threadIdx.x == 0) count[I] = tot;
+    __syncthreads();
+  }
+}
+
+static inline int bits_for(int64_t n) {  // bits of the largest value below n
+  int b = 1;
+  while (b < 31 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
 template <typename M>
 __global__ void k_pair_emit(int nH, const int64_t *__restrict__ seg, const int *__restrict__ keyJ,
                             const double *__restrict__ kval, const int64_t *__restrict__ rpH,
@@ -666,7 +768,7 @@ __global__ void k_agg_sort(int nH, const int *__restrict__ ptr, int *__restrict_
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   const int a0 = ptr[I], a1 = ptr[I + 1];
-  if (longlist && a1 - a0 > kAggShort && a1 - a0 <= 8192) {
+  if (longlist && a1 - a0 > kAggShort) {  // block sorts; k_agg_sort_long takes <= 8192
     longlist[1 + atomicAdd(longlist, 1)] = I;
     return;
   }
@@ -678,6 +780,7 @@ __global__ void k_agg_sort(int nH, const int *__restrict__ ptr, int *__restrict_
 }
 
 // one block per long member list: bitonic sort of the (distinct) vertex ids
+// for lists of up to 8192 members (longer ones: k_agg_sort_huge)
 __global__ void __launch_bounds__(128) k_agg_sort_long(const int *__restrict__ ptr, int *__restrict__ mem,
                                                         const int *longlist) {
   __shared__ int key[8192];
@@ -685,6 +788,7 @@ __global__ void __launch_bounds__(128) k_agg_sort_long(const int *__restrict__ p
   for (int r = blockIdx.x; r < nlong; r += gridDim.x) {
     const int I = longlist[1 + r];
     const int a0 = ptr[I], len = ptr[I + 1] - a0;
+    if (len > 8192) continue;  // block-uniform
     int p2 = 1;
     while (p2 < len) p2 <<= 1;
     for (int a = threadIdx.x; a < p2; a += blockDim.x) key[a] = a < len ? mem[a0 + a] : 0x7fffffff;
@@ -707,8 +811,22 @@ __global__ void __launch_bounds__(128) k_agg_sort_long(const int *__restrict__ p
   }
 }
 
+// member lists of more than 8192 members: one block each, radix sort of the
+// vertex ids (< n: `bits` bits) through scratch[ptr[I], ptr[I+1])
+__global__ void __launch_bounds__(kRadixThreads) k_agg_sort_huge(const int *__restrict__ ptr, int *mem,
+                                                                 const int *longlist, int *scratch, int bits) {
+  __shared__ int cnt[17 * kRadixThreads];
+  const int nlong = longlist[0];
+  for (int r = blockIdx.x; r < nlong; r += gridDim.x) {
+    const int I = longlist[1 + r];
+    const int a0 = ptr[I], len = ptr[I + 1] - a0;
+    if (len <= 8192) continue;  // block-uniform
+    block_radix_sort(mem + a0, nullptr, scratch + a0, nullptr, len, bits, cnt);
+  }
+}
+
 // sort member lists (ptr, mem) of nH aggregates in ascending order
-static amg_status sort_members(amg_handle_s *h, int nH, const int *ptr, int *mem) {
+static amg_status sort_members(amg_handle_s *h, int n, int nH, const int *ptr, int *mem) {
   cudaStream_t st = h->stream;
   int *longlist = nullptr;
   AMG_TRY(pool_alloc((void **)&longlist, sizeof(int) * (size_t)(nH + 1), st));
@@ -717,6 +835,14 @@ static amg_status sort_members(amg_handle_s *h, int nH, const int *ptr, int *mem
   LAUNCH_CHECK(&h->launches);
   k_agg_sort_long<<<std::max(1, std::min(nH, 4 * 152)), 128, 0, st>>>(ptr, mem, longlist);
   LAUNCH_CHECK(&h->launches);
+  // lists of more than 8192 members (some aggregate that large); the pass
+  // skips every other list
+  int *scratch = nullptr;
+  AMG_TRY(pool_alloc((void **)&scratch, sizeof(int) * (size_t)std::max(n, 1), st));
+  k_agg_sort_huge<<<std::max(1, std::min(nH, 152)), kRadixThreads, 0, st>>>(ptr, mem, longlist, scratch,
+                                                                            bits_for(n));
+  LAUNCH_CHECK(&h->launches);
+  pool_free(scratch, st);
   pool_free(longlist, st);
   return AMG_OK;
 }
@@ -901,12 +1027,37 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   AMG_TRY(pool_alloc((void **)&keyJ, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
   AMG_TRY(pool_alloc((void **)&kval, sizeof(double) * (size_t)std::max<int64_t>(segtot, 1), st));
   AMG_TRY(pool_alloc((void **)&count, sizeof(int64_t) * (size_t)(nH + 1), st));
-  int *longrows = nullptr;  // [0]: count, then the long rows
+  int *longrows = nullptr, *huge = nullptr;  // [0]: count, then the rows
+  unsigned long long *hugeoff = nullptr;     // [0]: total length, then scratch offsets
   AMG_TRY(pool_alloc((void **)&longrows, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&huge, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&hugeoff, sizeof(unsigned long long) * (size_t)(nH + 1), st));
   AMG_CUDA_TRY(cudaMemsetAsync(longrows, 0, sizeof(int), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(huge, 0, sizeof(int), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(hugeoff, 0, sizeof(unsigned long long), st));
   k_pair_gather<<<blocks_for(nH, 128), 128, 0, st>>>(nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, mb, seg, keyJ,
-                                                     kval, count, longrows);
+                                                     kval, count, longrows, huge, hugeoff);
   LAUNCH_CHECK(&h->launches);
+  {
+    int nhuge = 0;
+    unsigned long long hugetot = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&nhuge, huge, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaMemcpyAsync(&hugetot, hugeoff, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (nhuge > 0) {
+      int *skey = nullptr;
+      double *sval = nullptr;
+      AMG_TRY(pool_alloc((void **)&skey, sizeof(int) * (size_t)hugetot, st));
+      AMG_TRY(pool_alloc((void **)&sval, sizeof(double) * (size_t)hugetot, st));
+      k_gal_sort_huge<<<std::min(nhuge, 152), kRadixThreads, 0, st>>>(seg, keyJ, kval, count, huge, hugeoff, skey,
+                                                                       sval, bits_for(nH));
+      LAUNCH_CHECK(&h->launches);
+      pool_free(skey, st);
+      pool_free(sval, st);
+    }
+  }
+  pool_free(huge, st);
+  pool_free(hugeoff, st);
   AMG_TRY(sort_kernels_ready());
   k_gal_sort_long<<<std::max(1, std::min(nH, 4 * 152)), kSortThreads, kGalSortSmem, st>>>(seg, keyJ, kval, count,
                                                                                           longrows);
@@ -1128,7 +1279,7 @@ static amg_status coarsen_mis_pass(amg_handle_s *h, const LevelBuild &cur, Level
   AMG_TRY(exclusive_scan_i32(cnt, ptr, nH + 1, st, &tot));
   k_agg_place<<<blocks_for(n, 256), 256, 0, st>>>(n, aggp, ptr, fill, mem);
   LAUNCH_CHECK(&h->launches);
-  AMG_TRY(sort_members(h, nH, ptr, mem));
+  AMG_TRY(sort_members(h, n, nH, ptr, mem));
   AMG_TRY(galerkin(h, cur, aggp, ListMembers{ptr, mem}, nH, next));
   for (void *p : {(void *)cnt, (void *)fill, (void *)ptr, (void *)mem}) pool_free(p, st);
   *nH_out = nH;
@@ -1217,7 +1368,7 @@ static amg_status build_agg_lists(amg_handle_s *h, amg::Level &L) {
   AMG_TRY(exclusive_scan_i32(cnt, L.agg_ptr, L.nH + 1, st, &tot));
   k_agg_place<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.agg, L.agg_ptr, fill, L.agg_mem);
   LAUNCH_CHECK(&h->launches);
-  AMG_TRY(sort_members(h, L.nH, L.agg_ptr, L.agg_mem));
+  AMG_TRY(sort_members(h, L.n, L.nH, L.agg_ptr, L.agg_mem));
   pool_free(cnt, st);
   pool_free(fill, st);
   return AMG_OK;
