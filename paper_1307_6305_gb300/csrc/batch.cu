@@ -607,9 +607,12 @@ static std::map<std::string, std::pair<int, int>> g_tuned;
 // AMG_GB300_BATCH=<kb>,<tile> forces one.
 static amg_status autotune(amg_handle_s *h, int nrhs) {
   const int cap = std::min(kMaxBlock, pow2_at_least(nrhs));
+  // the decision depends on the hierarchy's shape: key it by the problem and
+  // every option that changes the levels or the cycle
   char key[200];
-  snprintf(key, sizeof(key), "d%d_n%lld_nnz%lld_r%d_p%d_m%d", h->device, (long long)h->n,
-           (long long)h->lv[0].A.nnz, cap, h->opt.precision, h->opt.degree);
+  snprintf(key, sizeof(key), "d%d_n%lld_nnz%lld_r%d_p%d_m%d_s%d_a%d_k%d_nu%d", h->device, (long long)h->n,
+           (long long)h->lv[0].A.nnz, cap, h->opt.precision, h->opt.degree, h->opt.passes, h->opt.aggregation,
+           h->opt.mis_k, h->opt.inner_iters);
   if (h->tuned_for == cap) return AMG_OK;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
