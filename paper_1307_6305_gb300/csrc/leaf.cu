@@ -9,9 +9,11 @@
 // preconditioned by the K-cycle at k0: smoothing, restriction, the inner
 // solve at k0+1 preconditioned by the dense two-level operator B,
 // prolongation, smoothing; Sec. 3, Sec. 4) on one cluster of C CTAs:
-//   * CTA c owns a contiguous block of rows on both levels and keeps its rows
-//     of A_k0 and A_k0+1 (compact CSR, no slice padding) and of B in shared
-//     memory;
+//   * CTA c owns a contiguous block of rows on both levels and keeps in
+//     shared memory its rows of A_k0 and of the smoother form 2 t(A_k0)
+//     (compact CSR, no slice padding) and its rows of B and of A_k0+1 B
+//     (computed once per setup), so a coarse inner step forms D = B r and
+//     W = A_k0+1 D = (A_k0+1 B) r in one phase;
 //   * every vector that some phase reads at another CTA's rows is kept as a
 //     full copy in every CTA's shared memory; the phase that produces it
 //     writes each new entry into all C copies with distributed-shared-memory
@@ -60,16 +62,16 @@ enum LeafArr : int {
   A_HB, A_HR, A_HX, A_HD0,
   // owned rows, level k0+1 (RH entries of T)
   A_HW0 = A_HD0 + kLeafMaxInner,
-  // compact CSR of the owned rows of A_k0 (off-diagonal) and its diagonal
-  A_LRP = A_HW0 + kLeafMaxInner, A_LCOL, A_LVAL, A_LDIAG,
+  // compact CSR of the owned rows of A_k0 (off-diagonal) and its diagonal,
+  // and the values and diagonal of the smoother form S = 2 t(A) on the same
+  // pattern (2 sa a_ij; 2 sa a_ii - 2 ca)
+  A_LRP = A_HW0 + kLeafMaxInner, A_LCOL, A_LVAL, A_LDIAG, A_SVAL, A_SDIAG,
   // aggregate id of every row of level k0
   A_AGG,
   // member lists of the owned aggregates
   A_LAP, A_LAM,
-  // compact CSR of the owned rows of A_k0+1 and its diagonal
-  A_HRP, A_HCOL, A_HVAL, A_HDIAG,
-  // owned rows of B (fp64, nH columns)
-  A_BROWS,
+  // owned rows of B and of A_k0+1 B (fp64, nH columns)
+  A_BROWS, A_ABROWS,
   // dot-product slot tables [2][C][kLeafSlot] and per-warp partials
   A_SLOTS, A_WRED,
   A_COUNT
@@ -77,18 +79,15 @@ enum LeafArr : int {
 
 template <typename T>
 struct LeafParams {
-  int n, nH, C, R, RH, m, nu, tpr, tprH;
-  int maxnz, maxnzH, maxmem;
-  T sa, ca;
+  int n, nH, C, R, RH, m, nu, tpr;
+  int maxnz, maxmem;
+  double two_sa, two_ca;  // smoother form: 2 sa = 4/(l1 - l0), 2 ca = 2 (l1 + l0)/(l1 - l0)
   T coef[kMaxDegree + 1];
   const int64_t *rp;
   const int32_t *col;
   const double *val, *diag;
   const int32_t *agg, *agg_ptr, *agg_mem;
-  const int64_t *rpH;
-  const int32_t *colH;
-  const double *valH, *diagH;
-  const double *B;
+  const double *B, *AB;   // B and A_k0+1 B, nH x nH row major
   const T *b;
   T *x;
   unsigned off[A_COUNT];  // byte offsets into dynamic shared memory
@@ -116,20 +115,16 @@ static unsigned leaf_layout(LeafParams<T> &P) {
   esz[A_LCOL] = sizeof(int);
   cnt[A_LVAL] = P.maxnz;
   cnt[A_LDIAG] = P.R;
+  cnt[A_SVAL] = P.maxnz;
+  cnt[A_SDIAG] = P.R;
   cnt[A_AGG] = P.n;
   esz[A_AGG] = sizeof(int);
   cnt[A_LAP] = P.RH + 1;
   esz[A_LAP] = sizeof(int);
   cnt[A_LAM] = P.maxmem;
   esz[A_LAM] = sizeof(int);
-  cnt[A_HRP] = P.RH + 1;
-  esz[A_HRP] = sizeof(int);
-  cnt[A_HCOL] = P.maxnzH;
-  esz[A_HCOL] = sizeof(int);
-  cnt[A_HVAL] = P.maxnzH;
-  cnt[A_HDIAG] = P.RH;
-  cnt[A_BROWS] = (size_t)P.RH * P.nH;
-  esz[A_BROWS] = sizeof(double);
+  cnt[A_BROWS] = cnt[A_ABROWS] = (size_t)P.RH * P.nH;
+  esz[A_BROWS] = esz[A_ABROWS] = sizeof(double);
   cnt[A_SLOTS] = 2 * (size_t)P.C * kLeafSlot;
   esz[A_SLOTS] = sizeof(double);
   cnt[A_WRED] = kLeafWarps * kLeafSlot;
@@ -162,9 +157,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
   T *xo = vec(A_XO);
   T *hb = vec(A_HB), *hr = vec(A_HR), *hx = vec(A_HX);
   int *lrp = ivec(A_LRP), *lcol = ivec(A_LCOL), *agg = ivec(A_AGG), *lap = ivec(A_LAP), *lam = ivec(A_LAM);
-  int *hrp = ivec(A_HRP), *hcol = ivec(A_HCOL);
-  T *lval = vec(A_LVAL), *ldiag = vec(A_LDIAG), *hval = vec(A_HVAL), *hdiag = vec(A_HDIAG);
+  T *lval = vec(A_LVAL), *ldiag = vec(A_LDIAG), *sval = vec(A_SVAL), *sdiag = vec(A_SDIAG);
   double *brows = reinterpret_cast<double *>(sm + P.off[A_BROWS]);
+  double *abrows = reinterpret_cast<double *>(sm + P.off[A_ABROWS]);
   double *slots = reinterpret_cast<double *>(sm + P.off[A_SLOTS]);
   double *wred = reinterpret_cast<double *>(sm + P.off[A_WRED]);
   __shared__ double s_sc[40];
@@ -176,31 +171,29 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
   }
   const int64_t e0 = P.rp[r0c];
   for (int li = tid; li <= nloc; li += kLeafThreads) lrp[li] = (int)(P.rp[r0c + li] - e0);
-  for (int li = tid; li < nloc; li += kLeafThreads) ldiag[li] = (T)P.diag[r0 + li];
+  for (int li = tid; li < nloc; li += kLeafThreads) {
+    const double dg = P.diag[r0 + li];
+    ldiag[li] = (T)dg;
+    sdiag[li] = (T)(P.two_sa * dg - P.two_ca);  // as the multi-kernel path stores it
+  }
   {
     const int cnt = (int)(P.rp[r0c + nloc] - e0);
     for (int e = tid; e < cnt; e += kLeafThreads) {
       lcol[e] = P.col[e0 + e];
       lval[e] = (T)P.val[e0 + e];
+      sval[e] = (T)(P.two_sa * P.val[e0 + e]);
     }
   }
-  const int64_t f0 = P.rpH[h0c];
   const int a0 = P.agg_ptr[h0c];
-  for (int lI = tid; lI <= nlocH; lI += kLeafThreads) {
-    hrp[lI] = (int)(P.rpH[h0c + lI] - f0);
-    lap[lI] = P.agg_ptr[h0c + lI] - a0;
-  }
-  for (int lI = tid; lI < nlocH; lI += kLeafThreads) hdiag[lI] = (T)P.diagH[h0 + lI];
+  for (int lI = tid; lI <= nlocH; lI += kLeafThreads) lap[lI] = P.agg_ptr[h0c + lI] - a0;
   {
-    const int cnt = (int)(P.rpH[h0c + nlocH] - f0);
-    for (int e = tid; e < cnt; e += kLeafThreads) {
-      hcol[e] = P.colH[f0 + e];
-      hval[e] = (T)P.valH[f0 + e];
-    }
     const int mc = P.agg_ptr[h0c + nlocH] - a0;
     for (int e = tid; e < mc; e += kLeafThreads) lam[e] = P.agg_mem[a0 + e];
   }
-  for (int e = tid; e < nlocH * nH; e += kLeafThreads) brows[e] = P.B[(size_t)h0c * nH + e];
+  for (int e = tid; e < nlocH * nH; e += kLeafThreads) {
+    brows[e] = P.B[(size_t)h0c * nH + e];
+    abrows[e] = P.AB[(size_t)h0c * nH + e];
+  }
   cl.sync();  // every CTA has started and loaded before any remote store
 
   // ---- building blocks ----
@@ -213,30 +206,20 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
   // but only lane q == 0 may write (a row's vectors are read and written in
   // place within one phase, e.g. x += c_j T_j, so a second writer could race
   // with a slower reader of the same row).
-  auto sweep = [&](auto xf, auto epi) {
+  // off-diagonal values `vals`: lval (A) or sval (the smoother form S)
+  auto sweepv = [&](const T *vals, auto xf, auto epi) {
     const int tpr = P.tpr, q = tid & (tpr - 1), per = kLeafThreads / tpr;
     for (int base = 0; base < P.R; base += per) {
       const int li = base + tid / tpr;
       const bool ok = li < nloc;
       T acc = T(0);
       if (ok)
-        for (int e = lrp[li] + q; e < lrp[li + 1]; e += tpr) acc = fma(lval[e], xf(lcol[e]), acc);
+        for (int e = lrp[li] + q; e < lrp[li + 1]; e += tpr) acc = fma(vals[e], xf(lcol[e]), acc);
       for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (ok) epi(li, r0 + li, acc, q);
     }
   };
-  auto sweepH = [&](auto xf, auto epi) {
-    const int tpr = P.tprH, q = tid & (tpr - 1), per = kLeafThreads / tpr;
-    for (int base = 0; base < P.RH; base += per) {
-      const int lI = base + tid / tpr;
-      const bool ok = lI < nlocH;
-      T acc = T(0);
-      if (ok)
-        for (int e = hrp[lI] + q; e < hrp[lI + 1]; e += tpr) acc = fma(hval[e], xf(hcol[e]), acc);
-      for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (ok) epi(lI, h0 + lI, acc, q);
-    }
-  };
+  auto sweep = [&](auto xf, auto epi) { sweepv(lval, xf, epi); };
   // dot products: post this CTA's nd partial sums (nd <= kLeafSlot, static
   // register indices) to every CTA's slot table
   int sb = 0;
@@ -299,13 +282,13 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
       cl.sync();
       return;
     }
-    const T sa = P.sa, ca = P.ca, b0 = P.coef[0], b1 = P.coef[1];
-    sweep([&](int j) { return r[j]; },
+    const T b0 = P.coef[0], b1 = P.coef[1];
+    // T_1 = S r / 2, T_{j+1} = S T_j - T_{j-1} with the stored smoother form
+    sweepv(sval, [&](int j) { return r[j]; },
           [&](int li, int i, T acc, int q) {
             if (q != 0) return;
             const T ri = r[i];
-            const T Ar = fma(ldiag[li], ri, acc);
-            const T t1 = fma(sa, Ar, -ca * ri);
+            const T t1 = T(0.5) * fma(sdiag[li], ri, acc);
             if (m > 1) put(vTa, i, t1);
             const T inc = fma(b1, t1, b0 * ri);
             const T v = add ? x[i] + inc : inc;
@@ -319,12 +302,10 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
       T *Tn = (j == 2) ? vTb : const_cast<T *>(Tp);
       const T bj = P.coef[j];
       const bool last = (j == m);
-      sweep([&](int jj) { return Tc[jj]; },
+      sweepv(sval, [&](int jj) { return Tc[jj]; },
             [&](int li, int i, T acc, int q) {
               if (q != 0) return;
-              const T tc = Tc[i];
-              const T At = fma(ldiag[li], tc, acc);
-              const T tn = T(2) * fma(sa, At, -ca * tc) - Tp[i];  // Tp[i] read before Tn[i] (may alias) is written
+              const T tn = fma(sdiag[li], Tc[i], acc) - Tp[i];  // Tp[i] read before Tn[i] (may alias) is written
               const T v = fma(bj, tn, x[i]);
               if (!last) put(Tn, i, tn);
               if (last) put(x, i, v);
@@ -343,33 +324,39 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
     for (int it = 0; it < nu; ++it) {
       const T *rin = (it == 0) ? hb : hr;
       T *D = vec(A_HD0 + it), *W = vec(A_HW0 + it);
-      // D = B rin (fp64), one warp per owned row
+      // D = B rin and W = A D = (A B) rin in one pass (fp64, one warp per
+      // owned row; both only at owned rows, so no copy is broadcast), with
+      // rho = D.W, sigma = rin.D (step 0) or D_l.W (step > 0)
+      double dv[kLeafSlot] = {};
       for (int base = 0; base < P.RH; base += kLeafWarps) {
         const int lI = base + warp;
         const bool ok = lI < nlocH;
-        double acc = 0.0;
+        double ad = 0.0, aw = 0.0;
         if (ok)
-          for (int j = lane; j < nH; j += 32) acc = fma(brows[(size_t)lI * nH + j], (double)rin[j], acc);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (ok && lane < C) *cl.map_shared_rank(D + h0 + lI, (unsigned)lane) = (T)acc;
-      }
-      cl.sync();
-      double dv[kLeafSlot] = {};
-      // W = A D with rho = D.W, sigma = rin.D (step 0) or D_l.W (step > 0)
-      sweepH([&](int j) { return D[j]; },
-             [&](int lI, int I, T acc, int q) {
-               if (q != 0) return;
-               const T w = fma(hdiag[lI], D[I], acc);
-               W[lI] = w;
-               if (it == 0) {
-                 dv[0] += (double)D[I] * (double)w;
-                 dv[1] += (double)rin[I] * (double)D[I];
-               } else {
+          for (int j = lane; j < nH; j += 32) {
+            const double rj = (double)rin[j];
+            ad = fma(brows[(size_t)lI * nH + j], rj, ad);
+            aw = fma(abrows[(size_t)lI * nH + j], rj, aw);
+          }
+        for (int o = 16; o > 0; o >>= 1) {
+          ad += __shfl_xor_sync(0xffffffffu, ad, o);
+          aw += __shfl_xor_sync(0xffffffffu, aw, o);
+        }
+        if (ok && lane == 0) {
+          const int I = h0 + lI;
+          const T d = (T)ad, w = (T)aw;
+          D[I] = d;
+          W[lI] = w;
+          if (it == 0) {
+            dv[0] += (double)d * (double)w;
+            dv[1] += (double)rin[I] * (double)d;
+          } else {
 #pragma unroll
-                 for (int l = 0; l < kLeafMaxInner; ++l)
-                   if (l < it) dv[l] += (double)vec(A_HD0 + l)[I] * (double)w;
-               }
-             });
+            for (int l = 0; l < kLeafMaxInner; ++l)
+              if (l < it) dv[l] += (double)vec(A_HD0 + l)[I] * (double)w;
+          }
+        }
+      }
       post(dv, it == 0 ? 2 : it);
       cl.sync();
       fold(sums, it == 0 ? 2 : it);
@@ -516,6 +503,19 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ L
   }
 }
 
+// AB = A B for the CSR operator A (off-diagonal part + diagonal) and the
+// dense row-major B, n x n: thread per entry, fp64
+__global__ void k_dense_ab(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ diag,
+                           const double *__restrict__ B, double *__restrict__ AB) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), c = (int)(idx % n);
+  double acc = diag[i] * B[idx];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = fma(val[p], B[(int64_t)col[p] * n + c], acc);
+  AB[idx] = acc;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -555,10 +555,9 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
   const Level &L = h->lv[k0];
   const Level &N = h->lv[k0 + 1];
   const int n = L.n, nH = N.n;
-  std::vector<int64_t> rp(n + 1), rpH(nH + 1);
+  std::vector<int64_t> rp(n + 1);
   std::vector<int32_t> ap(nH + 1);
   AMG_CUDA_TRY(cudaMemcpyAsync(rp.data(), L.A.rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
-  AMG_CUDA_TRY(cudaMemcpyAsync(rpH.data(), N.A.rowptr, sizeof(int64_t) * (nH + 1), cudaMemcpyDeviceToHost, h->stream));
   AMG_CUDA_TRY(cudaMemcpyAsync(ap.data(), L.agg_ptr, sizeof(int32_t) * (nH + 1), cudaMemcpyDeviceToHost, h->stream));
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
   int optin = 0;
@@ -578,20 +577,16 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     P.nu = h->opt.inner_iters;
     int tpr = 8;
     while (tpr > 1 && P.R * tpr > kLeafThreads) tpr >>= 1;
-    int tprH = 8;
-    while (tprH > 1 && P.RH * tprH > kLeafThreads) tprH >>= 1;
     // AMG_GB300_LEAF_TPR=1|2|4|8 overrides the lanes per row on level k0
     if (const char *e = getenv("AMG_GB300_LEAF_TPR")) {
       const int v = atoi(e);
       if (v == 1 || v == 2 || v == 4 || v == 8) tpr = v;
     }
     P.tpr = tpr;
-    P.tprH = tprH;
     for (int c = 0; c < C; ++c) {
       const int a = std::min(n, c * P.R), b = std::min(n, (c + 1) * P.R);
       const int aH = std::min(nH, c * P.RH), bH = std::min(nH, (c + 1) * P.RH);
       P.maxnz = std::max(P.maxnz, (int)(rp[b] - rp[a]));
-      P.maxnzH = std::max(P.maxnzH, (int)(rpH[bH] - rpH[aH]));
       P.maxmem = std::max(P.maxmem, ap[bH] - ap[aH]);
     }
     if (leaf_layout(P) > (unsigned)max_dynamic) continue;
@@ -612,8 +607,8 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
       cudaGetLastError();
       continue;
     }
-    P.sa = (T)(2.0 / (L.lam1 - L.lam0));
-    P.ca = (T)((L.lam1 + L.lam0) / (L.lam1 - L.lam0));
+    P.two_sa = 4.0 / (L.lam1 - L.lam0);
+    P.two_ca = 2.0 * (L.lam1 + L.lam0) / (L.lam1 - L.lam0);
     for (int j = 0; j <= P.m; ++j) P.coef[j] = (T)L.coef[j];
     P.rp = L.A.rowptr;
     P.col = L.A.col;
@@ -622,11 +617,16 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     P.agg = L.agg;
     P.agg_ptr = L.agg_ptr;
     P.agg_mem = L.agg_mem;
-    P.rpH = N.A.rowptr;
-    P.colH = N.A.col;
-    P.valH = N.A.val;
-    P.diagH = N.diag;
+    // A_k0+1 B, once per setup
+    double *AB = nullptr;
+    AMG_TRY(h->arena.alloc((void **)&AB, sizeof(double) * (size_t)nH * nH));
+    const int64_t nn = (int64_t)nH * nH;
+    k_dense_ab<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(nH, N.A.rowptr, N.A.col, N.A.val, N.diag, h->Bd,
+                                                                    AB);
+    AMG_CUDA_TRY(cudaGetLastError());
+    ++h->launches;
     P.B = h->Bd;
+    P.AB = AB;
     P.b = (const T *)L.b;
     P.x = (T *)L.x;
     LeafParams<T> *hp = new LeafParams<T>(P);
