@@ -11,9 +11,11 @@
  * (coarse)), with the smoother R = q_m(A), q_m the polynomial of best uniform
  * approximation to 1/x on [lambda1/10, ||A||_inf] (Sec. 3, Eq. (1x-1-min)).
  * Aggregates are built on the device by handshake matching (Sec. 2: a
- * matching is the simplest graph partitioning), several passes per level;
- * coarse operators are the Galerkin products P^T A P (Sec. 3 remark; Sec. 5:
- * sums of fine entries over aggregate pairs).
+ * matching is the simplest graph partitioning), several passes per level, or
+ * by the paper's maximal independent sets of the graph of A^k (Sec. 2 steps
+ * (A)-(B), option `aggregation`); coarse operators are the Galerkin products
+ * P^T A P (Sec. 3 remark; Sec. 5: sums of fine entries over aggregates).  The
+ * stationary AMLI W-cycle of Sec. 4 is option `cycle`.
  *
  * Conventions for every entry point:
  *  - Status codes only; nothing throws across this boundary.  After an error
@@ -52,16 +54,18 @@ typedef enum {
   AMG_ERR_NOT_CONVERGED = 8,  /* max_iters reached; x and info hold the last iterate */
   AMG_ERR_BREAKDOWN = 9,      /* outer CG: d^T A d <= 0 or non-finite              */
   AMG_ERR_TIMEOUT = 10,       /* a bounded device-side wait ran out                */
-  AMG_ERR_SETUP_STALL = 11    /* matching cannot coarsen a level of > 4096 vertices */
+  AMG_ERR_SETUP_STALL = 11    /* aggregation cannot coarsen a level of > 4096 vertices */
 } amg_status;
 
 enum { AMG_MEM_HOST = 0, AMG_MEM_DEVICE = 1 };
 enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1 };
 
-/* Solver options; amg_default_options() fills the paper's choices. */
+/* Solver options; amg_default_options() fills the defaults listed there
+ * (the paper's degree, interval, cycle and restart; matching aggregation). */
 typedef struct {
   int degree;          /* m, degree of q_m (Sec. 4 uses 4); 0..16                 */
-  int passes;          /* matching passes composed per level (~2^passes per aggregate) */
+  int passes;          /* matching passes composed per level (~2^passes per
+                          aggregate); AMG_AGG_MATCHING only                        */
   int coarse_max;      /* coarsen until n_k <= coarse_max; coarsest solved densely */
   int max_levels;      /* cap on the number of levels                              */
   int inner_iters;     /* nu: flexible-CG steps on coarse levels (2 = W-cycle)     */
@@ -73,7 +77,8 @@ typedef struct {
                           outer dots/orthogonalisation and the coarsest dense
                           solve stay fp64                                          */
   double lambda0_ratio;/* lambda0 = ratio * ||A_k||_inf (Sec. 4: 1/10)             */
-  uint64_t hash_salt;  /* salt of the matching tie-break hash                      */
+  uint64_t hash_salt;  /* salt of the matching tie-break hash and of the keys of
+                          AMG_AGG_MIS                                            */
   int cycle;           /* AMG_CYCLE_K: nonlinear AMLI cycle (K-cycle), inner
                           flexible CG on coarse levels.  AMG_CYCLE_AMLI:
                           stationary AMLI W-cycle (Sec. 4), a fixed polynomial
