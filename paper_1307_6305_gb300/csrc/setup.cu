@@ -468,7 +468,9 @@ __global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, M mb, int6
   len[I] = l;
 }
 // gather mapped entries of the coarse row into its segment, stable-sort by J,
-// count distinct J != I
+// count distinct J != I.  Rows of up to kLocalSort entries are sorted here by
+// their thread; longer rows are listed for k_gal_sort_long (up to kBlockSort,
+// bitonic in shared memory) or k_gal_sort_huge (radix through scratch).
 constexpr int kLocalSort = 64;
 constexpr int kBlockSort = 8192;  // longest row sorted in shared memory (128 KB)
 template <typename M>
