@@ -155,3 +155,40 @@ def test_history_and_stopping(orc):
     assert r.true_rel_residual < 1e-7
     r2 = orc.Hierarchy(g, degree=5, passes=3, max_iters=2).solve(gg.rhs(g.n, 2, False))
     assert r2.status == orc.ERR_NOT_CONVERGED and r2.iterations == 2
+
+
+@pytest.mark.parametrize("gname", ["grid", "rand"])
+def test_kcycle_inner_fcg_is_krylov_projection(orc, gname):
+    """Three levels: the preconditioner of the inner solve at level 1 is the
+    linear two-level operator M = B_1 (exact coarse solve at level 2), so nu = 2
+    flexible-CG steps are two PCG steps and their result is the A_1-orthogonal
+    projection of A_1^{-1} r_H onto K_2 = span{M r_H, M A_1 M r_H}: e_H =
+    V (V' A_1 V)^{-1} V' r_H (the optimality of CG, Sec. 4's NPCG on a linear
+    preconditioner).  The K-cycle at level 0 is then the two-level sweep of
+    Sec. 3 with that e_H."""
+    g = gg.grid2d_5pt(24) if gname == "grid" else random_graph(500, 0.01, 6, wmax=3, d_frac=0.05)
+    h = orc.Hierarchy(g, degree=3, passes=1, coarse_max=g.n // 7, max_levels=3, inner_iters=2)
+    assert h.status == 0 and h.n_levels == 3
+    A0, A1, A2 = (h.level_dense(k) for k in range(3))
+    def smoother(k, A):
+        l0, l1 = h.level_lambda(k)
+        return matrix_function(A, lambda lam: cheb_q(h.level_cheb(k), l0, l1, lam))
+    R0, R1 = smoother(0, A0), smoother(1, A1)
+    P0 = prolongation(h.level_agg(0), A1.shape[0])
+    P1 = prolongation(h.level_agg(1), A2.shape[0])
+    I1 = np.eye(A1.shape[0])
+    M = (2 * R1 - R1 @ A1 @ R1
+         + (I1 - R1 @ A1) @ P1 @ np.linalg.pinv(A2, rcond=1e-12, hermitian=True) @ P1.T @ (I1 - A1 @ R1))
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        r = rng.standard_normal(g.n)
+        if gg.is_pure_laplacian(g):
+            r -= r.mean()
+        u = R0 @ r
+        rH = P0.T @ (r - A0 @ u)
+        V = np.column_stack([M @ rH, M @ A1 @ (M @ rH)])
+        eH = V @ np.linalg.solve(V.T @ A1 @ V, V.T @ rH)
+        x = u + P0 @ eH
+        x = x + R0 @ (r - A0 @ x)
+        got = h.kcycle(0, r)
+        assert np.abs(got - x).max() <= 1e-9 * np.abs(x).max()
