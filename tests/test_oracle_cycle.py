@@ -192,3 +192,45 @@ def test_kcycle_inner_fcg_is_krylov_projection(orc, gname):
         x = x + R0 @ (r - A0 @ x)
         got = h.kcycle(0, r)
         assert np.abs(got - x).max() <= 1e-9 * np.abs(x).max()
+
+
+def restarted_pcg(A, B, b, R, iters):
+    """Textbook preconditioned CG (z = B r, beta = r'z / r_old'z_old), the
+    search direction reset to z at every multiple of R iterations."""
+    x = np.zeros_like(b); r = b.copy(); hist = [1.0]
+    p = rz_old = None
+    for it in range(iters):
+        z = B @ r
+        rz = r @ z
+        p = z.copy() if it % R == 0 else z + rz / rz_old * p
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        rz_old = rz
+        hist.append(np.linalg.norm(r) / np.linalg.norm(b))
+    return np.array(hist)
+
+
+@pytest.mark.parametrize("R", [1, 3, 5])
+@pytest.mark.parametrize("pre", ["identity", "two_level"])
+def test_restarted_flexible_cg_is_restarted_pcg(orc, pre, R):
+    """With a fixed SPD preconditioner the window's orthogonalisation reduces
+    to PCG's one-term recurrence (Sec. 4 restarts the outer iteration every
+    five steps); R = 1 with the identity is steepest descent.  Pins the window
+    reset index, the projection coefficients and the step length."""
+    g = random_graph(90, 0.05, 11, wmax=3, d_frac=0.05)
+    b = gg.rhs(g.n, 31, False)
+    iters = 12
+    if pre == "identity":
+        h = orc.Hierarchy(g, precond=orc.PREC_IDENTITY, restart=R, max_iters=iters)
+        A, B = dense_laplacian(g), np.eye(g.n)
+    else:
+        h = orc.Hierarchy(g, degree=3, passes=2, coarse_max=g.n // 3, max_levels=2, restart=R,
+                          max_iters=iters)
+        assert h.status == 0 and h.n_levels == 2
+        A, _, _, _, B = dense_B(orc, h, g, 3)
+    res = h.solve(b, tol=1e-30)
+    ref = restarted_pcg(A, B, b, R, iters)
+    assert len(res.history) == iters + 1
+    assert np.allclose(res.history, ref, rtol=1e-7, atol=1e-13)
