@@ -100,3 +100,18 @@ def test_inner_fcg_is_krylov_projection(orc, gname, nu):
         # to the constant vector's component on pure Laplacians)
         d = got - x
         assert np.sqrt(d @ A1 @ d) <= 1e-9 * np.sqrt(x @ A1 @ x)
+
+
+@pytest.mark.parametrize("gname", sorted(GRAPHS))
+def test_smoother_interval_on_every_level(orc, gname):
+    """lambda1 = ||A_k||_inf (a Gershgorin bound on lambda_max, Sec. 3) and
+    lambda0 = lambda1 / 10 (Sec. 4) on every smoothed level, from the dense
+    Galerkin chain; integer weights make the row sums exact."""
+    g = GRAPHS[gname]()
+    h = hierarchy(orc, g)
+    A = galerkin_chain(h, g)
+    for k in range(h.n_levels - 1):
+        l0, l1 = h.level_lambda(k)
+        assert l1 == np.abs(A[k]).sum(axis=1).max()
+        assert np.linalg.eigvalsh(A[k])[-1] <= l1 * (1 + 1e-14)
+        assert l0 == pytest.approx(0.1 * l1, rel=1e-15)
