@@ -12,6 +12,8 @@ tests compare against one by one.
   preconditioner is the linear two-level operator B (exact coarse solve,
   Sec. 3): nu PCG steps, i.e. the A-orthogonal projection onto the Krylov
   space K_nu(BA, Bb), for nu = 1, 2, 3.
+* The smoother interval of every smoothed level: lambda1 = ||A_k||_inf from
+  the dense chain, an upper bound on lambda_max, and lambda0 = lambda1 / 10.
 """
 import numpy as np
 import pytest
