@@ -1440,6 +1440,11 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   // ---- validation (order of the C ABI's error list) ----
   unsigned *flags = nullptr;
   AMG_TRY(pool_alloc((void **)&flags, sizeof(unsigned), st));
+  // validation failures release the flag word before returning
+  auto reject = [&](amg_status code, const char *msg) {
+    pool_free(flags, st);
+    return fail(code, msg);
+  };
   AMG_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
   k_check_rowptr<<<blocks_for(n64 + 1, 256), 256, 0, st>>>(n64, rowptr, flags);
   LAUNCH_CHECK(&h->launches);
@@ -1448,22 +1453,22 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaMemcpyAsync(&nnz, rowptr + n64, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
-  if (hf & F_ROWPTR) return fail(AMG_ERR_INVALID_ARG, "row_ptr must start at 0 and be non-decreasing");
-  if (nnz > 0 && (!col || !w)) return fail(AMG_ERR_INVALID_ARG, "col_idx and w must be non-NULL");
+  if (hf & F_ROWPTR) return reject(AMG_ERR_INVALID_ARG, "row_ptr must start at 0 and be non-decreasing");
+  if (nnz > 0 && (!col || !w)) return reject(AMG_ERR_INVALID_ARG, "col_idx and w must be non-NULL");
   k_check_entries<<<nb, 256, 0, st>>>(n, rowptr, col, w, d, flags);
   LAUNCH_CHECK(&h->launches);
   AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
   if (hf & (F_RANGE | F_ORDER))
-    return fail(AMG_ERR_INVALID_ARG, "column index out of range or row not strictly increasing");
-  if (hf & F_SELF) return fail(AMG_ERR_SELF_LOOP, "graph has a self loop");
+    return reject(AMG_ERR_INVALID_ARG, "column index out of range or row not strictly increasing");
+  if (hf & F_SELF) return reject(AMG_ERR_SELF_LOOP, "graph has a self loop");
   k_check_symmetry<<<nb, 256, 0, st>>>(n, rowptr, col, w, flags);
   LAUNCH_CHECK(&h->launches);
   AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
-  if (hf & F_SYM) return fail(AMG_ERR_NOT_SYMMETRIC, "graph is not symmetric (pattern or weights)");
-  if (hf & F_W) return fail(AMG_ERR_BAD_WEIGHT, "edge weights must be finite and > 0");
-  if (hf & F_D) return fail(AMG_ERR_BAD_WEIGHT, "lower-order terms must be finite and >= 0");
+  if (hf & F_SYM) return reject(AMG_ERR_NOT_SYMMETRIC, "graph is not symmetric (pattern or weights)");
+  if (hf & F_W) return reject(AMG_ERR_BAD_WEIGHT, "edge weights must be finite and > 0");
+  if (hf & F_D) return reject(AMG_ERR_BAD_WEIGHT, "lower-order terms must be finite and >= 0");
   pool_free(flags, st);
   // pure Laplacian?  (d NULL or all zero)
   h->pure = true;
