@@ -234,6 +234,10 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     // measured neutral on the 128^3 workload, so it is off by default
     const char *pdl = getenv("AMG_GB300_PDL");
     h->use_pdl = (pdl && pdl[0] == '1');
+    // AMG_GB300_PROLONG_SPLIT=0 keeps the fused prolongation-residual kernel
+    // on every level (A/B timing of the two equivalent forms)
+    const char *ps = getenv("AMG_GB300_PROLONG_SPLIT");
+    h->prolong_split = !(ps && ps[0] == '0');
   }
   cudaGetDevice(&h->device);
   // NULL selects the legacy default stream, which orders our work after any

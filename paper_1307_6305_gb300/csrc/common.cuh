@@ -236,6 +236,7 @@ struct amg_handle_s {
   // CUDA graph and replayed every outer iteration
   bool use_graph = true;
   bool use_pdl = true;              // programmatic dependent launch of solve kernels
+  bool prolong_split = true;        // streaming prolongation + residual on large levels
   bool capturing = false;
   cudaStream_t cap = nullptr;       // private stream used only for capture
   cudaGraphExec_t pre_exec = nullptr;
