@@ -276,3 +276,30 @@ def test_split_rows_match_one_thread_per_row(amg, orc, precision, monkeypatch):
         m = min(len(h1), len(ref.history))
         assert np.abs(h1[:m] - ref.history[:m]).max() <= 1e-10
     close(x1, x0, 1e-7)
+
+
+@pytest.mark.parametrize("precision,cycle", [(0, 0), (1, 0), (0, 1)])
+def test_split_prolongation_equals_fused(amg, monkeypatch, precision, cycle):
+    """Levels of one warp per slice and >= 2^17 rows write x = u + P e_H with
+    a streaming kernel and then run the residual on x; the fused kernel forms
+    the same x_j inside the residual's gather.  Both do the same operations in
+    the same order, so residual histories and solutions are equal bit for bit
+    (AMG_GB300_PROLONG_SPLIT=0 selects the fused form on every level)."""
+    g = gg.grid3d_7pt(64, 1.0)
+    b = gg.rhs(g.n, 12, False)
+    runs = []
+    for split in ("1", "0"):
+        monkeypatch.setenv("AMG_GB300_PROLONG_SPLIT", split)
+        gh = amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, degree=5, passes=3,
+                                      precision=precision, cycle=cycle)
+        assert gh.status == 0, gh.error
+        assert gh.level_n(0) >= 1 << 17
+        x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        st, info, hist = gh.solve(cuda(b), x, tol=1e-8)
+        assert st == amg.AMG_OK, amg.amg_last_error(gh.h)
+        runs.append((hist, x.cpu().numpy(), gh.launch_count(), info.iterations))
+        gh.close()
+    (hs, xs, ls, its), (hf, xf, lf, itf) = runs
+    assert its == itf
+    assert np.array_equal(hs, hf) and np.array_equal(xs, xf)
+    assert ls > lf          # the split form ran (one more launch per level-0 cycle)
