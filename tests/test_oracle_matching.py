@@ -70,3 +70,46 @@ def test_matching_is_maximal_and_numbered_by_representatives(orc, make):
     assert np.array_equal(agg, rank[owner])
     assert nH == rep.sum()
     assert np.all(np.bincount(agg, minlength=nH) <= 2) and np.all(np.bincount(agg) >= 1)
+
+
+def numbered_by_representatives(mate):
+    n = mate.size
+    rep = (mate < 0) | (np.arange(n) < mate)
+    rank = np.cumsum(rep) - 1
+    owner = np.where(rep, np.arange(n), np.minimum(np.arange(n), mate))
+    return rank[owner]
+
+
+@pytest.mark.parametrize("make,passes", [
+    (lambda: gg.grid2d_5pt(16), 3),
+    (lambda: gg.grid3d_7pt(6, 1.0), 3),
+    (lambda: random_graph(160, 0.03, 2, wmax=4, d_frac=0.1), 2),
+])
+def test_each_pass_is_the_greedy_matching_of_the_intermediate_graph(orc, make, passes):
+    """Sec. 2 repeats pairwise matching on the graph of the previous pass's
+    Galerkin operator.  Built here independently: B_0 = A_k from the graph and
+    the composite maps (dense), B_{p+1} = Q_p^T B_p Q_p; pass p's map must be the
+    sequential greedy matching of B_p's graph by strength |b_ij| / sqrt(b_ii b_jj)
+    (integer weights: every product exact, the strength rounded once per IEEE
+    operation on both sides), numbered by representatives."""
+    from helpers import dense_laplacian, prolongation
+    g = make()
+    h = orc.Hierarchy(g, passes=passes, coarse_max=8)
+    assert h.status == 0 and h.n_levels >= 3
+    Ak = dense_laplacian(g)
+    for k in range(h.n_levels - 1):
+        B = Ak
+        maps = h.level_pass_aggs(k)
+        assert len(maps) == passes
+        for a in maps:
+            n = B.shape[0]
+            rows, cols = np.nonzero(B - np.diag(np.diag(B)))
+            rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]).astype(np.int64)
+            s = -B[rows, cols] / np.sqrt(np.diag(B)[rows] * np.diag(B)[cols])
+            inter = gg.Graph(n, rowptr, cols.astype(np.int32), s, None)
+            mate = greedy_matching(inter, 0)
+            assert np.array_equal(a, numbered_by_representatives(mate))
+            Q = prolongation(a, a.max() + 1)
+            B = Q.T @ B @ Q
+        assert np.array_equal(B, h.level_dense(k + 1))
+        Ak = B
