@@ -35,3 +35,19 @@ def test_delaunay3d_is_deterministic():
     assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.col, b.col)
     c = gg.delaunay3d(8, 4)
     assert not (np.array_equal(a.rowptr, c.rowptr) and np.array_equal(a.col, c.col))
+
+
+@pytest.mark.parametrize("name,n,edges,nnz_diag,boundary,nrhs", [
+    ("grid2d_64", 4096, 8064, 20224, 0, 1),
+    ("grid3d_128", 2097152, 6242304, 14581760, 96776, 1),
+    ("grid3d_96x32", 884736, 2626560, 6137856, 54152, 32),
+    ("rdiag2d_2048", 4194304, 12574721, 29343746, 0, 1),
+])
+def test_workload_sizes(name, n, edges, nnz_diag, boundary, nrhs):
+    """The synthetic workloads have the sizes of the benchmark configurations:
+    vertices, undirected edges, stored entries with the diagonal, vertices
+    carrying a lower-order term (the boundary faces), right-hand sides."""
+    g, p = gg.workload(name)
+    assert g.n == n and g.col.size == 2 * edges and g.col.size + g.n == nnz_diag
+    assert (0 if g.d is None else int((g.d > 0).sum())) == boundary
+    assert len(p["rhs_seeds"]) == nrhs
