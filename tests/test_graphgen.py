@@ -51,3 +51,17 @@ def test_workload_sizes(name, n, edges, nnz_diag, boundary, nrhs):
     assert g.n == n and g.col.size == 2 * edges and g.col.size + g.n == nnz_diag
     assert (0 if g.d is None else int((g.d > 0).sum())) == boundary
     assert len(p["rhs_seeds"]) == nrhs
+
+
+@pytest.mark.parametrize("n,seed", [(20000, 61), (100000, 3)])
+def test_random_geometric_graph(n, seed):
+    """Random geometric graphs in the unit square: the radius gives mean degree
+    8; the largest component is kept (over 99% of the points), so the graph is
+    connected, symmetric and a pure Laplacian."""
+    g = gg.random_geometric(n, seed)
+    A = sp.csr_matrix((np.ones(g.col.size), g.col, g.rowptr), shape=(g.n, g.n))
+    assert 0.99 * n <= g.n <= n
+    assert abs(g.col.size / g.n - 8.0) < 0.2
+    assert connected_components(A, directed=False)[0] == 1
+    assert (A != A.T).nnz == 0 and g.d is None
+    assert np.all(np.diff(g.rowptr) > 0)
