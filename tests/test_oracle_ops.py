@@ -13,7 +13,10 @@ tests compare against one by one.
   Sec. 3): nu PCG steps, i.e. the A-orthogonal projection onto the Krylov
   space K_nu(BA, Bb), for nu = 1, 2, 3.
 * The smoother interval of every smoothed level: lambda1 = ||A_k||_inf from
-  the dense chain, an upper bound on lambda_max, and lambda0 = lambda1 / 10.
+  the dense chain, an upper bound on lambda_max, and lambda0 = lambda1 / 10
+  (or the configured ratio, with the Remez coefficients of that interval).
+* Pure Laplacians: the constant part of b does not change the solution, which
+  has zero mean.
 """
 import numpy as np
 import pytest
@@ -117,3 +120,35 @@ def test_smoother_interval_on_every_level(orc, gname):
         assert l1 == np.abs(A[k]).sum(axis=1).max()
         assert np.linalg.eigvalsh(A[k])[-1] <= l1 * (1 + 1e-14)
         assert l0 == pytest.approx(0.1 * l1, rel=1e-15)
+
+
+@pytest.mark.parametrize("ratio", [0.05, 0.2])
+def test_smoother_interval_follows_lambda0_ratio(orc, ratio):
+    """lambda0 = ratio * lambda1 for a non-default ratio, and the stored
+    coefficients are the best approximation on that interval (Remez, Sec. 3)."""
+    g = GRAPHS["rand_w"]()
+    h = orc.Hierarchy(g, degree=4, passes=1, coarse_max=12, lambda0_ratio=ratio)
+    assert h.status == 0
+    for k in range(h.n_levels - 1):
+        l0, l1 = h.level_lambda(k)
+        assert l0 == pytest.approx(ratio * l1, rel=1e-15)
+        ref = orc.remez_inverse(4, l0, l1)[0]
+        assert np.allclose(h.level_cheb(k), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("gname", ["grid2d_14", "rand_w"])
+def test_pure_laplacian_ignores_the_constant_part_of_b(orc, gname):
+    """The range of a pure Laplacian is 1-perp (Sec. 1): b and b + c 1 give the
+    same solution, which has zero mean; with a lower-order term they differ."""
+    g = GRAPHS[gname]()
+    h = orc.Hierarchy(g, degree=3, passes=2, coarse_max=12)
+    b = gg.rhs(g.n, 41, True)
+    x1 = h.solve(b, tol=1e-12).x
+    x2 = h.solve(b + 5.0, tol=1e-12).x
+    if gg.is_pure_laplacian(g):
+        assert np.allclose(x1, x2, rtol=0, atol=1e-10 * np.abs(x1).max())
+        assert abs(x1.mean()) <= 1e-12 * np.abs(x1).max()
+    else:
+        A = dense_laplacian(g)
+        assert np.linalg.norm(A @ x2 - (b + 5.0)) <= 1e-10 * np.linalg.norm(b + 5.0)
+        assert not np.allclose(x1, x2)
