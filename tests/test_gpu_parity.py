@@ -303,3 +303,33 @@ def test_split_prolongation_equals_fused(amg, monkeypatch, precision, cycle):
     assert its == itf
     assert np.array_equal(hs, hf) and np.array_equal(xs, xf)
     assert ls > lf          # the split form ran (one more launch per level-0 cycle)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(degree=4, passes=3, lambda0_ratio=0.05),
+    dict(degree=4, passes=3, hash_salt=0x9E3779B97F4A7C15),
+    dict(degree=3, passes=2, lambda0_ratio=0.2, hash_salt=12345, coarse_max=32, restart=3),
+])
+def test_non_default_options_match_oracle(amg, orc, opts):
+    """Options other than the benchmark's: the smoother interval ratio (Sec. 3)
+    and the salt of the matching's tie-break hash (Sec. 2) reach both sides the
+    same way -- aggregates bit for bit, smoother intervals and coefficients to
+    rounding, and the solve's residual history within 1e-10."""
+    g = random_graph(6000, 0.0012, 13, wmax=4, d_frac=0.02)
+    gh, oh = pair(amg, orc, g, **opts)
+    assert gh.n_levels == oh.n_levels
+    for k in range(oh.n_levels - 1):
+        assert np.array_equal(gh.level_agg(k), oh.level_agg(k))
+        l0, l1, coef = gh.level_smoother(k)
+        o0, o1 = oh.level_lambda(k)
+        assert l1 == o1 and l0 == pytest.approx(o0, rel=1e-15)
+        ref = oh.level_cheb(k)
+        assert np.abs(coef - ref).max() <= 1e-12 * np.abs(ref).max()
+    b = gg.rhs(g.n, 43, False)
+    res = oh.solve(b, tol=1e-8)
+    x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    st, info, hist = gh.solve(cuda(b), x, tol=1e-8)
+    assert st == res.status and abs(info.iterations - res.iterations) <= 1
+    m = min(len(hist), len(res.history))
+    assert np.abs(hist[:m] - res.history[:m]).max() <= 1e-10
+    close(x.cpu().numpy(), res.x, 1e-7)
