@@ -308,7 +308,8 @@ amg_status amg_server_submit(amg_server s, int64_t graph_id, const double *rhs, 
  * the solve's status */
 amg_status amg_server_poll(amg_server s, int64_t ticket, double *x, amg_info *info, int *done,
                            double *latency_ms);
-/* as amg_server_poll, blocking until the request is done */
+/* as amg_server_poll, blocking until the request is done; AMG_ERR_INVALID_ARG
+ * if another caller takes the same ticket first */
 amg_status amg_server_wait(amg_server s, int64_t ticket, double *x, amg_info *info, double *latency_ms);
 amg_status amg_server_stats(amg_server s, amg_server_stats_t *out);
 /* stops the workers after their current solves and frees every hierarchy */

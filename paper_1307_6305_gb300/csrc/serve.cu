@@ -274,6 +274,7 @@ static amg_status take(amg_server s, Request &r, double *x, amg_info *info, doub
   const amg_status st = r.status;
   if (st != AMG_OK) fail(st, r.err);
   s->requests.erase(r.ticket);
+  s->cv_done.notify_all();  // other waiters on this ticket see it released
   return st;
 }
 
@@ -290,9 +291,15 @@ amg_status amg_server_poll(amg_server s, int64_t ticket, double *x, amg_info *in
 amg_status amg_server_wait(amg_server s, int64_t ticket, double *x, amg_info *info, double *latency_ms) {
   if (!s) return fail(AMG_ERR_INVALID_ARG, "server is NULL");
   std::unique_lock<std::mutex> lk(s->mu);
+  if (s->requests.find(ticket) == s->requests.end()) return fail(AMG_ERR_INVALID_ARG, "unknown ticket");
+  // looked up again after every wake-up: another caller may have taken the
+  // ticket (and erased the request) in the meantime
+  s->cv_done.wait(lk, [&] {
+    auto f = s->requests.find(ticket);
+    return f == s->requests.end() || f->second.done;
+  });
   auto it = s->requests.find(ticket);
-  if (it == s->requests.end()) return fail(AMG_ERR_INVALID_ARG, "unknown ticket");
-  s->cv_done.wait(lk, [&] { return it->second.done; });
+  if (it == s->requests.end()) return fail(AMG_ERR_INVALID_ARG, "the ticket was taken by another caller");
   return take(s, it->second, x, info, latency_ms);
 }
 
