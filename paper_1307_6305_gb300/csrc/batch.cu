@@ -599,11 +599,18 @@ static int pow2_at_least(int v) {
 static std::mutex g_tune_mu;
 static std::map<std::string, std::pair<int, int>> g_tuned;
 
+// a block shape the block kernels support: kb a power of two up to kMaxBlock,
+// the row tile one of the three timed sizes
+static bool valid_shape(int kb, int tile) {
+  return kb >= 1 && kb <= kMaxBlock && (kb & (kb - 1)) == 0 && (tile == 128 || tile == 256 || tile == 512);
+}
+
 // Pick (block width, SpMM tile) for `nrhs` columns by timing graph replays of
 // the block preconditioner; the cost compared is time per column.  The
-// choice is kept per (device, n, nnz, nrhs, precision, degree) for the
-// process (later handles of the same shape reuse it) and, with
-// AMG_GB300_TUNE_CACHE=<file>, in a JSON file across processes;
+// choice is kept per (device, n, nnz, width cap, precision, degree, passes,
+// aggregation, k, nu) for the process (later handles of the same shape reuse
+// it) and, with AMG_GB300_TUNE_CACHE=<file>, in a JSON file across processes
+// (an entry that is not a supported shape is ignored and the shape re-timed);
 // AMG_GB300_BATCH=<kb>,<tile> forces one.
 static amg_status autotune(amg_handle_s *h, int nrhs) {
   const int cap = std::min(kMaxBlock, pow2_at_least(nrhs));
@@ -627,8 +634,7 @@ static amg_status autotune(amg_handle_s *h, int nrhs) {
   }
   if (const char *env = getenv("AMG_GB300_BATCH")) {
     int kb = 0, tile = 0;
-    if (sscanf(env, "%d,%d", &kb, &tile) == 2 && kb >= 1 && kb <= kMaxBlock && (kb & (kb - 1)) == 0 &&
-        (tile == 128 || tile == 256 || tile == 512)) {
+    if (sscanf(env, "%d,%d", &kb, &tile) == 2 && valid_shape(kb, tile)) {
       h->bw_use = kb;
       h->b_tile = tile;
       h->tuned_for = cap;
@@ -645,7 +651,7 @@ static amg_status autotune(amg_handle_s *h, int nrhs) {
       const std::string want = std::string("\"") + key + "\": [";
       if (const char *p = strstr(buf, want.c_str())) {
         int kb = 0, tile = 0;
-        if (sscanf(p + want.size(), "%d, %d", &kb, &tile) == 2 && kb >= 1 && kb <= cap) {
+        if (sscanf(p + want.size(), "%d, %d", &kb, &tile) == 2 && valid_shape(kb, tile) && kb <= cap) {
           h->bw_use = kb;
           h->b_tile = tile;
           h->tuned_for = cap;
