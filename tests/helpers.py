@@ -80,3 +80,36 @@ def sparse_laplacian(g: gg.Graph):
     if g.d is not None:
         deg = deg + g.d
     return (sp.diags(deg) - W).tocsr()
+
+
+def c_struct_layouts(include_dir: str, header: str, structs, workdir) -> dict:
+    """{(struct, field): offset, (struct, 'sizeof'): size} as a C compiler lays
+    out `structs` (pairs of C name and ctypes class, whose field names are the
+    C member names) from `header`; None if no C compiler is available."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        return None
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{header}"', "int main(void) {"]
+    for name, cls in structs:
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = workdir / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = workdir / "layout"
+    subprocess.run([cc, "-std=c99", "-I", include_dir, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return {(a, b): int(c) for a, b, c in (ln.split() for ln in out.splitlines())}
+
+
+def assert_layouts_match(layout: dict, structs):
+    import ctypes as C
+
+    for name, cls in structs:
+        assert layout[(name, "sizeof")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert layout[(name, f)] == getattr(cls, f).offset, (name, f)

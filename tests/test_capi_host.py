@@ -117,29 +117,12 @@ def test_struct_layouts_match_the_header(tmp_path):
     """The binding's ctypes structures have the field names, offsets and sizes
     of the C declarations (a C program built against include/amg.h reports
     them), so options and reports cross the boundary unchanged."""
-    import ctypes as C
-    import shutil
-
+    from helpers import assert_layouts_match, c_struct_layouts
     from paper_1307_6305_gb300 import binding as B
 
-    cc = shutil.which("gcc") or shutil.which("cc")
-    if cc is None:
-        pytest.skip("no C compiler")
     structs = [("amg_options", B.amg_options), ("amg_info", B.amg_info),
                ("amg_server_config", B.amg_server_config), ("amg_server_stats_t", B.amg_server_stats_t)]
-    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "amg.h"', "int main(void) {"]
-    for name, cls in structs:
-        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
-        for f, _ in cls._fields_:
-            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
-    lines.append("return 0; }")
-    src = tmp_path / "layout.c"
-    src.write_text("\n".join(lines) + "\n")
-    exe = tmp_path / "layout"
-    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
-    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out.splitlines())}
-    for name, cls in structs:
-        assert got[(name, "sizeof")] == C.sizeof(cls), name
-        for f, _ in cls._fields_:
-            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+    layout = c_struct_layouts(os.path.join(ROOT, "include"), "amg.h", structs, tmp_path)
+    if layout is None:
+        pytest.skip("no C compiler")
+    assert_layouts_match(layout, structs)

@@ -69,3 +69,17 @@ def test_stall_guard(orc):
     assert small.status == orc.OK and small.n_levels == 1
     big = orc.Hierarchy(star_graph(5000), coarse_max=8)
     assert big.status == orc.ERR_SETUP_STALL
+
+
+def test_oracle_struct_layouts_match_its_header(orc, tmp_path):
+    """The oracle's ctypes option and report structures match oracle/amg_oracle.h."""
+    import os
+
+    from helpers import assert_layouts_match, c_struct_layouts
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = [("orc_options", orc.Options), ("orc_info", orc.Info)]
+    layout = c_struct_layouts(os.path.join(root, "oracle"), "amg_oracle.h", structs, tmp_path)
+    if layout is None:
+        pytest.skip("no C compiler")
+    assert_layouts_match(layout, structs)
