@@ -71,7 +71,10 @@ def test_argument_errors_before_device(amg):
                 dict(precision=3), dict(lambda0_ratio=1.5), dict(coarse_max=0), dict(cycle=2), dict(rho=-1.0),
                 dict(rho=1e-12), dict(cycle=1, amli_alpha=0.0), dict(cycle=1, amli_alpha=0.1),
                 dict(cycle=1, inner_iters=1), dict(aggregation=2), dict(aggregation=1, mis_k=0),
-                dict(aggregation=1, mis_k=17)):
+                dict(aggregation=1, mis_k=17), dict(passes=17), dict(coarse_max=4097), dict(max_levels=0),
+                dict(max_levels=65), dict(inner_iters=0), dict(restart=17), dict(max_iters=-1),
+                dict(precision=-1), dict(lambda0_ratio=0.0), dict(lambda0_ratio=float("nan")),
+                dict(rho=float("inf")), dict(rho=float("nan")), dict(cycle=1, amli_alpha=1.0), dict(cycle=-1)):
         st, h = amg.amg_setup(g.n, rp, col, w, None, amg.amg_default_options(**bad))
         assert st == amg.AMG_ERR_INVALID_ARG, bad
         assert amg.amg_last_error(None)
@@ -81,6 +84,23 @@ def test_argument_errors_before_device(amg):
     st, h = amg.amg_setup(g.n, rp, col, w, None, None, 7)
     assert st == amg.AMG_ERR_INVALID_ARG
     assert amg.amg_solve(None, np.zeros(3), np.zeros(3), 1, 3, 1e-8) == amg.AMG_ERR_INVALID_ARG
+
+
+def test_option_limits_are_inclusive(amg):
+    """Options at the documented limits pass validation: on a machine without
+    a device, setup gets as far as the device check (AMG_ERR_CUDA)."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-device path")
+    g = gg.grid2d_5pt(4)
+    for edge in (dict(degree=0), dict(degree=16), dict(passes=16), dict(coarse_max=1), dict(coarse_max=4096),
+                 dict(max_levels=1), dict(max_levels=64), dict(inner_iters=8), dict(restart=1),
+                 dict(restart=16), dict(max_iters=0), dict(aggregation=1, mis_k=1),
+                 dict(aggregation=1, mis_k=16), dict(cycle=1, inner_iters=2, amli_alpha=0.25),
+                 dict(rho=1 / 3), dict(precision=1)):
+        st, h = amg.amg_setup(g.n, g.rowptr, g.col, g.w, None, amg.amg_default_options(**edge))
+        assert st == amg.AMG_ERR_CUDA, (edge, st, amg.amg_last_error(None))
 
 
 def test_no_device_is_reported(amg):
