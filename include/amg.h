@@ -138,7 +138,7 @@ int amg_degree_for(double rho, double lambda0_ratio);
  * kernels: validation, connectivity, matching passes, Galerkin sums, lambda1
  * = ||A_k||_inf, the coarsest-level pseudo-inverse, the solve-phase layouts).
  *
- *  n            number of vertices, 1 <= n < 2^31
+ *  n            number of vertices, 1 <= n <= 2^31 - 2^16 (row indices are 32-bit)
  *  row_ptr      int64[n+1] CSR row offsets of the graph (row_ptr[0] = 0)
  *  col_idx      int32[nnz] neighbours; strictly increasing within each row;
  *               no self loops; the pattern is symmetric
@@ -239,7 +239,8 @@ amg_status amg_apply_kcycle(amg_handle h, int k, const double *r, double *z);
  * (s_ij, splitmix64(salt ^ (lo << 32 | hi)), lo, hi), largest wins.
  * Outputs (device): mate[n] (-1 unmatched), agg[n] coarse ids (rank of each
  * pair's smaller vertex / singleton); *n_coarse and *rounds (host) receive the
- * coarse size and the number of proposal rounds.  stream may be NULL. */
+ * coarse size and the number of proposal rounds.  1 <= n <= 2^31 - 2^16.
+ * stream may be NULL. */
 amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *s,
                      uint64_t salt, int32_t *mate, int32_t *agg, int64_t *n_coarse, int *rounds,
                      void *cuda_stream);

@@ -207,7 +207,7 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
                      amg_handle *out) {
   if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (n < 1 || n > 2147483647LL) return fail(AMG_ERR_INVALID_ARG, "n must be in [1, 2^31)");
+  if (n < 1 || n > kMaxRows) return fail(AMG_ERR_INVALID_ARG, "n must be in [1, 2^31 - 2^16]");
   if (!row_ptr) return fail(AMG_ERR_INVALID_ARG, "row_ptr is NULL");
   if (mem_space != AMG_MEM_HOST && mem_space != AMG_MEM_DEVICE)
     return fail(AMG_ERR_INVALID_ARG, "mem_space must be AMG_MEM_HOST or AMG_MEM_DEVICE");
@@ -501,7 +501,7 @@ amg_status amg_apply_kcycle(amg_handle h, int k, const double *r, double *z) {
 amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *s,
                      uint64_t salt, int32_t *mate, int32_t *agg, int64_t *n_coarse, int *rounds,
                      void *cuda_stream) {
-  if (n < 1 || n > 2147483647LL || !row_ptr || !mate || !agg)
+  if (n < 1 || n > kMaxRows || !row_ptr || !mate || !agg)
     return fail(AMG_ERR_INVALID_ARG, "n, row_ptr, mate or agg invalid");
   AMG_TRY(cuda_ready());
   cudaStream_t st = (cudaStream_t)cuda_stream;

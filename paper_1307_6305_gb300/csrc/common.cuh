@@ -34,6 +34,10 @@ constexpr int kMaxDots = 8;       // dots per fused reduction
 constexpr int kRedBlocks = 608;   // partial sums per reduction = 4 x 152 SMs
 constexpr int kStallMaxCoarse = 4096;
 constexpr double kStallRatio = 0.95;
+// largest vertex count: the one-thread-per-row kernels index rows in 32-bit
+// integers over grids rounded up to whole blocks, so every thread index of a
+// launch must stay below 2^31
+constexpr int64_t kMaxRows = (int64_t(1) << 31) - (int64_t(1) << 16);
 
 // ---------------------------------------------------------------------------
 // error plumbing: status + message, no exceptions across the C ABI

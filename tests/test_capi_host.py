@@ -65,6 +65,10 @@ def test_argument_errors_before_device(amg):
     rp, col, w = g.rowptr, g.col, g.w
     st, h = amg.amg_setup(0, rp, col, w)
     assert st == amg.AMG_ERR_INVALID_ARG and not h.value
+    # row indices are 32-bit in the kernels: n above 2^31 - 2^16 is refused
+    # before any buffer is read
+    st, h = amg.amg_setup((1 << 31) - (1 << 16) + 1, rp, col, w)
+    assert st == amg.AMG_ERR_INVALID_ARG and "2^31" in amg.amg_last_error(None)
     st, h = amg.amg_setup(g.n, None, col, w)
     assert st == amg.AMG_ERR_INVALID_ARG
     for bad in (dict(degree=-1), dict(degree=17), dict(passes=0), dict(inner_iters=9), dict(restart=0),
