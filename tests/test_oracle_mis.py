@@ -68,12 +68,13 @@ GRAPHS = {
 }
 
 
+@pytest.mark.parametrize("salt", [0, 0x5DEECE66D])
 @pytest.mark.parametrize("k", [1, 2, 4])
 @pytest.mark.parametrize("gname", sorted(GRAPHS))
-def test_mis_roots_and_nearest_root_assignment(orc, gname, k):
+def test_mis_roots_and_nearest_root_assignment(orc, gname, k, salt):
     g = GRAPHS[gname]()
     A = adjacency(g)
-    agg, root, nH = orc.mis_aggregate(g.rowptr, g.col, k)
+    agg, root, nH = orc.mis_aggregate(g.rowptr, g.col, k, salt)
     R = np.flatnonzero(root)
     assert nH == R.size
     D = shortest_path(A, unweighted=True, indices=R)          # |R| x n distances
@@ -83,7 +84,7 @@ def test_mis_roots_and_nearest_root_assignment(orc, gname, k):
     assert DR.min() > k
     assert D.min(axis=0).max() <= k
     # the same set as the fixed-key parallel rule
-    keys = np.array([key(v) for v in range(g.n)], dtype=object)
+    keys = np.array([key(v, salt) for v in range(g.n)], dtype=object)
     assert np.array_equal(luby_fixed_keys(A, keys, k), root)
     # nearest root, ties to the larger key; ids by root vertex order
     rank = {r: i for i, r in enumerate(R)}
