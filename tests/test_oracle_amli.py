@@ -156,3 +156,18 @@ def test_amli_polynomial_is_scaled_best_approximation(orc, nu, alpha):
     t = np.linspace(alpha, 1, 2001)
     tq = t * Chebyshev(h.amli_coef(), domain=[alpha, 1.0])(t)
     assert tq.max() <= 1 + 1e-12 and tq.min() > 0
+
+
+@pytest.mark.parametrize("nu,alpha", [(2, 0.25), (3, 0.15)])
+def test_amli_cycle_is_dense_recursion_on_independent_set_aggregates(orc, nu, alpha):
+    """The same dense recursion on a hierarchy built by the paper's aggregation
+    (maximal independent sets of the graph of A^k, Sec. 2; k = 1 keeps five
+    levels on a 20 x 20 grid): the cycle depends on the aggregates only through
+    P and the Galerkin operators."""
+    g = gg.grid2d_5pt(20)
+    h = orc.Hierarchy(g, degree=3, passes=1, coarse_max=12, cycle=1, amli_alpha=alpha, inner_iters=nu,
+                      aggregation=1, mis_k=1)
+    assert h.status == 0 and h.n_levels >= 4
+    B = dense_amli(orc, h, alpha, nu)
+    Bcyc = np.column_stack([h.amli_cycle(0, e) for e in np.eye(g.n)])
+    assert np.abs(Bcyc - B).max() <= 1e-10 * np.abs(B).max()
