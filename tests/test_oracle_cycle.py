@@ -157,7 +157,7 @@ def test_history_and_stopping(orc):
     assert r2.status == orc.ERR_NOT_CONVERGED and r2.iterations == 2
 
 
-@pytest.mark.parametrize("gname", ["grid", "rand"])
+@pytest.mark.parametrize("gname", ["grid", "rand", "grid_mis"])
 def test_kcycle_inner_fcg_is_krylov_projection(orc, gname):
     """Three levels: the preconditioner of the inner solve at level 1 is the
     linear two-level operator M = B_1 (exact coarse solve at level 2), so nu = 2
@@ -166,8 +166,9 @@ def test_kcycle_inner_fcg_is_krylov_projection(orc, gname):
     V (V' A_1 V)^{-1} V' r_H (the optimality of CG, Sec. 4's NPCG on a linear
     preconditioner).  The K-cycle at level 0 is then the two-level sweep of
     Sec. 3 with that e_H."""
-    g = gg.grid2d_5pt(24) if gname == "grid" else random_graph(500, 0.01, 6, wmax=3, d_frac=0.05)
-    h = orc.Hierarchy(g, degree=3, passes=1, coarse_max=g.n // 7, max_levels=3, inner_iters=2)
+    g = gg.grid2d_5pt(24) if gname.startswith("grid") else random_graph(500, 0.01, 6, wmax=3, d_frac=0.05)
+    agg = dict(aggregation=1, mis_k=1) if gname.endswith("mis") else {}
+    h = orc.Hierarchy(g, degree=3, passes=1, coarse_max=g.n // 7, max_levels=3, inner_iters=2, **agg)
     assert h.status == 0 and h.n_levels == 3
     A0, A1, A2 = (h.level_dense(k) for k in range(3))
     def smoother(k, A):
