@@ -113,3 +113,21 @@ def assert_layouts_match(layout: dict, structs):
         assert layout[(name, "sizeof")] == C.sizeof(cls), name
         for f, _ in cls._fields_:
             assert layout[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def restarted_pcg(A, B, b, R, iters):
+    """Textbook preconditioned CG (z = B r, beta = r'z / r_old'z_old), the
+    search direction reset to z at every multiple of R iterations."""
+    x = np.zeros_like(b); r = b.copy(); hist = [1.0]
+    p = rz_old = None
+    for it in range(iters):
+        z = B @ r
+        rz = r @ z
+        p = z.copy() if it % R == 0 else z + rz / rz_old * p
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        rz_old = rz
+        hist.append(np.linalg.norm(r) / np.linalg.norm(b))
+    return np.array(hist)

@@ -171,3 +171,24 @@ def test_amli_cycle_is_dense_recursion_on_independent_set_aggregates(orc, nu, al
     B = dense_amli(orc, h, alpha, nu)
     Bcyc = np.column_stack([h.amli_cycle(0, e) for e in np.eye(g.n)])
     assert np.abs(Bcyc - B).max() <= 1e-10 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("R", [1, 5])
+@pytest.mark.parametrize("gname", ["grid3d_7_d", "rand_w"])
+def test_amli_solve_is_restarted_pcg_with_dense_B(orc, gname, R):
+    """The stationary AMLI cycle is a fixed linear SPD operator B_0, so the
+    outer flexible CG preconditioned by it (Sec. 4, restarted every R steps)
+    has the residual history of textbook PCG with the dense B_0 built by the
+    bottom-up recursion."""
+    from helpers import restarted_pcg
+
+    g = GRAPHS[gname]()
+    iters = 10
+    h = orc.Hierarchy(g, degree=3, passes=1, coarse_max=12, cycle=1, restart=R, max_iters=iters)
+    assert h.status == 0 and h.n_levels >= 4
+    B = dense_amli(orc, h, 0.25, 2)
+    b = gg.rhs(g.n, 33, False)
+    res = h.solve(b, tol=1e-30)
+    ref = restarted_pcg(h.level_dense(0), B, b, R, iters)
+    assert len(res.history) == iters + 1
+    assert np.allclose(res.history, ref, rtol=1e-7, atol=1e-13)

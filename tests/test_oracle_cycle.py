@@ -14,7 +14,7 @@ import pytest
 
 import graphgen as gg
 from helpers import (cheb_q, complete_graph, dense_laplacian, matrix_function, path_graph,
-                     prolongation, random_graph)
+                     prolongation, random_graph, restarted_pcg)
 
 
 def two_level(orc, g, m):
@@ -193,24 +193,6 @@ def test_kcycle_inner_fcg_is_krylov_projection(orc, gname):
         x = x + R0 @ (r - A0 @ x)
         got = h.kcycle(0, r)
         assert np.abs(got - x).max() <= 1e-9 * np.abs(x).max()
-
-
-def restarted_pcg(A, B, b, R, iters):
-    """Textbook preconditioned CG (z = B r, beta = r'z / r_old'z_old), the
-    search direction reset to z at every multiple of R iterations."""
-    x = np.zeros_like(b); r = b.copy(); hist = [1.0]
-    p = rz_old = None
-    for it in range(iters):
-        z = B @ r
-        rz = r @ z
-        p = z.copy() if it % R == 0 else z + rz / rz_old * p
-        Ap = A @ p
-        a = rz / (p @ Ap)
-        x += a * p
-        r -= a * Ap
-        rz_old = rz
-        hist.append(np.linalg.norm(r) / np.linalg.norm(b))
-    return np.array(hist)
 
 
 @pytest.mark.parametrize("R", [1, 3, 5])
