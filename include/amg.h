@@ -9,7 +9,8 @@
  * preconditioned by the nonlinear AMLI cycle (K-cycle, W(1,1)) of Sec. 4 over
  * unsmoothed (piecewise-constant) aggregation coarse spaces (Sec. 2, Eq.
  * (coarse)), with the smoother R = q_m(A), q_m the polynomial of best uniform
- * approximation to 1/x on [lambda1/10, ||A||_inf] (Sec. 3, Eq. (1x-1-min)).
+ * approximation to 1/x on [lambda0, lambda1], lambda1 = ||A||_inf and lambda0 =
+ * lambda1/10 by default (Sec. 3, Eq. (1x-1-min); Sec. 4).
  * Aggregates are built on the device by handshake matching (Sec. 2: a
  * matching is the simplest graph partitioning), several passes per level, or
  * by the paper's maximal independent sets of the graph of A^k (Sec. 2 steps
@@ -65,18 +66,20 @@ enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1 };
 typedef struct {
   int degree;          /* m, degree of q_m (Sec. 4 uses 4); 0..16                 */
   int passes;          /* matching passes composed per level (~2^passes per
-                          aggregate); AMG_AGG_MATCHING only                        */
-  int coarse_max;      /* coarsen until n_k <= coarse_max; coarsest solved densely */
-  int max_levels;      /* cap on the number of levels                              */
-  int inner_iters;     /* nu: flexible-CG steps on coarse levels (2 = W-cycle)     */
-  int restart;         /* outer flexible CG window cleared every `restart` its (5) */
-  int max_iters;       /* outer iteration cap                                      */
+                          aggregate), 1..16; AMG_AGG_MATCHING only                 */
+  int coarse_max;      /* coarsen until n_k <= coarse_max; coarsest solved densely;
+                          1..4096                                                  */
+  int max_levels;      /* cap on the number of levels, 1..64                       */
+  int inner_iters;     /* nu: flexible-CG steps on coarse levels (2 = W-cycle), 1..8 */
+  int restart;         /* outer flexible CG window cleared every `restart` its (5),
+                          1..16                                                    */
+  int max_iters;       /* outer iteration cap, >= 0                                */
   int precision;       /* AMG_PREC_FP64: everything in fp64.  AMG_PREC_FP32: the
                           whole preconditioner (smoother, transfers, coarse-level
                           cycles) in fp32 inside fp64 outer CG; outer residual,
                           outer dots/orthogonalisation and the coarsest dense
                           solve stay fp64                                          */
-  double lambda0_ratio;/* lambda0 = ratio * ||A_k||_inf (Sec. 4: 1/10)             */
+  double lambda0_ratio;/* lambda0 = ratio * ||A_k||_inf, in (0, 1) (Sec. 4: 1/10) */
   uint64_t hash_salt;  /* salt of the matching tie-break hash and of the keys of
                           AMG_AGG_MIS                                            */
   int cycle;           /* AMG_CYCLE_K: nonlinear AMLI cycle (K-cycle), inner
@@ -161,8 +164,9 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
 
 /*
  * Solve A x = rhs for nrhs right-hand sides by flexible CG (Sec. 4: NPCG,
- * window cleared every `restart` iterations) preconditioned by the K-cycle,
- * from x0 = 0, until ||r_k|| <= tol ||b|| (recursive residual, fp64).
+ * window cleared every `restart` iterations) preconditioned by the handle's
+ * cycle (option `cycle`), from x0 = 0, until ||r_k|| <= tol ||b|| (recursive
+ * residual, fp64).
  *
  *  rhs, x   column j at rhs + j*ld, x + j*ld (column major, ld >= n); host or
  *           device memory (each pointer classified independently); x is
@@ -201,7 +205,8 @@ int64_t amg_level_nnz(amg_handle h, int k);
 amg_status amg_level_csr(amg_handle h, int k, int64_t *rowptr, int32_t *col, double *val,
                          double *diag, double *dlow);
 /* Composite aggregate map level k -> k+1 (k < levels-1): agg[n_k] in [0, n_{k+1}).
- * Coarse ids rank the aggregates' smallest members.  Host buffer. */
+ * Coarse ids rank the aggregates' smallest members (AMG_AGG_MATCHING) or their
+ * roots (AMG_AGG_MIS).  Host buffer. */
 amg_status amg_level_agg(amg_handle h, int k, int32_t *agg);
 /* Smoother data of level k < levels-1: lambda0, lambda1 = ||A_k||_inf and the
  * m+1 Chebyshev coefficients of q_m in t = (2x - l1 - l0)/(l1 - l0), m the
