@@ -318,7 +318,9 @@ amg_status amg_server_poll(amg_server s, int64_t ticket, double *x, amg_info *in
  * if another caller takes the same ticket first */
 amg_status amg_server_wait(amg_server s, int64_t ticket, double *x, amg_info *info, double *latency_ms);
 amg_status amg_server_stats(amg_server s, amg_server_stats_t *out);
-/* stops the workers after their current solves and frees every hierarchy */
+/* stops the workers after their current solves and frees every hierarchy;
+ * requests still queued are dropped.  No other call on s may be in progress
+ * (a blocked amg_server_wait included) or follow. */
 void amg_server_destroy(amg_server s);
 
 /* ---------------------------------------------------------------------- */
@@ -330,7 +332,9 @@ void amg_server_destroy(amg_server s);
  * enabling resets the accumulators. */
 amg_status amg_kernel_timing(amg_handle h, int enable);
 /* Accumulated launches, total device milliseconds and the algorithmic bytes
- * of one launch (matrix + vectors touched once, see the library's notes). */
+ * of one launch: nnz (v + 4) + 8 (slices + 1) + 6 n v for level 0 (stored
+ * values and columns, slice offsets, the diagonal, T_j, T_{j-1}, T_{j+1} and
+ * x read and written once; v = 8, or 4 for AMG_PREC_FP32). */
 amg_status amg_kernel_timing_read(amg_handle h, int64_t *launches, double *total_ms,
                                   double *bytes_per_launch);
 /* Number of kernel launches issued by the last amg_setup/amg_solve on h. */
