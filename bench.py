@@ -123,6 +123,8 @@ def serve_bench(args):
                                       "peak_resident_gb": stats.peak_resident_bytes / 2 ** 30}}
     print(json.dumps(line), flush=True)
     return 0
+
+
 METRIC = "DOF/s solved to 1e-8 rel. residual (setup + solve per step)"
 UNIT = "DOF/s"
 L2_BYTES = 129 * 2 ** 20
