@@ -1,7 +1,7 @@
 """Python loader for the FP64 CPU oracle (test infrastructure only).
 
 Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
-leg may import this package.  It compiles ``amg_oracle.c`` with gcc on first
+leg and ``--impl reference`` arm may import this package.  It compiles ``amg_oracle.c`` with gcc on first
 use (or via :func:`build`) and wraps it with ctypes; nothing here shares code
 with the CUDA library.
 """
