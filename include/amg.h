@@ -245,7 +245,9 @@ amg_status amg_apply_kcycle(amg_handle h, int k, const double *r, double *z);
  * Outputs (device): mate[n] (-1 unmatched), agg[n] coarse ids (rank of each
  * pair's smaller vertex / singleton); *n_coarse and *rounds (host) receive the
  * coarse size and the number of proposal rounds.  1 <= n <= 2^31 - 2^16.
- * stream may be NULL. */
+ * row_ptr, col_idx, s, mate and agg must be non-NULL (AMG_ERR_INVALID_ARG);
+ * a round limit of 4n + 8 guards against non-symmetric or non-finite s
+ * (AMG_ERR_INVALID_ARG).  stream may be NULL. */
 amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *s,
                      uint64_t salt, int32_t *mate, int32_t *agg, int64_t *n_coarse, int *rounds,
                      void *cuda_stream);
@@ -259,11 +261,13 @@ amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
  * that loads the library, kept until the process exits), so:
  *  - n must be <= 1048576 (2^20); larger n returns AMG_ERR_INVALID_ARG;
  *  - no cudaMalloc/cudaFree or allocating library routine is called;
- *  - the first call on a device looks up that array's device address (with
- *    that device current); make that first call before any stream capture;
- *  - all calls on a device share the array: calls that overlap on the GPU
- *    (other streams, threads or processes on the same context) race and must
- *    be serialised by the caller.
+ *  - every call looks up that array's device address for the current device
+ *    (a host-side lookup) and waits for its own work on `cuda_stream`
+ *    (stream synchronisation between batches of rounds and before return);
+ *  - every process holds its own copy of the array, and all calls of one
+ *    process on a device share it: calls from different streams or threads
+ *    of one process that overlap on the GPU race and must be serialised by
+ *    the caller.
  * Arguments, outputs and results are those of amg_match. */
 amg_status amg_match_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                              const double *s, uint64_t salt, int32_t *mate, int32_t *agg,

@@ -16,6 +16,8 @@
 // kernels (rows per CTA = threads / kb) are chosen by timing graph replays
 // of every candidate on the first batched solve of a handle.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -757,6 +759,10 @@ static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int
   AMG_CUDA_TRY(cudaMemsetAsync(h->bo_x, 0, sizeof(double) * nk, st));
   AMG_CUDA_TRY(cudaMemcpyAsync(h->bo_r, h->bo_b, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int c = 0; c < nr; ++c)
+    if (!std::isfinite(hp[c]))
+      return fail(AMG_ERR_INVALID_ARG, "right-hand side " + std::to_string(c) +
+                                           " has a non-finite entry or a norm beyond the fp64 range");
   std::vector<double> nb(kb), res(kb, 0.0);
   std::vector<int> done(kb, 0), brk(kb, 0);
   int remaining = 0;

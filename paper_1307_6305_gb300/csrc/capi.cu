@@ -48,10 +48,28 @@ static amg_status device_pool(cudaMemPool_t *out) {
   return AMG_OK;
 }
 
+// Injected allocation failure, for testing the error paths of the setup
+// without a real out-of-memory condition: amg_setup arms the calling thread's
+// countdown from AMG_GB300_FAIL_ALLOC=k (k >= 1) and disarms it on return;
+// while armed, the k-th device allocation of the setup fails as if the pool
+// were exhausted.  Nothing is injected on the device.
+static thread_local int64_t t_alloc_countdown = 0;
+
+struct AllocFailArm {
+  AllocFailArm() {
+    const char *e = getenv("AMG_GB300_FAIL_ALLOC");
+    t_alloc_countdown = e ? std::max<long long>(0, atoll(e)) : 0;
+  }
+  ~AllocFailArm() { t_alloc_countdown = 0; }
+};
+
 amg_status pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (t_alloc_countdown > 0 && --t_alloc_countdown == 0)
+    return fail(AMG_ERR_OOM, "injected allocation failure (AMG_GB300_FAIL_ALLOC) of " + std::to_string(bytes) +
+                                 " bytes");
   cudaMemPool_t pool;
   AMG_TRY(device_pool(&pool));
-  *p = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -220,6 +238,8 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     if (row_ptr[n] > 0 && (!col_idx || !w)) return fail(AMG_ERR_INVALID_ARG, "col_idx and w must be non-NULL");
   }
   AMG_TRY(cuda_ready());
+  const AllocFailArm fail_arm;  // AMG_GB300_FAIL_ALLOC: test hook, off unless set
+  const NvtxRange setup_range("amg_setup");
   auto t0 = std::chrono::steady_clock::now();
   amg_handle_s *h = new amg_handle_s();
   h->opt = o;
@@ -272,10 +292,12 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   }
   if (!s) s = build_hierarchy(h, n, drp, dcol, dw, dd);
   for (void *p : tmp) pool_free(p, h->stream);
-  if (!s) s = allocate_solve_buffers(h);
-  if (!s) s = build_dense_two_level(h);
-  if (!s) s = prepare_tail(h);
-  if (!s) s = prepare_leaf(h);
+  {
+    const NvtxRange r("amg_setup: solve buffers, dense two-level operator, leaf kernel");
+    if (!s) s = allocate_solve_buffers(h);
+    if (!s) s = build_dense_two_level(h);
+    if (!s) s = prepare_leaf(h);
+  }
   if (!s) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) s = fail(AMG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e));
@@ -297,6 +319,7 @@ amg_status amg_solve(amg_handle h, const double *rhs, double *x, int nrhs, int64
   if (!rhs || !x || nrhs < 1 || ld < h->n || !(tol >= 0.0))
     return record(h, fail(AMG_ERR_INVALID_ARG, "rhs/x NULL, nrhs < 1, ld < n or tol invalid"));
   if (cudaSetDevice(h->device) != cudaSuccess) return record(h, fail(AMG_ERR_CUDA, "cudaSetDevice"));
+  const NvtxRange solve_range("amg_solve");
   auto t0 = std::chrono::steady_clock::now();
   h->launches = 0;
   const bool rdev = is_device_ptr(rhs), xdev = is_device_ptr(x);
@@ -503,6 +526,7 @@ amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
                      void *cuda_stream) {
   if (n < 1 || n > kMaxRows || !row_ptr || !mate || !agg)
     return fail(AMG_ERR_INVALID_ARG, "n, row_ptr, mate or agg invalid");
+  if (!col_idx || !s) return fail(AMG_ERR_INVALID_ARG, "col_idx and s must be non-NULL");
   AMG_TRY(cuda_ready());
   cudaStream_t st = (cudaStream_t)cuda_stream;
   int nH = 0, r = 0;

@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -64,6 +65,28 @@ struct Error {
 
 amg_status fail(amg_status code, const std::string &msg);  // records thread-local error
 const std::string &thread_error();
+
+// NVTX range over a host-side phase (setup steps, outer iterations); a no-op
+// unless a profiler that collects NVTX is attached
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+// consecutive phases of one function: next() closes the open range and opens
+// the next one; the destructor closes the last
+struct NvtxPhase {
+  bool open = false;
+  void next(const char *name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhase() {
+    if (open) nvtxRangePop();
+  }
+};
 
 // ---------------------------------------------------------------------------
 // device memory: one library-owned stream-ordered pool per device
@@ -207,8 +230,6 @@ struct amg_handle_s {
   int leaf_csize = 0;
   void *leaf_params = nullptr;             // host copy of the launch parameters
   void (*leaf_free)(void *) = nullptr;
-  // levels >= tail_k0 run as one persistent cluster kernel per inner solve
-  int tail_k0 = -1;
   // batched path (batch.cu)
   int bw = 0;                        // allocated block width (0: not yet)
   int bw_use = 32;                   // block width in use
@@ -225,13 +246,6 @@ struct amg_handle_s {
   double *b_pinned = nullptr;
   cudaGraphExec_t bpre_exec = nullptr;
   int64_t bgraph_kernels = 0;
-  int tail_csize = 0;
-  int tail_mode = 0;
-  int tail_test_stall = 0;
-  void *tail_params = nullptr;
-  unsigned *tail_bar = nullptr;
-  double *tail_gpart = nullptr;
-  int *tail_err = nullptr;           // set by a tail barrier that timed out
   double setup_ms = 0;
   double grid_complexity = 0, op_complexity = 0;
   int64_t launches = 0;
@@ -263,9 +277,7 @@ amg_status build_dense_two_level(amg_handle_s *h);
 // batch.cu
 amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs, int64_t ld, double tol,
                          amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown);
-// tail.cu
-amg_status prepare_tail(amg_handle_s *h);
-amg_status launch_tail(amg_handle_s *h);
+// leaf.cu
 amg_status prepare_leaf(amg_handle_s *h);
 amg_status launch_leaf(amg_handle_s *h);
 amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol,

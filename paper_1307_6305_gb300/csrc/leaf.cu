@@ -647,7 +647,7 @@ amg_status prepare_leaf(amg_handle_s *h) {
   const char *env = getenv("AMG_GB300_LEAF");
   if (env && env[0] == '0') return AMG_OK;
   const int k0 = h->Bk - 1;
-  if (h->Bk < 0 || k0 < 1 || h->tail_k0 >= 0 || h->opt.cycle != AMG_CYCLE_K) return AMG_OK;
+  if (h->Bk < 0 || k0 < 1 || h->opt.cycle != AMG_CYCLE_K) return AMG_OK;
   if (h->opt.inner_iters > kLeafMaxInner || h->opt.degree > kMaxDegree) return AMG_OK;
   if (h->lv[k0].n > kLeafMaxRows || h->lv[k0 + 1].n > kLeafMaxCoarse) return AMG_OK;
   if (h->opt.precision == AMG_PREC_FP32) return prepare_t<float>(h, k0);

@@ -11,12 +11,10 @@
 // g_match_scratch below.
 //
 // Cost of the design: every GPU that loads this library keeps the array
-// (kMaxN + 1024 ints, about 4 MiB) until the process exits; all calls on a
-// device share it, so calls that overlap on the GPU (different streams,
-// threads or processes sharing a context) race and must be serialised by the
-// caller.
-#include <mutex>
-
+// (kMaxN + 1024 ints, about 4 MiB) until the process exits.  Each process
+// holds its own copy, so only calls made by one process share it: calls from
+// different streams or threads of one process that overlap on the GPU race
+// and must be serialised by the caller.
 #include "common.cuh"
 
 namespace amg {
@@ -49,28 +47,18 @@ constexpr int kScratchInts = kMaxN + 1024;
 
 static __device__ __align__(256) int g_match_scratch[kScratchInts];
 
-std::mutex g_mu;
-int *g_addr[128];
-bool g_ready[128];
-
-// device address of g_match_scratch for the current device; obtained once per
-// device, on the first call made with that device current
+// Device address of g_match_scratch in the current device's context.  Looked
+// up on every call (a host-side lookup that allocates nothing): a cached
+// address would dangle after cudaDeviceReset recreates the context, and would
+// belong to the wrong context if the caller switches contexts on one device.
 amg_status scratch_address(int **out) {
-  int dev = 0;
-  AMG_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return fail(AMG_ERR_CUDA, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ready[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(AMG_ERR_CUDA, std::string("cudaGetSymbolAddress(g_match_scratch): ") + cudaGetErrorString(e));
-    }
-    g_addr[dev] = static_cast<int *>(p);
-    g_ready[dev] = true;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AMG_ERR_CUDA, std::string("cudaGetSymbolAddress(g_match_scratch): ") + cudaGetErrorString(e));
   }
-  *out = g_addr[dev];
+  *out = static_cast<int *>(p);
   return AMG_OK;
 }
 
@@ -143,6 +131,7 @@ extern "C" amg_status amg_match_noalloc(int64_t n64, const int64_t *row_ptr, con
                                         int64_t *n_coarse, int *rounds, void *cuda_stream) {
   if (n64 < 1 || !row_ptr || !mate || !agg)
     return fail(AMG_ERR_INVALID_ARG, "n, row_ptr, mate or agg invalid");
+  if (!col_idx || !s) return fail(AMG_ERR_INVALID_ARG, "col_idx and s must be non-NULL");
   if (n64 > kMaxN)
     return fail(AMG_ERR_INVALID_ARG, "amg_match_noalloc: n = " + std::to_string(n64) +
                                          " exceeds the fixed scratch capacity of " + std::to_string(kMaxN) +
@@ -164,8 +153,10 @@ extern "C" amg_status amg_match_noalloc(int64_t n64, const int64_t *row_ptr, con
   for (;;) {
     AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * kBatch, st));  // counters start at zero
     for (int b = 0; b < kBatch; ++b) {
-      k_propose<<<nb, 256, 0, st>>>(n, row_ptr, col_idx, s, salt, mate, work, nullptr);
-      k_accept<<<nb, 256, 0, st>>>(n, work, mate, added + b, nullptr);
+      // a round after one that added no pair returns at once on the device
+      const int *prev = b ? added + b - 1 : nullptr;
+      k_propose<<<nb, 256, 0, st>>>(n, row_ptr, col_idx, s, salt, mate, work, prev);
+      k_accept<<<nb, 256, 0, st>>>(n, work, mate, added + b, prev);
     }
     AMG_CUDA_TRY(cudaGetLastError());
     AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * kBatch, cudaMemcpyDeviceToHost, st));
@@ -176,7 +167,8 @@ extern "C" amg_status amg_match_noalloc(int64_t n64, const int64_t *row_ptr, con
       done = (h_added[b] == 0);
     }
     if (done) break;
-    if (r > 4 * n + 8) return fail(AMG_ERR_CUDA, "matching did not terminate");
+    if (r > 4 * n + 8)
+      return fail(AMG_ERR_INVALID_ARG, "matching did not terminate: s must be symmetric and finite");
   }
   // representative flags -> coarse ids (in place) -> aggregate ids
   const int tiles = (n + kTile - 1) / kTile;

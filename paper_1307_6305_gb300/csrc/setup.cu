@@ -397,7 +397,8 @@ static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, cons
       if (h_added[b] == 0) { done = true; break; }
     }
     if (done) break;
-    if (rounds > 4 * n + 8) return fail(AMG_ERR_CUDA, "matching did not terminate");
+    if (rounds > 4 * n + 8)
+      return fail(AMG_ERR_INVALID_ARG, "matching did not terminate: s must be symmetric and finite");
   }
   AMG_TRY(pool_alloc((void **)&rep, sizeof(int) * (size_t)std::max(n, 1), st));
   AMG_TRY(pool_alloc((void **)&id, sizeof(int) * (size_t)std::max(n, 1), st));
@@ -1437,6 +1438,8 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   cudaStream_t st = h->stream;
   const int n = (int)n64;
   const unsigned nb = blocks_for(n, 256);
+  NvtxPhase phase;
+  phase.next("amg_setup: validation");
   // ---- validation (order of the C ABI's error list) ----
   unsigned *flags = nullptr;
   AMG_TRY(pool_alloc((void **)&flags, sizeof(unsigned), st));
@@ -1484,6 +1487,7 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     pool_free(mx, st);
     h->pure = (hm == 0ULL);
   }
+  phase.next("amg_setup: connectivity");
   // ---- connectivity ----
   {
     int *parent = nullptr, *changed = nullptr, *posd = nullptr, *cnt = nullptr;
@@ -1544,10 +1548,12 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     k_assemble<<<nb, 256, 0, st>>>(n, rowptr, w, d, L0.A.val, L0.diag, L0.dlow);
     LAUNCH_CHECK(&h->launches);
   }
+  phase.next("amg_setup: coarsening (matching/independent sets + Galerkin)");
   // ---- coarsening ----
   const bool mis = h->opt.aggregation == AMG_AGG_MIS;
   const int passes = mis ? 1 : h->opt.passes;
   while (h->lv.back().n > h->opt.coarse_max && (int)h->lv.size() < h->opt.max_levels) {
+    const NvtxRange level_range("amg_setup: one coarser level");
     const int k = (int)h->lv.size() - 1;
     const int nk = h->lv[k].n;
     LevelBuild cur;
@@ -1593,6 +1599,7 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     h->lv.push_back(nl);
   }
   h->L = (int)h->lv.size();
+  phase.next("amg_setup: smoother intervals and coefficients");
   // ---- smoother interval and polynomial per level (Sec. 3, Sec. 4) ----
   unsigned long long *nrm = nullptr;
   AMG_TRY(pool_alloc((void **)&nrm, sizeof(unsigned long long), st));
@@ -1623,6 +1630,7 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     h->amli_sA = 2.0 / (1.0 - al);
     h->amli_sB = (1.0 + al) / (1.0 - al);
   }
+  phase.next("amg_setup: solve layouts and coarsest pseudo-inverse");
   // ---- solve layouts ----
   const bool want32 = h->opt.precision == AMG_PREC_FP32;
   for (int k = 0; k < h->L; ++k) AMG_TRY(build_sell(h, h->lv[k], want32));

@@ -16,6 +16,8 @@
 // The host walks the cycle and issues launches; it reads one scalar per
 // outer iteration (the residual norm for the stopping test).
 #include <math.h>
+
+#include <cmath>
 #include <stdlib.h>
 
 #include <algorithm>
@@ -725,7 +727,6 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else if (k + 1 == h->leaf_k) AMG_TRY(launch_leaf(h));
-  else if (k + 1 == h->tail_k0) AMG_TRY(launch_tail(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
   AMG_TRY(prolong_residual<T>(h, k, (const T *)N.x, u, r, x, s));
   AMG_TRY(smooth<T>(h, k, s, x, true));
@@ -1020,23 +1021,6 @@ static amg_status run_precondition(amg_handle_s *h) {
   return precondition(h, h->or_, h->oz);
 }
 
-// A grid barrier of the tail kernel gave up waiting: the kernel returned
-// without further writes; clear its flags so the handle stays usable.
-static amg_status tail_timeout(amg_handle_s *h) {
-  cudaMemsetAsync(h->tail_err, 0, sizeof(int) * 4, h->stream);
-  cudaMemsetAsync(h->tail_bar, 0, sizeof(unsigned) * 4, h->stream);
-  cudaStreamSynchronize(h->stream);
-  return fail(AMG_ERR_TIMEOUT, "a bounded barrier wait of the coarse-level kernel ran out");
-}
-
-static amg_status check_tail(amg_handle_s *h) {
-  if (!h->tail_err) return AMG_OK;
-  int e = 0;
-  AMG_CUDA_TRY(cudaMemcpyAsync(&e, h->tail_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return e ? tail_timeout(h) : AMG_OK;
-}
-
 // ---------------------------------------------------------------------------
 // outer flexible CG (Sec. 4: NPCG on the finest level, window cleared every
 // `restart` iterations), fp64
@@ -1074,6 +1058,10 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
   AMG_CUDA_TRY(cudaMemcpyAsync(h->or_, h->ob, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   AMG_CUDA_TRY(cudaMemsetAsync(sc + 34, 0, sizeof(double), st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  // a NaN or infinity anywhere in b (or entries so large that ||b||^2
+  // overflows) makes b^T b non-finite: refuse rather than iterate on garbage
+  if (!std::isfinite(hp[0]))
+    return fail(AMG_ERR_INVALID_ARG, "right-hand side has a non-finite entry or a norm beyond the fp64 range");
   const double nb = sqrt(hp[0]);
   int hl = 0;
   if (info && info->history && info->history_cap > 0) info->history[hl++] = nb > 0 ? 1.0 : 0.0;
@@ -1083,6 +1071,7 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
   AMG_TRY(ensure_graph(h));
   if (h->timing.enabled) h->timing.used = 0;
   while (!converged && it < h->opt.max_iters) {
+    const NvtxRange iter_range("outer flexible-CG iteration");
     if (it % R == 0) nwin = 0;
     double *d = h->oD[nwin], *q = h->oQ[nwin];
     AMG_TRY(run_precondition(h));
@@ -1119,12 +1108,7 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
                                                       h->red.ticket, Fin{FIN_STORE, 33, 0.0, sc}));
     SLAUNCH(h);
     AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 33, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
-    if (h->tail_err) AMG_CUDA_TRY(cudaMemcpyAsync(hp + 4, h->tail_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h->tail_err && *reinterpret_cast<int *>(hp + 4)) {
-      status = tail_timeout(h);
-      break;
-    }
     if (h->pre_exec && h->graph_timed) AMG_TRY(timing_accumulate(h, h->graph_events));
     if (hp[1] != 0.0) {
       status = fail(AMG_ERR_BREAKDOWN, "flexible CG breakdown: d^T A d <= 0 or non-finite");
@@ -1272,7 +1256,7 @@ amg_status apply_kcycle(amg_handle_s *h, int k, const double *r, double *z) {
     return cycle<double>(h, k, (const double *)a, (double *)b);
   }));
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return check_tail(h);
+  return AMG_OK;
 }
 
 }  // namespace amg

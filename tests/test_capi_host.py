@@ -90,6 +90,21 @@ def test_argument_errors_before_device(amg):
     assert amg.amg_solve(None, np.zeros(3), np.zeros(3), 1, 3, 1e-8) == amg.AMG_ERR_INVALID_ARG
 
 
+def test_match_entry_points_refuse_null_pointers(amg):
+    """amg_match and amg_match_noalloc check every pointer on the host before
+    any device work (the addresses below are never dereferenced)."""
+    fake = 1 << 20
+    for fn in (amg.amg_match, amg.amg_match_noalloc):
+        for col, s in ((None, fake), (fake, None), (None, None)):
+            st, _, _ = fn(16, fake, col, s, 0, fake, fake)
+            assert st == amg.AMG_ERR_INVALID_ARG, (fn.__name__, col, s)
+            assert "non-NULL" in amg.amg_last_error(None)
+        st, _, _ = fn(16, None, fake, fake, 0, fake, fake)
+        assert st == amg.AMG_ERR_INVALID_ARG
+        st, _, _ = fn(0, fake, fake, fake, 0, fake, fake)
+        assert st == amg.AMG_ERR_INVALID_ARG
+
+
 def test_option_limits_are_inclusive(amg):
     """Options at the documented limits pass validation: on a machine without
     a device, setup gets as far as the device check (AMG_ERR_CUDA)."""

@@ -1,5 +1,4 @@
-"""GPU checks of the mixed-precision form and of the persistent coarse-level
-(tail) kernel variants.
+"""GPU checks of the mixed-precision form.
 
 * fp32 preconditioner inside fp64 flexible CG: the outer residual is fp64,
   so every solve still reaches ||r||/||b|| <= 1e-8.  Two solutions that each
@@ -9,16 +8,7 @@
   within a few of the fp64 method's.
 * fp32 K-cycle applications agree with the fp64 oracle to single-precision
   accuracy (1e-4 relative to the result's max norm).
-* The coarse-level tail kernel, in each of its modes (cooperative grid with
-  a bounded software barrier, the default; one 16-CTA cluster; one CTA),
-  reproduces the multi-kernel path: fp64 results stay within the fp64
-  parity bar.
-* A tail barrier whose wait runs out (test hook: it waits for a generation
-  that never comes) ends the kernel without hanging and the solve reports
-  AMG_ERR_TIMEOUT; the device stays usable for the next handle.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -53,28 +43,6 @@ def resid_gap(orc, g, opts, x, xref):
     return np.linalg.norm(sparse_laplacian(g) @ (x - xref))
 
 
-def with_env(env, fn):
-    """Run fn with the given environment variables set (None: unset)."""
-    old = {k: os.environ.get(k) for k in env}
-    for k, v in env.items():
-        if v is None:
-            os.environ.pop(k, None)
-        else:
-            os.environ[k] = str(v)
-    try:
-        return fn()
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-
-
-def with_tail(rows, fn, mode=None):
-    return with_env({"AMG_GB300_TAIL_ROWS": rows, "AMG_GB300_TAIL_MODE": mode}, fn)
-
-
 GRAPHS = {
     "grid3d_24_d": (lambda: gg.grid3d_7pt(24, 1.0), dict(degree=5, passes=3)),
     "rdiag_96": (lambda: gg.grid2d_random_diag(96, 3), dict(degree=4, passes=3)),
@@ -84,14 +52,12 @@ GRAPHS = {
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-@pytest.mark.parametrize("tail", [None, 0])
-def test_fp32_preconditioner_solve(amg, orc, name, tail):
+def test_fp32_preconditioner_solve(amg, orc, name):
     make, opts = GRAPHS[name]
     g = make()
     b = gg.rhs(g.n, 13, gg.is_pure_laplacian(g))
     ref = orc.Hierarchy(g, **opts).solve(b, tol=1e-8)
-    h = with_tail(tail, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE,
-                                                          precision=amg.AMG_PREC_FP32, **opts))
+    h = amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, precision=amg.AMG_PREC_FP32, **opts)
     assert h.status == 0, h.error
     bd = cuda(b)
     xd = torch.zeros_like(bd)
@@ -119,44 +85,6 @@ def test_fp32_kcycle_single_precision_accuracy(amg, orc, name):
             out.zero_()
             gh.apply("smoother", k, cuda(v), out)
             assert rel(out.cpu().numpy(), oh.smooth(k, v)) < 1e-5
-
-
-@pytest.mark.parametrize("mode", ["grid", "cluster", "cta"])
-@pytest.mark.parametrize("name", ["grid3d_24_d", "rdiag_96", "rgg_8000"])
-def test_fp64_tail_modes_match_oracle(amg, orc, name, mode):
-    make, opts = GRAPHS[name]
-    g = make()
-    gh = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts), mode)
-    oh = orc.Hierarchy(g, **opts)
-    assert gh.status == 0 and gh.n_levels == oh.n_levels
-    for k in range(oh.n_levels):
-        v = gg.uniform_pm1(500 + k, oh.level_n(k))
-        out = torch.zeros(v.size, dtype=torch.float64, device="cuda")
-        gh.apply("kcycle", k, cuda(v), out)
-        assert rel(out.cpu().numpy(), oh.kcycle(k, v)) < 1e-11
-    b = gg.rhs(g.n, 17, gg.is_pure_laplacian(g))
-    ref = oh.solve(b, tol=1e-8)
-    bd = cuda(b)
-    xd = torch.zeros_like(bd)
-    st, info, hist = gh.solve(bd, xd, tol=1e-8)
-    assert st == 0 and abs(info.iterations - ref.iterations) <= 1
-    m = min(len(hist), len(ref.history))
-    assert np.abs(hist[:m] - ref.history[:m]).max() <= 1e-10
-    assert rel(xd.cpu().numpy(), ref.x) < 1e-7
-
-
-@pytest.mark.parametrize("mode", ["grid", "cluster", "cta"])
-def test_fp32_tail_matches_fp32_multikernel_path(amg, mode):
-    g = gg.grid3d_7pt(28, 1.0)
-    opts = dict(degree=5, passes=3, precision=amg.AMG_PREC_FP32)
-    a = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts), mode)
-    b = with_tail(0, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts))
-    v = cuda(gg.uniform_pm1(3, g.n))
-    oa = torch.zeros_like(v)
-    ob = torch.zeros_like(v)
-    a.apply("kcycle", 0, v, oa)
-    b.apply("kcycle", 0, v, ob)
-    assert rel(oa.cpu().numpy(), ob.cpu().numpy()) < 1e-5
 
 
 @pytest.mark.slow
@@ -187,20 +115,3 @@ def test_full_size_rdiag_2048_fp32(amg, orc):
           f"fp32-precond {it32} it, rel err {e32:.2e}, ||A(x-x_orc)||/||b|| {g32:.2e}, true res {t32:.2e}")
     assert abs(it64 - ref.iterations) <= 1 and e64 < 1e-7
     assert it32 <= it64 + 3 and g32 <= 2.1e-8
-
-
-def test_tail_barrier_timeout_is_reported(amg):
-    g = gg.grid3d_7pt(24, 1.0)
-    opts = dict(degree=5, passes=3)
-    bad = with_env({"AMG_GB300_TAIL_ROWS": 1 << 20, "AMG_GB300_TAIL_MODE": "grid", "AMG_GB300_TAIL_TEST_STALL": 1},
-                   lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts))
-    assert bad.status == 0
-    b = cuda(gg.rhs(g.n, 5, False))
-    x = torch.zeros_like(b)
-    st, info, hist = bad.solve(b, x, tol=1e-8)
-    assert st == amg.AMG_ERR_TIMEOUT
-    assert "ran out" in amg.amg_last_error(bad.h)
-    bad.close()
-    good = with_tail(1 << 20, lambda: amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts), "grid")
-    st, info, hist = good.solve(b, x, tol=1e-8)
-    assert st == amg.AMG_OK and hist[-1] <= 1e-8

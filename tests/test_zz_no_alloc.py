@@ -55,6 +55,25 @@ def test_noalloc_matches_amg_match_on_consecutive_calls(amg):
         assert got[3] < g.n
 
 
+def test_noalloc_at_its_capacity_matches_amg_match_and_the_oracle(amg, orc):
+    """The two-level scan of the coarse ids at its fixed limit: n = 2^20
+    (1024^2 grid: 512 scan tiles, the full width of the block-sum scan) and
+    n = 101^3 = 1,030,301 (a ragged last tile), twice in a row; integer
+    outputs bit for bit against amg_match and against the oracle's matching."""
+    for g, salt in ((gg.grid2d_5pt(1024), 3), (gg.grid3d_7pt(101, None), 11)):
+        s = g.w.astype(np.float64)
+        o_mate, o_agg, o_nH, o_rounds = orc.match(g.rowptr, g.col, s, salt)
+        ref = run(amg.amg_match, g, s, salt)
+        assert ref[0] == amg.AMG_OK, amg.amg_last_error(None)
+        for _ in range(2):
+            got = run(amg.amg_match_noalloc, g, s, salt)
+            assert got[0] == amg.AMG_OK, amg.amg_last_error(None)
+            assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+            assert got[3] == ref[3] and got[4] == ref[4]
+            assert np.array_equal(got[1], o_mate) and np.array_equal(got[2], o_agg)
+            assert got[3] == o_nH and got[4] == o_rounds
+
+
 def test_noalloc_rejects_sizes_beyond_capacity(amg):
     n = (1 << 20) + 1
     rp = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
