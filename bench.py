@@ -5,12 +5,20 @@ A step is one pass of the whole method on one synthetic problem: amg_setup on
 the device-resident graph (validation, matching, Galerkin, smoother data,
 coarsest pseudo-inverse) followed by amg_solve (flexible CG + K-cycle with the
 polynomial smoother) to ||r|| <= 1e-8 ||b||, then amg_free.  value = DOF of
-all ranks per step / step time.  Workload: 3D 7-point graph Laplacian on a
-128^3 grid (2,097,152 vertices, unit weights, d_i = 1 on boundary-face
-vertices), degree-5 smoother, three matching passes per level, nu = 2 inner
-flexible-CG steps, seeded uniform[-1,1] right-hand side.
+all ranks per step / step time; solve_dof_per_s divides by the solve phase
+alone (setup timed and reported beside it).  Workload: 3D 7-point graph
+Laplacian on a 128^3 grid (2,097,152 vertices, unit weights, d_i = 1 on
+boundary-face vertices), degree-5 smoother, three matching passes per level,
+nu = 2 inner flexible-CG steps, seeded uniform[-1,1] right-hand side.
+
+The default run also reports, under "variants", the other configurations of
+the measurement plan, each with its own bounded oracle sample: the fp32
+preconditioner on the same workload, the 64^2 case (us per solve), the
+2048^2 random-diagonal case (fp64 and fp32 preconditioner, error against the
+oracle), the 96^3 x 32 batched case and the serving run (solves/s, p50/p99).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--variants all|none|fp32,c1,c3,c4,c5] [--workload NAME]
 
 Multi-GPU runs (torchrun) solve independent replicas, one per rank (weak
 scaling, no data-path collective); the reference arm runs the CPU oracle.
@@ -26,6 +34,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import traceback
 
 import numpy as np
 
@@ -37,6 +46,10 @@ import graphgen as gg  # noqa: E402
 WORKLOADS = {
     "grid3d_128": ("128^3 7-point graph Laplacian, w=1, d=1 on boundary faces; degree-5 polynomial "
                    "smoother, 3 matching passes/level, K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64)"),
+    "grid2d_64": ("64^2 5-point pure graph Laplacian; degree-3 smoother, 2 matching passes/level, K-cycle nu=2, "
+                  "coarsest <= 64 vertices, tol 1e-8 (fp64)"),
+    "rdiag2d_2048": ("2048^2 grid, each square split along a seeded random diagonal (4,194,304 vertices), pure "
+                     "Laplacian; degree-4 smoother, 3 passes/level, K-cycle nu=2, tol 1e-8"),
     "grid3d_128_neumann_mis": ("128^3 7-point pure (Neumann) graph Laplacian; degree-4 polynomial smoother, "
                                "aggregation by the maximal independent set of the graph of A^4 (one pass per "
                                "level), K-cycle nu=2, FCG restart 5, tol 1e-8 (fp64): the setting of the paper's "
@@ -47,89 +60,19 @@ WORKLOADS = {
                           "K-cycle nu=2, tol 1e-8 (fp64): the paper's unstructured setting (synthetic mesh)"),
     "grid3d_96x32": ("96^3 7-point graph Laplacian, d=1 on boundary faces, 32 right-hand sides solved in one "
                      "batched call; degree-5 smoother, 3 passes/level, fp32 preconditioner / fp64 FCG, tol 1e-8"),
-    "serve": ("continuous-batching server: pool of 16 graphs (8 random geometric, 4 2D and 4 3D grids), sizes "
-              "log-uniform in [1e4, 1e6], resident hierarchies, 8 slots, 60 GB cap, Poisson arrivals; "
-              "degree-4 smoother, 3 passes, fp32 preconditioner / fp64 FCG, tol 1e-8"),
+    "serve": ("continuous-batching server: Poisson arrivals of solve requests over a pool of 48 graphs (half "
+              "random geometric graphs in the unit square with mean degree 8, a quarter each 2D/3D grids), sizes "
+              "log-uniform in [1e4, 1e6], hierarchies set up on first arrival and kept resident, same-graph "
+              "requests batched (up to 8 per solve), 8 slots, 60 GB cap; degree-4 smoother, 3 passes, fp32 "
+              "preconditioner / fp64 FCG, tol 1e-8"),
 }
-
-
-def serve_bench(args):
-    """Solves/s and p50/p99 latency of the server under Poisson arrivals at
-    1.2x and 0.5x of its saturated throughput."""
-    import torch
-
-    import paper_1307_6305_gb300 as amg
-
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(5)
-    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e6), 16))
-    graphs = []
-    for i, sz in enumerate(sizes):
-        if i < 8:
-            graphs.append(gg.random_geometric(int(sz), 500 + i))
-        elif i < 12:
-            graphs.append(gg.grid2d_5pt(int(round(np.sqrt(sz)))))
-        else:
-            graphs.append(gg.grid3d_7pt(int(round(sz ** (1.0 / 3.0))), None))
-    rhs = [[gg.rhs(g.n, 7000 + 10 * gi + j, True) for j in range(4)] for gi, g in enumerate(graphs)]
-    srv = amg.Server(60 << 30, 8, degree=4, passes=3, precision=amg.AMG_PREC_FP32)
-    ids = [srv.add_graph(g) for g in graphs]
-    for gi in range(len(graphs)):                      # hierarchies become resident
-        st, _, _, _ = srv.wait(srv.submit(ids[gi], rhs[gi][0]))
-        assert st == 0
-    def pick():
-        gi = int(rng.integers(len(graphs)))
-        return gi, rhs[gi][int(rng.integers(4))]
-    # saturated throughput: everything queued at once
-    burst = [pick() for _ in range(256)]
-    t0 = time.perf_counter()
-    tickets = [srv.submit(ids[gi], b) for gi, b in burst]
-    for t in tickets:
-        assert srv.wait(t)[0] == 0
-    sat = len(burst) / (time.perf_counter() - t0)
-    runs = []
-    for load, count in ((1.2, 2000), (0.5, 600)):
-        rate = load * sat
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
-        reqs = [pick() for _ in range(count)]
-        tickets = []
-        t0 = time.perf_counter()
-        for (gi, b), ta in zip(reqs, arrivals):
-            delay = ta - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(srv.submit(ids[gi], b))
-        lat, iters = [], []
-        for t in tickets:
-            st, x, info, ms = srv.wait(t)
-            assert st == 0
-            lat.append(ms)
-            iters.append(info.iterations)
-        wall = time.perf_counter() - t0
-        runs.append({"offered_load": load, "requests": count, "solves_per_s": count / wall,
-                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "mean_iterations": float(np.mean(iters))})
-    stats = srv.stats()
-    srv.close()
-    main = runs[0]
-    line = {"metric": "solves/s under Poisson arrivals at 1.2x saturated throughput (p50/p99 latency)",
-            "value": main["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": main["requests"],
-            "warmup": len(graphs), "ms_per_step": 1e3 / main["solves_per_s"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 outer", "data": "synthetic",
-            "config": {"workload": WORKLOADS["serve"], "graphs": [int(g.n) for g in graphs]},
-            "saturated_solves_per_s": sat, "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
-            "runs": runs, "server": {"peak_active": stats.peak_active, "setups": int(stats.setups),
-                                      "evictions": int(stats.evictions),
-                                      "peak_resident_gb": stats.peak_resident_bytes / 2 ** 30}}
-    print(json.dumps(line), flush=True)
-    return 0
-
 
 METRIC = "DOF/s solved to 1e-8 rel. residual (setup + solve per step)"
 UNIT = "DOF/s"
 L2_BYTES = 129 * 2 ** 20
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PROFILE = os.path.join(ROOT, "profiles", "cheb_step_grid3d_128.txt")
+VARIANTS = ("fp32", "c1", "c3", "c4", "c5")
 
 
 def dist_env():
@@ -189,6 +132,15 @@ def profiled_traffic():
         return None
 
 
+def workload_config(name: str, g, nrhs: int, world: int, cycle: int = 0) -> dict:
+    """The `config` object of the JSON line; both arms print the same one."""
+    in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + 8 * g.n * nrhs
+    return {"workload": WORKLOADS[name] + ("" if cycle == 0 else "; stationary AMLI W-cycle instead of the K-cycle"),
+            "n": int(g.n), "nrhs": int(nrhs), "nnz_offdiag": int(g.nnz),
+            "l2": f"inputs {in_bytes / 2**20:.0f} MiB vs 129 MiB L2 (no flush)",
+            "parallelism": f"replicas x{world}"}
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling in the background during the timed region."""
 
@@ -239,7 +191,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_oracle_step(g, p, b, ncols=None, cycle=0):
+def run_oracle_step(g, p, b, ncols=None, cycle=0, want_x=False):
     """Oracle setup + solve of the first `ncols` right-hand sides (all by default)."""
     import oracle
 
@@ -248,12 +200,368 @@ def run_oracle_step(g, p, b, ncols=None, cycle=0):
     t0 = time.perf_counter()
     h = oracle.Hierarchy(g, degree=p["degree"], passes=p["passes"], cycle=cycle,
                          aggregation=p.get("aggregation", 0))
+    r = None
     for j in range(ncols):
         r = h.solve(b[j * g.n:(j + 1) * g.n], tol=1e-8)
         assert r.status == 0, r.status
     dt = time.perf_counter() - t0
     assert h.status == 0
     return dt, r, ncols
+
+
+def guarded(name, fn):
+    """Run one variant; a failure is reported in its entry, not raised."""
+    t0 = time.perf_counter()
+    try:
+        out = fn()
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        out = {"error": f"{type(e).__name__}: {e}", "trace": traceback.format_exc(limit=3)[-600:]}
+    out["wall_s"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# GPU helpers (imported lazily: the reference arm needs no torch.cuda)
+# ---------------------------------------------------------------------------
+class Problem:
+    """A workload resident on the device, with pinned host copies for e2e."""
+
+    def __init__(self, name, dev):
+        import torch
+
+        self.name = name
+        self.g, self.p = gg.workload(name)
+        g = self.g
+        self.nrhs = len(self.p["rhs_seeds"])
+        self.b = np.concatenate([gg.rhs(g.n, sd, gg.is_pure_laplacian(g)) for sd in self.p["rhs_seeds"]])
+        self.rp = torch.as_tensor(g.rowptr, device=dev)
+        self.col = torch.as_tensor(g.col, device=dev)
+        self.w = torch.as_tensor(g.w, device=dev)
+        self.d = None if g.d is None else torch.as_tensor(g.d, device=dev)
+        self.bd = torch.as_tensor(self.b, device=dev)
+        self.xd = torch.zeros_like(self.bd)
+
+
+def make_opts(amg, p, precision, cycle=0):
+    return amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=precision, cycle=cycle,
+                                   aggregation=p.get("aggregation", 0))
+
+
+def timed_steps(amg, P, opts, sp, stream, steps, warmup):
+    """`warmup` untimed then `steps` timed steps (setup + solve + free) on the
+    device-resident problem.  CUDA events on the library's stream bracket the
+    steps and split each step into setup and solve."""
+    import torch
+
+    def one(evs=None):
+        if evs:
+            evs[0].record(stream)
+        st, h = amg.amg_setup(P.g.n, P.rp, P.col, P.w, P.d, opts, amg.AMG_MEM_DEVICE, sp)
+        assert st == 0, amg.amg_last_error(None)
+        launches = amg.lib().amg_launch_count(h)
+        if evs:
+            evs[1].record(stream)
+        info = amg.amg_info()
+        st = amg.amg_solve(h, P.bd, P.xd, P.nrhs, P.g.n, 1e-8, info)
+        assert st == 0, amg.amg_last_error(h)
+        if evs:
+            evs[2].record(stream)
+        launches += amg.lib().amg_launch_count(h)
+        amg.amg_free(h)
+        return launches, info
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    marks = [[ev(), ev(), ev()] for _ in range(steps)]
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    launches, infos = 0, []
+    for k in range(steps):
+        nl, info = one(marks[k])
+        launches += nl
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    setup = [m[0].elapsed_time(m[1]) for m in marks]
+    solve = [m[1].elapsed_time(m[2]) for m in marks]
+    return {"ms_per_step": total / steps, "setup_ms": statistics.median(setup),
+            "solve_ms": statistics.median(solve), "launches": launches, "iterations": infos[-1].iterations,
+            "n_levels": infos[-1].n_levels, "true_rel_residual": infos[-1].true_rel_residual}
+
+
+def kernel_roofline(amg, P, opts, sp, precision, steps=2):
+    """The dominant kernel (the level-0 fused smoother step) timed live with
+    CUDA events in a separate pass, so that the headline's steps carry no
+    timing nodes."""
+    import ctypes as C
+
+    nl_tot, ms_tot, bpl = 0, 0.0, 0.0
+    for _ in range(steps):
+        st, h = amg.amg_setup(P.g.n, P.rp, P.col, P.w, P.d, opts, amg.AMG_MEM_DEVICE, sp)
+        assert st == 0, amg.amg_last_error(None)
+        amg.lib().amg_kernel_timing(h, 1)
+        assert amg.amg_solve(h, P.bd, P.xd, P.nrhs, P.g.n, 1e-8, None) == 0
+        nl, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        amg.lib().amg_kernel_timing_read(h, C.byref(nl), C.byref(ms), C.byref(b))
+        nl_tot += nl.value
+        ms_tot += ms.value
+        bpl = b.value
+        amg.amg_free(h)
+    if nl_tot == 0:
+        return None
+    avg_ms = ms_tot / nl_tot
+    gbs = bpl / (avg_ms * 1e-3) / 1e9
+    # one step T_{j+1} = S T_j - T_{j-1}, x += c_j T_{j+1} with the smoother
+    # form S = 2 t(A): 2 flops per stored off-diagonal, the diagonal product,
+    # one subtraction and one FMA per row
+    flops = 2.0 * P.g.nnz + 4.0 * P.g.n
+    tflops = flops / (avg_ms * 1e-3) / 1e12
+    hbm_peak, peak_kind = peaks()
+    f64 = precision == 0
+    kname = "k_cheb_step<%s> (level 0: SELL-32 SpMV + Chebyshev recurrence step)" % ("double" if f64 else "float")
+    hbm_view = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)"}
+    alu_view = {"achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (an FMA probe measured 1.198)"}
+    traffic = profiled_traffic() if f64 else None
+    if f64 and alu_view["frac"] > hbm_view["frac"]:
+        roof = dict(bound="alu", traffic=traffic, hbm_view=hbm_view, **alu_view)
+    else:
+        roof = dict(bound="hbm", traffic=traffic, **hbm_view)
+        if f64:
+            roof["alu_view"] = alu_view
+    roof.update({"kernel": kname, "launches_timed": nl_tot, "avg_launch_us": avg_ms * 1e3,
+                 "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": flops})
+    return roof
+
+
+# ---------------------------------------------------------------------------
+# variants
+# ---------------------------------------------------------------------------
+def variant_fp32(amg, P, sp, stream, args, world, dev, cycle):
+    opts32 = make_opts(amg, P.p, amg.AMG_PREC_FP32, cycle)
+    r = timed_steps(amg, P, opts32, sp, stream, args.steps, args.warmup)
+    ms = max_over_ranks(r["ms_per_step"], world, dev)
+    return {"value": job_value(P.g.n * P.nrhs, world, ms), "unit": UNIT, "ms_per_step": ms,
+            "solve_dof_per_s": P.g.n * P.nrhs / (r["solve_ms"] * 1e-3), "setup_ms": r["setup_ms"],
+            "solve_ms": r["solve_ms"], "iterations": r["iterations"],
+            "roofline": kernel_roofline(amg, P, opts32, sp, 1),
+            "dtype": "f32 preconditioner / f64 outer CG, dots and coarsest solve"}
+
+
+def variant_c1(amg, dev, sp, stream):
+    """64^2 pure Laplacian: latency-bound, reported as us per solve."""
+    import torch
+
+    P = Problem("grid2d_64", dev)
+    opts = make_opts(amg, P.p, amg.AMG_PREC_FP64)
+    setups = []
+    for _ in range(8):
+        t0 = time.perf_counter()
+        st, h = amg.amg_setup(P.g.n, P.rp, P.col, P.w, P.d, opts, amg.AMG_MEM_DEVICE, sp)
+        setups.append((time.perf_counter() - t0) * 1e3)
+        assert st == 0
+        if _ < 7:
+            amg.amg_free(h)
+    info = amg.amg_info()
+    for _ in range(5):
+        assert amg.amg_solve(h, P.bd, P.xd, 1, P.g.n, 1e-8, info) == 0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    e0.record(stream)
+    for _ in range(reps):
+        amg.amg_solve(h, P.bd, P.xd, 1, P.g.n, 1e-8, info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    amg.amg_free(h)
+    dt, ref, _ = run_oracle_step(P.g, P.p, P.b)
+    return {"workload": WORKLOADS["grid2d_64"], "n": P.g.n, "us_per_solve": us,
+            "solve_dof_per_s": P.g.n / (us * 1e-6), "setup_ms_host": statistics.median(setups[2:]),
+            "iterations": info.iterations, "oracle_iterations": ref.iterations,
+            "cpu_baseline": {"value": P.g.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"oracle setup + solve in full, {dt * 1e3:.1f} ms single thread"}}
+
+
+def variant_c3(amg, dev, sp, stream):
+    """2048^2 random diagonals: fp64 GPU, fp32-preconditioner GPU, both against
+    the fp64 oracle (final error and iterations)."""
+    import torch
+
+    P = Problem("rdiag2d_2048", dev)
+    out = {"workload": WORKLOADS["rdiag2d_2048"], "n": P.g.n}
+    xs = {}
+    for prec, key in ((amg.AMG_PREC_FP64, "fp64"), (amg.AMG_PREC_FP32, "fp32_precond")):
+        opts = make_opts(amg, P.p, prec)
+        r = timed_steps(amg, P, opts, sp, stream, 3, 1)
+        xs[key] = P.xd.cpu().numpy().copy()
+        out[key] = {"value": P.g.n / (r["ms_per_step"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                    "solve_dof_per_s": P.g.n / (r["solve_ms"] * 1e-3), "setup_ms": r["setup_ms"],
+                    "solve_ms": r["solve_ms"], "iterations": r["iterations"],
+                    "true_rel_residual": r["true_rel_residual"]}
+    dt, ref, _ = run_oracle_step(P.g, P.p, P.b)
+    nx = np.linalg.norm(ref.x)
+    for key, x in xs.items():
+        out[key]["rel_error_vs_oracle"] = float(np.linalg.norm(x - ref.x) / nx)
+    out["oracle_iterations"] = ref.iterations
+    out["cpu_baseline"] = {"value": P.g.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": f"oracle setup + solve in full ({ref.iterations} iterations), "
+                                     f"{dt:.1f} s single thread"}
+    del P
+    torch.cuda.empty_cache()
+    return out
+
+
+def variant_c4(amg, dev, sp, stream):
+    """96^3 x 32 right-hand sides in one batched call, fp32 preconditioner."""
+    import torch
+
+    P = Problem("grid3d_96x32", dev)
+    opts = make_opts(amg, P.p, amg.AMG_PREC_FP32)
+    r = timed_steps(amg, P, opts, sp, stream, 3, 2)
+    units = P.g.n * P.nrhs
+    dt, ref, nc = run_oracle_step(P.g, P.p, P.b, 2)
+    out = {"workload": WORKLOADS["grid3d_96x32"], "n": P.g.n, "nrhs": P.nrhs,
+           "value": units / (r["ms_per_step"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms_per_step"],
+           "solve_dof_per_s": units / (r["solve_ms"] * 1e-3), "setup_ms": r["setup_ms"], "solve_ms": r["solve_ms"],
+           "iterations": r["iterations"], "oracle_iterations_col0": ref.iterations,
+           "dtype": "f32 preconditioner / f64 outer CG",
+           "cpu_baseline": {"value": P.g.n * nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"oracle setup + {nc} of {P.nrhs} right-hand sides, {dt:.1f} s single thread"}}
+    del P
+    torch.cuda.empty_cache()
+    return out
+
+
+def _build_serve_graph(spec):
+    return gg.serve_graph(spec)
+
+
+def serve_graphs(count):
+    """The serving pool, built by a process pool of the host's cores (spawned,
+    so that it is safe after CUDA initialisation)."""
+    import multiprocessing as mp
+
+    specs = gg.serve_graph_specs(count)
+    workers = max(1, min(8, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return list(pool.map(_build_serve_graph, specs, chunksize=1))
+
+
+def serve_bench(count_graphs=48, main_requests=2000, low_requests=600, oracle_requests=50):
+    """Solves/s and p50/p99 latency of the server under Poisson arrivals at
+    1.2x and 0.5x of its saturated throughput.  The main run starts cold: each
+    graph's hierarchy is set up when its first request arrives, under load."""
+    import paper_1307_6305_gb300 as amg
+
+    graphs = serve_graphs(count_graphs)
+    rng = np.random.default_rng(5)
+
+    def new_server():
+        srv = amg.Server(60 << 30, 8, batch_max=8, degree=4, passes=3, precision=amg.AMG_PREC_FP32)
+        return srv, [srv.add_graph(g) for g in graphs]
+
+    seed = [7000]
+
+    def pick():
+        gi = int(rng.integers(len(graphs)))
+        seed[0] += 1
+        return gi, gg.rhs(graphs[gi].n, seed[0], True)
+
+    # saturated throughput, cold: everything queued at once
+    srv, ids = new_server()
+    burst = [pick() for _ in range(256)]
+    t0 = time.perf_counter()
+    tickets = [srv.submit(ids[gi], b) for gi, b in burst]
+    for t in tickets:
+        assert srv.wait(t)[0] == 0
+    sat = len(burst) / (time.perf_counter() - t0)
+    srv.close()
+    srv, ids = new_server()
+    runs, stream_main = [], None
+    for load, count in ((1.2, main_requests), (0.5, low_requests)):
+        before = srv.stats()
+        rate = load * sat
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+        reqs = [pick() for _ in range(count)]
+        if stream_main is None:
+            stream_main = reqs
+        tickets = []
+        t0 = time.perf_counter()
+        for (gi, b), ta in zip(reqs, arrivals):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(ids[gi], b))
+        lat, iters = [], []
+        for t in tickets:
+            st, x, info, ms = srv.wait(t)
+            assert st == 0
+            lat.append(ms)
+            iters.append(info.iterations)
+        wall = time.perf_counter() - t0
+        after = srv.stats()
+        solves = after.solves - before.solves
+        runs.append({"offered_load": load, "offered_rate_per_s": rate, "requests": count,
+                     "solves_per_s": count / wall, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "mean_iterations": float(np.mean(iters)),
+                     "setups": int(after.setups - before.setups),
+                     "mean_batch": count / max(solves, 1), "peak_active": int(after.peak_active)})
+    stats = srv.stats()
+    srv.close()
+    # oracle on the first requests of the main stream: each graph set up once
+    # (as the server keeps hierarchies resident), every request solved
+    import oracle
+
+    sub = stream_main[:oracle_requests]
+    t0 = time.perf_counter()
+    orc_h = {}
+    for gi, b in sub:
+        if gi not in orc_h:
+            orc_h[gi] = oracle.Hierarchy(graphs[gi], degree=4, passes=3)
+        assert orc_h[gi].solve(b, tol=1e-8).status == 0
+    dt = time.perf_counter() - t0
+    main = runs[0]
+    return {"metric": "solves/s under Poisson arrivals at 1.2x saturated throughput (p50/p99 latency)",
+            "value": main["solves_per_s"], "unit": "solves/s", "saturated_solves_per_s": sat,
+            "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]}, "runs": runs,
+            "graphs": [int(g.n) for g in graphs],
+            "server": {"setups": int(stats.setups), "solves": int(stats.solves), "completed": int(stats.completed),
+                       "evictions": int(stats.evictions), "setup_retries": int(stats.setup_retries),
+                       "peak_active": int(stats.peak_active),
+                       "peak_resident_gb": stats.peak_resident_bytes / 2 ** 30},
+            "cpu_baseline": {"value": len(sub) / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the first {len(sub)} requests of the 1.2x stream, {len(orc_h)} graphs set "
+                                       f"up once each, {dt:.1f} s single thread"}}
+
+
+# ---------------------------------------------------------------------------
+def reference_arm(args, name, cycle):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, p = gg.workload(name)
+    nrhs = len(p["rhs_seeds"])
+    b = np.concatenate([gg.rhs(g.n, sd, gg.is_pure_laplacian(g)) for sd in p["rhs_seeds"]])
+    ncols = 1 if nrhs == 1 else 2          # bounded sample: two of the 32 columns
+    for _ in range(args.warmup):
+        run_oracle_step(g, p, b, ncols, cycle)
+    times = [run_oracle_step(g, p, b, ncols, cycle)[0] for _ in range(args.steps)]
+    ms = 1e3 * sum(times) / len(times)
+    value = g.n * ncols / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(name, g, nrhs, world, cycle),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"oracle setup + {ncols} of {nrhs} right-hand sides per step, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
@@ -264,7 +572,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-variant", action="store_true", help="skip the fp32-preconditioner variant")
+    ap.add_argument("--no-variant", action="store_true", help="same as --variants none")
+    ap.add_argument("--variants", default="all", help="all, none, or a comma list of " + ",".join(VARIANTS))
     ap.add_argument("--workload", default="grid3d_128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32: the whole preconditioner in fp32 inside the fp64 outer CG")
@@ -274,33 +583,20 @@ def main():
     CYCLE = 1 if args.cycle == "amli" else 0
     rank, world, local = dist_env()
     if args.workload == "serve":
-        return serve_bench(args) if args.impl == "ours" and rank == 0 else 0
-    WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOADS[args.workload]
-    g, p = gg.workload(WORKLOAD)
-    nrhs = len(p["rhs_seeds"])
-    if nrhs > 1:
-        args.precision = "fp32" if p["precision"] else args.precision
-    b = np.concatenate([gg.rhs(g.n, sd, gg.is_pure_laplacian(g)) for sd in p["rhs_seeds"]])
-
-    if args.impl == "reference":
-        if rank != 0:
+        if args.impl != "ours" or rank != 0:
             return 0
-        ncols = 1 if nrhs == 1 else 2          # bounded sample: two of the 32 columns
-        for _ in range(args.warmup):
-            run_oracle_step(g, p, b, ncols, CYCLE)
-        times = [run_oracle_step(g, p, b, ncols, CYCLE)[0] for _ in range(args.steps)]
-        ms = 1e3 * sum(times) / len(times)
-        value = g.n * ncols / (ms / 1e3)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD_DESC + ("" if CYCLE == 0 else "; stationary AMLI W-cycle"),
-                           "n": g.n, "nrhs": nrhs},
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"oracle setup + {ncols} of {nrhs} right-hand sides per step, single thread"},
-                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        import torch
+
+        torch.cuda.set_device(0)
+        r = serve_bench()
+        r.update({"n_gpus": 1, "steps": r["runs"][0]["requests"], "warmup": 256,
+                  "ms_per_step": 1e3 / r["value"], "higher_is_better": True, "scaling": "weak",
+                  "vs_baseline": None, "dtype": "f32 preconditioner / f64 outer", "data": "synthetic",
+                  "config": {"workload": WORKLOADS["serve"]}})
+        print(json.dumps(r), flush=True)
         return 0
+    if args.impl == "reference":
+        return reference_arm(args, args.workload, CYCLE)
 
     import torch
 
@@ -314,41 +610,16 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
-    rp = torch.as_tensor(g.rowptr, device=dev)
-    col = torch.as_tensor(g.col, device=dev)
-    w = torch.as_tensor(g.w, device=dev)
-    d = None if g.d is None else torch.as_tensor(g.d, device=dev)
-    bd = torch.as_tensor(b, device=dev)          # column j at bd[j*n:(j+1)*n]
-    xd = torch.zeros_like(bd)
-    in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + b.nbytes
+    P = Problem(args.workload, dev)
+    g, nrhs = P.g, P.nrhs
+    if nrhs > 1:
+        args.precision = "fp32" if P.p["precision"] else args.precision
     prec = amg.AMG_PREC_FP32 if args.precision == "fp32" else amg.AMG_PREC_FP64
-    opts = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=prec, cycle=CYCLE,
-                                   aggregation=p.get("aggregation", 0))
-    state = {"launches": 0, "iters": [], "setup_ms": [], "solve_ms": [], "kt": [0, 0.0, 0.0]}
+    opts = make_opts(amg, P.p, prec, CYCLE)
 
-    def step(timed_kernel: bool):
-        st, h = amg.amg_setup(g.n, rp, col, w, d, opts, amg.AMG_MEM_DEVICE, sp)
-        assert st == 0, amg.amg_last_error(None)
-        launches = amg.lib().amg_launch_count(h)
-        if timed_kernel:
-            amg.lib().amg_kernel_timing(h, 1)
-        info = amg.amg_info()
-        st = amg.amg_solve(h, bd, xd, nrhs, g.n, 1e-8, info)
-        assert st == 0, amg.amg_last_error(h)
-        launches += amg.lib().amg_launch_count(h)
-        if timed_kernel:
-            import ctypes as C
-
-            nl, ms, bpl = C.c_int64(), C.c_double(), C.c_double()
-            amg.lib().amg_kernel_timing_read(h, C.byref(nl), C.byref(ms), C.byref(bpl))
-            state["kt"][0] += nl.value
-            state["kt"][1] += ms.value
-            state["kt"][2] = bpl.value
-        amg.amg_free(h)
-        return launches, info
-
+    # ---- headline: setup + solve steps, nothing else on the stream ----
     for _ in range(args.warmup):
-        step(False)
+        timed_steps(amg, P, opts, sp, stream, 1, 0)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -358,60 +629,25 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    launches = 0
-    last_info = None
-    for _ in range(args.steps):
-        nl, last_info = step(True)
-        launches += nl
-        state["iters"].append(last_info.iterations)
-        state["setup_ms"].append(last_info.setup_ms)
-        state["solve_ms"].append(last_info.solve_ms)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    head = timed_steps(amg, P, opts, sp, stream, args.steps, 0)
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    ms = max_over_ranks(head["ms_per_step"], world, dev)
+    solve_ms = max_over_ranks(head["solve_ms"], world, dev)
     value = job_value(g.n * nrhs, world, ms)
 
-    # the fp32-preconditioner form on the same workload (the metric compares both)
-    variant = None
-    if args.precision == "fp64" and nrhs == 1 and not args.no_variant:
-        opts32 = amg.amg_default_options(degree=p["degree"], passes=p["passes"], precision=amg.AMG_PREC_FP32,
-                                         cycle=CYCLE, aggregation=p.get("aggregation", 0))
-        its = []
+    # ---- the dominant kernel, timed in its own pass ----
+    roof = kernel_roofline(amg, P, opts, sp, prec) if nrhs == 1 else None
 
-        def step32():
-            st, h = amg.amg_setup(g.n, rp, col, w, d, opts32, amg.AMG_MEM_DEVICE, sp)
-            assert st == 0
-            info = amg.amg_info()
-            assert amg.amg_solve(h, bd, xd, nrhs, g.n, 1e-8, info) == 0
-            its.append(info.iterations)
-            amg.amg_free(h)
-
-        for _ in range(args.warmup):
-            step32()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step32()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / args.steps
-        ms32 = max_over_ranks(ms32, world, dev)
-        variant = {"fp32_precond": {"value": job_value(g.n * nrhs, world, ms32), "unit": UNIT, "ms_per_step": ms32,
-                                    "iterations": its[-1],
-                                    "dtype": "f32 preconditioner / f64 outer CG, dots and coarsest solve"}}
-
-    # end to end through the C ABI with pinned host buffers (H2D + D2H inside)
+    # ---- end to end through the C ABI with pinned host buffers (H2D + D2H inside) ----
     e2e_steps = 0 if args.no_e2e else args.steps
     pin = lambda a: torch.as_tensor(a).pin_memory()
     hrp, hcol, hw = pin(g.rowptr), pin(g.col), pin(g.w)
     hd = None if g.d is None else pin(g.d)
-    hb = pin(b)
+    hb = pin(P.b)
     hx = torch.zeros_like(hb).pin_memory()
+    in_bytes = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + (0 if g.d is None else g.d.nbytes) + P.b.nbytes
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -425,41 +661,31 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / max(e2e_steps, 1) if e2e_steps else float("nan")
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
+
+    # ---- the other configurations (rank 0 of a single-GPU run only) ----
+    want = set() if args.no_variant or args.variants == "none" else (
+        set(VARIANTS) if args.variants == "all" else set(args.variants.split(",")))
+    variants = {}
+    if "fp32" in want and args.precision == "fp64" and nrhs == 1:
+        variants["fp32_precond"] = guarded("fp32", lambda: variant_fp32(amg, P, sp, stream, args, world, dev, CYCLE))
+    if world == 1 and args.workload == "grid3d_128" and CYCLE == 0:
+        if "c1" in want:
+            variants["c1_grid2d_64"] = guarded("c1", lambda: variant_c1(amg, dev, sp, stream))
+        if "c3" in want:
+            variants["c3_rdiag2d_2048"] = guarded("c3", lambda: variant_c3(amg, dev, sp, stream))
+        if "c4" in want:
+            variants["c4_grid3d_96x32"] = guarded("c4", lambda: variant_c4(amg, dev, sp, stream))
+        if "c5" in want:
+            variants["c5_serve"] = guarded("c5", serve_bench)
     if world > 1:
         dist.barrier()
     if rank != 0:
         dist.destroy_process_group()
         return 0
 
-    nl, kms, bpl = state["kt"]
-    avg_ms = kms / max(nl, 1)
-    gbs = bpl / (avg_ms * 1e-3) / 1e9 if nl else None
-    # one step T_{j+1} = S T_j - T_{j-1}, x += c_j T_{j+1} with the smoother form
-    # S = 2 t(A): 2 flops per stored off-diagonal, the diagonal product, one
-    # subtraction and one FMA per row
-    flops = 2.0 * g.nnz + 4.0 * g.n
-    tflops = flops / (avg_ms * 1e-3) / 1e12 if nl else None
-    hbm_peak, peak_kind = peaks()
-    kname = "k_cheb_step<%s> (level 0: SELL-32 SpMV + Chebyshev recurrence step)" % (
-        "double" if args.precision == "fp64" else "float")
-    hbm_view = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if gbs else None,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)"}
-    alu_view = {"achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS if tflops else None,
-                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (an FMA probe measured 1.198)"}
-    if args.precision == "fp64" and (alu_view["frac"] or 0) > (hbm_view["frac"] or 0):
-        # the FP64 pipe (2 lanes/clk/SM on this part) is the closer ceiling
-        roof = dict(bound="alu", traffic=profiled_traffic(), hbm_view=hbm_view, **alu_view)
-    else:
-        roof = dict(bound="hbm", traffic=profiled_traffic() if args.precision == "fp64" else None,
-                    **{k: v for k, v in hbm_view.items()})
-        if args.precision == "fp64":
-            roof["alu_view"] = alu_view
-    roof.update({"kernel": kname, "launches_timed": nl, "avg_launch_us": avg_ms * 1e3,
-                 "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": flops})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        dt, r, nc = run_oracle_step(g, p, b, 1 if nrhs == 1 else 2, CYCLE)
+        dt, r, nc = run_oracle_step(g, P.p, P.b, 1 if nrhs == 1 else 2, CYCLE)
         cpu = {"value": g.n * nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle setup + {nc} of {nrhs} right-hand sides ({r.iterations} iterations), "
                          f"{dt:.1f} s single thread"}
@@ -467,17 +693,14 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 preconditioner / f64 outer",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC + ("" if CYCLE == 0 else "; stationary AMLI W-cycle instead of the K-cycle"),
-                   "n": g.n, "nrhs": nrhs, "nnz_offdiag": g.nnz,
-                   "l2": f"inputs {in_bytes / 2**20:.0f} MiB > 129 MiB L2 (no flush)",
-                   "parallelism": f"replicas x{world}"},
-        "iterations": state["iters"][-1], "setup_ms_host": statistics.median(state["setup_ms"]),
-        "solve_ms_host": statistics.median(state["solve_ms"]),
+        "data": "synthetic", "config": workload_config(args.workload, g, nrhs, world, CYCLE),
+        "solve_dof_per_s": job_value(g.n * nrhs, world, solve_ms),
+        "iterations": head["iterations"], "n_levels": head["n_levels"],
+        "setup_ms": head["setup_ms"], "solve_ms": head["solve_ms"],
         "e2e": {"value": job_value(g.n * nrhs, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": b.nbytes, "ms_per_step": e2e_ms},
-        "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": ck,
-        "variants": variant,
+                "d2h_bytes_per_step": P.b.nbytes, "ms_per_step": e2e_ms},
+        "gpu_launches": head["launches"], "roofline": roof, "cpu_baseline": cpu, "clocks": ck,
+        "variants": variants or None,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

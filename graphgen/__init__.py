@@ -295,5 +295,26 @@ def workload(name: str) -> tuple[Graph, dict]:
     raise KeyError(name)
 
 
+def serve_graph_specs(count: int, seed: int = 5) -> list[tuple[str, int, int]]:
+    """The serving workload's graphs as (kind, n, seed): target sizes
+    log-uniform in [1e4, 1e6] (u from splitmix64(seed ^ index)); kinds cycle
+    random geometric, random geometric, 2D 5-point grid, 3D 7-point grid (half
+    random geometric graphs, a quarter each grid shape of the nearest size)."""
+    u = uniform01(seed, count)
+    sizes = np.exp(np.log(1e4) + u * np.log(100.0))
+    kinds = ("rgg", "rgg", "grid2d", "grid3d")
+    return [(kinds[i % 4], int(sizes[i]), 100 * seed + i) for i in range(count)]
+
+
+def serve_graph(spec: tuple[str, int, int]) -> Graph:
+    """Build one graph of serve_graph_specs (pure Laplacians, unit weights)."""
+    kind, n, sd = spec
+    if kind == "rgg":
+        return random_geometric(n, sd)
+    if kind == "grid2d":
+        return grid2d_5pt(max(2, int(round(np.sqrt(n)))))
+    return grid3d_7pt(max(2, int(round(n ** (1.0 / 3.0)))), None)
+
+
 def is_pure_laplacian(g: Graph) -> bool:
     return g.d is None or not np.any(g.d)

@@ -177,7 +177,9 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
  *           preconditioner applied to all of them in one multi-vector pass
  *  info     optional report (may be NULL)
  * Returns AMG_OK, AMG_ERR_NOT_CONVERGED (x holds the last iterate),
- * AMG_ERR_BREAKDOWN, AMG_ERR_INVALID_ARG or AMG_ERR_CUDA.
+ * AMG_ERR_BREAKDOWN, AMG_ERR_INVALID_ARG (also when a right-hand side has a
+ * NaN or infinite entry, or a norm beyond the fp64 range; x is then
+ * unspecified) or AMG_ERR_CUDA.
  */
 amg_status amg_solve(amg_handle h, const double *rhs, double *x, int nrhs, int64_t ld, double tol,
                      amg_info *info);
@@ -277,14 +279,23 @@ amg_status amg_match_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *c
 /* Serving (not in the paper: a request loop around amg_setup/amg_solve).  */
 /*                                                                        */
 /* Continuous batching on one GPU: registered graphs keep their hierarchy */
-/* resident; solve requests are admitted as soon as one of `max_active`   */
-/* slots and device memory under `mem_cap_bytes` are free (idle           */
-/* hierarchies are evicted least-recently-used first); solves of          */
-/* different graphs run concurrently on their own streams, requests for   */
-/* one graph take turns.  Results are bit-identical to solving alone.     */
-/* A hierarchy's size is its arena bytes, measured at its first setup     */
-/* (estimated from n and nnz before that); a request whose hierarchy      */
-/* alone exceeds mem_cap_bytes completes with AMG_ERR_OOM.                */
+/* resident; work is admitted as soon as one of `max_active` slots and    */
+/* device memory under `mem_cap_bytes` are free (idle hierarchies are     */
+/* evicted least-recently-used first).  A slot takes the oldest queued    */
+/* request whose graph is idle together with the other queued requests   */
+/* for that graph and tolerance, up to `batch_max`, and solves them in    */
+/* one multi-right-hand-side call (one sweep over the levels serves the   */
+/* whole batch); solves of different graphs run concurrently on their own */
+/* streams.  With batch_max >= 2 every solve runs the block kernels at    */
+/* one fixed width (the smallest power of two >= batch_max), so a        */
+/* request's result does not depend on what else is queued; with          */
+/* batch_max 0 or 1 requests for one graph take turns on the             */
+/* single-right-hand-side path.  A hierarchy's size is its arena bytes,   */
+/* measured at its first setup (estimated from n and nnz before that); a  */
+/* setup whose measured size does not fit beside the busy hierarchies     */
+/* gives its memory back and its requests are queued again (counted in    */
+/* setup_retries), so resident bytes stay under the cap; a request whose  */
+/* hierarchy alone exceeds mem_cap_bytes completes with AMG_ERR_OOM.      */
 /* All pointers are host memory; the server copies what it needs.         */
 /* ---------------------------------------------------------------------- */
 
@@ -293,6 +304,8 @@ typedef struct amg_server_s *amg_server;
 typedef struct {
   size_t mem_cap_bytes;  /* device bytes for resident hierarchies (>= 1 MiB) */
   int max_active;        /* concurrent solves, 1..64                         */
+  int batch_max;         /* requests of one graph solved together, 0..32
+                            (0, 1: no batching)                              */
   amg_options opt;       /* solver options of every request                  */
 } amg_server_config;
 
@@ -303,6 +316,8 @@ typedef struct {
   size_t resident_bytes, peak_resident_bytes;
   int active, peak_active;
   int64_t queued, completed, setups, evictions;
+  int64_t solves;         /* solve calls; completed / solves = mean batch size */
+  int64_t setup_retries;  /* setups redone to keep resident bytes under the cap */
 } amg_server_stats_t;
 
 amg_status amg_server_create(const amg_server_config *cfg, amg_server *out);
@@ -310,7 +325,9 @@ amg_status amg_server_create(const amg_server_config *cfg, amg_server *out);
  * is built by the first request that needs it */
 amg_status amg_server_add_graph(amg_server s, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                                 const double *w, const double *d, int64_t *graph_id);
-/* queue one right-hand side (n doubles) for graph_id; *ticket identifies it */
+/* queue one right-hand side (n doubles) for graph_id; *ticket identifies it.
+ * A right-hand side with a non-finite entry (or whose norm overflows) is
+ * refused with AMG_ERR_INVALID_ARG. */
 amg_status amg_server_submit(amg_server s, int64_t graph_id, const double *rhs, double tol, int64_t *ticket);
 /* *done = 0 while the request runs; once done, copies the solution into x
  * (n doubles, may be NULL), the report into info (history not filled), the

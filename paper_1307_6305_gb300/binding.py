@@ -66,13 +66,15 @@ class amg_info(C.Structure):
 
 
 class amg_server_config(C.Structure):
-    _fields_ = [("mem_cap_bytes", C.c_size_t), ("max_active", C.c_int), ("opt", amg_options)]
+    _fields_ = [("mem_cap_bytes", C.c_size_t), ("max_active", C.c_int), ("batch_max", C.c_int),
+                ("opt", amg_options)]
 
 
 class amg_server_stats_t(C.Structure):
     _fields_ = [("resident_bytes", C.c_size_t), ("peak_resident_bytes", C.c_size_t), ("active", C.c_int),
                 ("peak_active", C.c_int), ("queued", C.c_int64), ("completed", C.c_int64),
-                ("setups", C.c_int64), ("evictions", C.c_int64)]
+                ("setups", C.c_int64), ("evictions", C.c_int64), ("solves", C.c_int64),
+                ("setup_retries", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -310,10 +312,11 @@ class Hierarchy:
 class Server:
     """Continuous-batching solve server (amg_server_* of the C ABI)."""
 
-    def __init__(self, mem_cap_bytes: int, max_active: int, **opts):
+    def __init__(self, mem_cap_bytes: int, max_active: int, batch_max: int = 8, **opts):
         cfg = amg_server_config()
         cfg.mem_cap_bytes = int(mem_cap_bytes)
         cfg.max_active = int(max_active)
+        cfg.batch_max = int(batch_max)
         cfg.opt = amg_default_options(**opts)
         h = C.c_void_p()
         self.status = lib().amg_server_create(C.byref(cfg), C.byref(h))

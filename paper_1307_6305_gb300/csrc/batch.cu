@@ -496,12 +496,26 @@ static amg_status bprecondition(amg_handle_s *h) {
   return bkcycle<double>(h, 0, h->bo_r, h->bo_z);
 }
 
-// buffers for blocks of up to kMaxBlock columns, allocated on first use
-static amg_status ensure_batch_buffers(amg_handle_s *h) {
-  if (h->bw) return AMG_OK;
+// buffers for blocks of up to W columns (W a power of two <= kMaxBlock),
+// allocated on first use and re-allocated, larger, when a later solve needs
+// a wider block (the old ones are released stream-ordered and the captured
+// block preconditioner, which points at them, is dropped)
+static amg_status ensure_batch_buffers(amg_handle_s *h, int W) {
+  if (h->bw >= W) return AMG_OK;
+  if (h->bw) {
+    if (h->bpre_exec) {
+      cudaGraphExecDestroy(h->bpre_exec);
+      h->bpre_exec = nullptr;
+    }
+    for (void *p : h->batch_blocks) h->arena.free_block(p);
+    h->batch_blocks.clear();
+    h->bw = 0;
+    h->tuned_for = 0;
+  }
   const bool f32 = h->opt.precision == AMG_PREC_FP32;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
-  const int W = kMaxBlock, L = h->L, nu = h->opt.inner_iters;
+  const int L = h->L, nu = h->opt.inner_iters;
+  const size_t blocks_before = h->arena.blocks.size();
   h->blv.assign(L, amg::BatchLevel());
   for (int k = 0; k < L; ++k) {
     amg::BatchLevel &B = h->blv[k];
@@ -544,7 +558,8 @@ static amg_status ensure_batch_buffers(amg_handle_s *h) {
     AMG_TRY(h->arena.alloc(&h->b_r32, sizeof(float) * n0));
     AMG_TRY(h->arena.alloc(&h->b_z32, sizeof(float) * n0));
   }
-  if (!h->b_pinned) AMG_CUDA_TRY(cudaMallocHost((void **)&h->b_pinned, sizeof(double) * 8 * W));
+  h->batch_blocks.assign(h->arena.blocks.begin() + (ptrdiff_t)blocks_before, h->arena.blocks.end());
+  if (!h->b_pinned) AMG_CUDA_TRY(cudaMallocHost((void **)&h->b_pinned, sizeof(double) * 8 * kMaxBlock));
   h->bw = W;
   return AMG_OK;
 }
@@ -671,7 +686,7 @@ static amg_status autotune(amg_handle_s *h, int nrhs) {
   double best = 1e300;
   int bkb = cap, btile = 256;
   std::string log;
-  AMG_CUDA_TRY(cudaMemsetAsync(h->bo_r, 0, sizeof(double) * h->n * kMaxBlock, h->stream));
+  AMG_CUDA_TRY(cudaMemsetAsync(h->bo_r, 0, sizeof(double) * h->n * h->bw, h->stream));
   for (int kb = std::max(1, cap / 4); kb <= cap; kb *= 2) {
     for (int tile : {128, 256, 512}) {
       h->bw_use = kb;
@@ -730,7 +745,7 @@ static amg_status autotune(amg_handle_s *h, int nrhs) {
 // one block of nr (<= kb) columns: outer flexible CG per column, fp64
 static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int nr, int64_t ld, double tol,
                               amg_info *info, int *iters, double *rel, double *true_rel, int *conv,
-                              bool *breakdown) {
+                              bool *breakdown, ColumnReport *cols) {
   const int kb = h->bw_use, n = (int)h->n, R = h->opt.restart;
   const int64_t nk = (int64_t)n * kb;
   cudaStream_t st = h->stream;
@@ -764,7 +779,7 @@ static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int
       return fail(AMG_ERR_INVALID_ARG, "right-hand side " + std::to_string(c) +
                                            " has a non-finite entry or a norm beyond the fp64 range");
   std::vector<double> nb(kb), res(kb, 0.0);
-  std::vector<int> done(kb, 0), brk(kb, 0);
+  std::vector<int> done(kb, 0), brk(kb, 0), col_it(kb, 0);
   int remaining = 0;
   for (int c = 0; c < kb; ++c) {
     nb[c] = sqrt(hp[c]);
@@ -826,6 +841,7 @@ static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int
         continue;
       }
       res[c] = sqrt(hp[c]) / nb[c];
+      col_it[c] = it;
       if (res[c] <= tol) {
         done[c] = 1;
         --remaining;
@@ -868,9 +884,17 @@ static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int
   bool anybrk = false;
   for (int c = 0; c < nr; ++c) {
     mrel = std::max(mrel, res[c]);
-    if (nb[c] > 0.0) mtrue = std::max(mtrue, sqrt(hp[c]) / nb[c]);
+    const double tr = nb[c] > 0.0 ? sqrt(hp[c]) / nb[c] : 0.0;
+    mtrue = std::max(mtrue, tr);
     all &= (done[c] && !brk[c]);
     anybrk |= brk[c] != 0;
+    if (cols) {
+      cols[c].iterations = col_it[c];
+      cols[c].rel_residual = res[c];
+      cols[c].true_rel_residual = tr;
+      cols[c].converged = done[c] && !brk[c];
+      cols[c].breakdown = brk[c] != 0;
+    }
   }
   *iters = it;
   *rel = mrel;
@@ -880,12 +904,35 @@ static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int
   return AMG_OK;
 }
 
-// Solve nrhs >= 2 right-hand sides (device pointers, column major with ld)
-// in blocks of the tuned width.
+// Buffers and the captured block preconditioner for solves at a fixed width
+// (the server calls this right after a setup, so that the hierarchy's arena
+// bytes include them).
+amg_status prepare_batched(amg_handle_s *h, int width) {
+  if (!valid_shape(width, 256)) return fail(AMG_ERR_INVALID_ARG, "block width must be 1, 2, 4, 8, 16 or 32");
+  AMG_TRY(ensure_batch_buffers(h, width));
+  if (h->tuned_for != -width || !h->bpre_exec) {
+    h->bw_use = width;
+    h->b_tile = 256;
+    h->tuned_for = -width;
+    AMG_TRY(capture_batch_graph(h));
+  }
+  return AMG_OK;
+}
+
+// Solve nrhs right-hand sides (device pointers, column major with ld) in
+// blocks of the tuned width, or of a fixed width.
 amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs, int64_t ld, double tol,
-                         amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown) {
-  AMG_TRY(ensure_batch_buffers(h));
-  AMG_TRY(autotune(h, nrhs));
+                         amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown,
+                         int fixed_width, ColumnReport *cols) {
+  if (fixed_width > 0) {
+    // a block shape that does not depend on nrhs: every column runs the same
+    // kernels at the same width whatever else shares its block
+    if (!valid_shape(fixed_width, 256)) return fail(AMG_ERR_INVALID_ARG, "block width must be 1, 2, 4, 8, 16 or 32");
+    AMG_TRY(prepare_batched(h, fixed_width));
+  } else {
+    AMG_TRY(ensure_batch_buffers(h, std::min(kMaxBlock, pow2_at_least(nrhs))));
+    AMG_TRY(autotune(h, nrhs));
+  }
   int mit = 0, all = 1;
   double mrel = 0.0, mtrue = 0.0;
   bool brk = false;
@@ -895,7 +942,7 @@ amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs
     double r1 = 0.0, t1 = 0.0;
     bool b1 = false;
     AMG_TRY(solve_block(h, rhs + (int64_t)c0 * ld, x + (int64_t)c0 * ld, nr, ld, tol, c0 == 0 ? info : nullptr,
-                        &it, &r1, &t1, &cv, &b1));
+                        &it, &r1, &t1, &cv, &b1, cols ? cols + c0 : nullptr));
     mit = std::max(mit, it);
     mrel = std::max(mrel, r1);
     mtrue = std::max(mtrue, t1);

@@ -86,15 +86,57 @@ void pool_free(void *p, cudaStream_t s) {
 amg_status Arena::alloc(void **p, size_t nbytes) {
   AMG_TRY(pool_alloc(p, nbytes, stream));
   blocks.push_back(*p);
+  sizes.push_back(nbytes);
   bytes += nbytes;
   return AMG_OK;
+}
+
+void Arena::free_block(void *p) {
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    if (blocks[i] != p) continue;
+    pool_free(p, stream);
+    bytes -= sizes[i];
+    blocks.erase(blocks.begin() + (ptrdiff_t)i);
+    sizes.erase(sizes.begin() + (ptrdiff_t)i);
+    return;
+  }
 }
 
 void Arena::release() {
   for (void *p : blocks) pool_free(p, stream);
   blocks.clear();
+  sizes.clear();
   bytes = 0;
   cudaStreamSynchronize(stream);
+}
+
+// The server's batched solve: nr host columns (n doubles each, one pointer
+// per request) staged into one column-major device block, solved by the
+// multi-right-hand-side path at the fixed block width `width`, and copied
+// back column by column.  Runs on the handle's stream; returns after the
+// copies have completed.
+amg_status solve_host_columns(amg_handle_s *h, const double *const *rhs, double *const *x, int nr, double tol,
+                              int width, ColumnReport *cols) {
+  const int64_t n = h->n;
+  const size_t col_bytes = sizeof(double) * (size_t)n, bytes = col_bytes * (size_t)nr;
+  cudaStream_t st = h->stream;
+  double *bd = nullptr, *xd = nullptr;
+  AMG_TRY(pool_alloc((void **)&bd, bytes, st));
+  amg_status s = pool_alloc((void **)&xd, bytes, st);
+  for (int c = 0; c < nr && !s; ++c)
+    if (cudaMemcpyAsync(bd + (size_t)c * n, rhs[c], col_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      s = fail(AMG_ERR_CUDA, "copy of a right-hand side");
+  int it = 0, conv = 0;
+  double rel = 0.0, tr = 0.0;
+  bool brk = false;
+  if (!s) s = solve_batched(h, bd, xd, nr, n, tol, nullptr, &it, &rel, &tr, &conv, &brk, width, cols);
+  for (int c = 0; c < nr && !s; ++c)
+    if (cudaMemcpyAsync(x[c], xd + (size_t)c * n, col_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      s = fail(AMG_ERR_CUDA, "copy of a solution");
+  if (!s && cudaStreamSynchronize(st) != cudaSuccess) s = fail(AMG_ERR_CUDA, "batched solve");
+  pool_free(bd, st);
+  pool_free(xd, st);
+  return s;
 }
 
 }  // namespace amg
@@ -344,7 +386,7 @@ amg_status amg_solve(amg_handle h, const double *rhs, double *x, int nrhs, int64
     int it = 0, conv = 0;
     double rel = 0.0, tr = 0.0;
     bool brk = false;
-    if (!s) s = solve_batched(h, bd, xd, nrhs, ld, tol, info, &it, &rel, &tr, &conv, &brk);
+    if (!s) s = solve_batched(h, bd, xd, nrhs, ld, tol, info, &it, &rel, &tr, &conv, &brk, 0, nullptr);
     if (!s && !xdev) {
       if (cudaMemcpyAsync(x, xstage, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
           cudaStreamSynchronize(h->stream) != cudaSuccess)

@@ -33,6 +33,7 @@ constexpr int kMaxInner = 8;      // largest nu
 constexpr int kMaxWindow = 16;    // largest outer restart window
 constexpr int kMaxDots = 8;       // dots per fused reduction
 constexpr int kRedBlocks = 608;   // partial sums per reduction = 4 x 152 SMs
+constexpr int kMaxBatchServe = 32; // largest server batch (the widest block)
 constexpr int kStallMaxCoarse = 4096;
 constexpr double kStallRatio = 0.95;
 // largest vertex count: the one-thread-per-row kernels index rows in 32-bit
@@ -94,8 +95,10 @@ struct NvtxPhase {
 struct Arena {
   cudaStream_t stream = nullptr;
   std::vector<void *> blocks;
+  std::vector<size_t> sizes;
   size_t bytes = 0;
   amg_status alloc(void **p, size_t bytes);
+  void free_block(void *p);  // stream-ordered release of one block
   template <typename T>
   amg_status get(T **p, size_t count) {
     return alloc(reinterpret_cast<void **>(p), count * sizeof(T));
@@ -139,11 +142,17 @@ struct SellView {
   const int32_t *__restrict__ scol;
   const T *__restrict__ val;
   const T *__restrict__ diag;
+  // 1: the stored values and columns are read with the streaming
+  // (evict-first) cache policy -- levels whose matrix is far larger than L2,
+  // so that one pass over it does not evict the vectors and the smaller
+  // levels' working sets
+  int stream = 0;
 };
 
 struct Level {
   int n = 0;
   int wps = 1;           // warps per SELL slice in the solve kernels (1, 2, 4 or 8)
+  int stream = 0;        // matrix loads with the streaming cache policy (SellView::stream)
   Csr A;                 // setup form
   double *diag = nullptr;
   double *dlow = nullptr;
@@ -237,6 +246,7 @@ struct amg_handle_s {
   int tuned_for = 0;
   std::string tune_log;
   std::vector<amg::BatchLevel> blv;
+  std::vector<void *> batch_blocks;  // arena blocks of the batched path (for re-allocation)
   double *bo_b = nullptr, *bo_x = nullptr, *bo_r = nullptr, *bo_z = nullptr, *bo_t = nullptr;
   double *boD[amg::kMaxWindow] = {}, *boQ[amg::kMaxWindow] = {};
   double *bo_scal = nullptr;
@@ -247,6 +257,7 @@ struct amg_handle_s {
   cudaGraphExec_t bpre_exec = nullptr;
   int64_t bgraph_kernels = 0;
   double setup_ms = 0;
+  int match_rounds_hint = 0;         // rounds of the last matching pass (setup)
   double grid_complexity = 0, op_complexity = 0;
   int64_t launches = 0;
   amg::Timing timing;
@@ -275,8 +286,23 @@ amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32
 amg_status allocate_solve_buffers(amg_handle_s *h);
 amg_status build_dense_two_level(amg_handle_s *h);
 // batch.cu
+// outcome of one column of a multi-right-hand-side solve
+struct ColumnReport {
+  int iterations = 0;  // outer iterations until the column met tol (or stopped)
+  double rel_residual = 0.0, true_rel_residual = 0.0;
+  bool converged = false, breakdown = false;
+};
+// nrhs right-hand sides (device, column major with ld) in blocks of the
+// autotuned width, or of `fixed_width` (1..32, a power of two) when > 0;
+// `cols` (optional, nrhs entries) receives each column's outcome
 amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs, int64_t ld, double tol,
-                         amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown);
+                         amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown,
+                         int fixed_width = 0, ColumnReport *cols = nullptr);
+amg_status prepare_batched(amg_handle_s *h, int width);
+// capi.cu: the server's batched solve: host columns in and out, staged
+// through device buffers of the handle's pool
+amg_status solve_host_columns(amg_handle_s *h, const double *const *rhs, double *const *x, int nr, double tol,
+                              int width, ColumnReport *cols);
 // leaf.cu
 amg_status prepare_leaf(amg_handle_s *h);
 amg_status launch_leaf(amg_handle_s *h);

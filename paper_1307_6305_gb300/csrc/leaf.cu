@@ -44,8 +44,7 @@ namespace cg = cooperative_groups;
 
 namespace amg {
 
-constexpr int kLeafThreads = 256;
-constexpr int kLeafWarps = kLeafThreads / 32;
+constexpr int kLeafDefaultThreads = 256;  // CTA size; 512 and 1024 are also instantiated
 constexpr int kLeafMaxC = 16;
 constexpr int kLeafMaxInner = 4;
 constexpr int kLeafMaxRows = 2048;    // rows of level k0
@@ -80,6 +79,7 @@ enum LeafArr : int {
 template <typename T>
 struct LeafParams {
   int n, nH, C, R, RH, m, nu, tpr;
+  int nt;                 // threads per CTA (the kernel's template argument)
   int maxnz, maxmem;
   double two_sa, two_ca;  // smoother form: 2 sa = 4/(l1 - l0), 2 ca = 2 (l1 + l0)/(l1 - l0)
   T coef[kMaxDegree + 1];
@@ -127,7 +127,7 @@ static unsigned leaf_layout(LeafParams<T> &P) {
   esz[A_BROWS] = esz[A_ABROWS] = sizeof(double);
   cnt[A_SLOTS] = 2 * (size_t)P.C * kLeafSlot;
   esz[A_SLOTS] = sizeof(double);
-  cnt[A_WRED] = kLeafWarps * kLeafSlot;
+  cnt[A_WRED] = (size_t)(P.nt / 32) * kLeafSlot;
   esz[A_WRED] = sizeof(double);
   size_t o = 0;
   for (int a = 0; a < A_COUNT; ++a) {
@@ -139,8 +139,9 @@ static unsigned leaf_layout(LeafParams<T> &P) {
   return P.smem;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kLeafThreads) k_leaf(const __grid_constant__ LeafParams<T> P) {
+template <typename T, int kLeafThreads>
+__global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant__ LeafParams<T> P) {
+  constexpr int kLeafWarps = kLeafThreads / 32;
   extern __shared__ __align__(16) unsigned char sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -520,8 +521,10 @@ __global__ void k_dense_ab(int n, const int64_t *__restrict__ rp, const int32_t 
 // host side
 // ---------------------------------------------------------------------------
 template <typename T>
-static void *kernel_ptr() {
-  return (void *)k_leaf<T>;
+static void *kernel_ptr(int nt) {
+  if (nt == 1024) return (void *)k_leaf<T, 1024>;
+  if (nt == 512) return (void *)k_leaf<T, 512>;
+  return (void *)k_leaf<T, 256>;
 }
 
 // The kernel attributes are process-wide state of the function: set them
@@ -529,25 +532,38 @@ static void *kernel_ptr() {
 // that handles set up concurrently (the server's slots) never lower the
 // limit under another handle's launch.
 template <typename T>
-static amg_status leaf_attrs(int device, int optin, bool *nonportable, int *max_dynamic) {
+static amg_status leaf_attrs(int device, int optin, int nt, bool *nonportable, int *max_dynamic) {
   static std::mutex mu;
-  static bool done[64], np_ok[64];
-  static int dyn[64];
+  static bool done[64][3], np_ok[64][3];
+  static int dyn[64][3];
   if (device < 0 || device >= 64) return fail(AMG_ERR_CUDA, "device index out of range");
+  const int v = nt == 1024 ? 2 : (nt == 512 ? 1 : 0);
   std::lock_guard<std::mutex> lk(mu);
-  if (!done[device]) {
-    void *kern = kernel_ptr<T>();
+  bool(&done_d)[3] = done[device];
+  bool(&np_d)[3] = np_ok[device];
+  int(&dyn_d)[3] = dyn[device];
+  if (!done_d[v]) {
+    void *kern = kernel_ptr<T>(nt);
     cudaFuncAttributes fa{};
     AMG_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
-    dyn[device] = optin - (int)fa.sharedSizeBytes;  // the kernel's static shared memory counts too
-    AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn[device]));
-    np_ok[device] = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
-    if (!np_ok[device]) cudaGetLastError();
-    done[device] = true;
+    dyn_d[v] = optin - (int)fa.sharedSizeBytes;  // the kernel's static shared memory counts too
+    AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_d[v]));
+    np_d[v] = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    if (!np_d[v]) cudaGetLastError();
+    done_d[v] = true;
   }
-  *nonportable = np_ok[device];
-  *max_dynamic = dyn[device];
+  *nonportable = np_d[v];
+  *max_dynamic = dyn_d[v];
   return AMG_OK;
+}
+
+// threads per CTA of the leaf kernel: AMG_GB300_LEAF_THREADS=256|512|1024
+static int leaf_threads() {
+  if (const char *e = getenv("AMG_GB300_LEAF_THREADS")) {
+    const int v = atoi(e);
+    if (v == 256 || v == 512 || v == 1024) return v;
+  }
+  return kLeafDefaultThreads;
 }
 
 template <typename T>
@@ -562,10 +578,11 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
   int optin = 0;
   AMG_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  void *kern = kernel_ptr<T>();
+  const int nt = leaf_threads();
+  void *kern = kernel_ptr<T>(nt);
   bool nonportable = false;
   int max_dynamic = 0;
-  AMG_TRY(leaf_attrs<T>(h->device, optin, &nonportable, &max_dynamic));
+  AMG_TRY(leaf_attrs<T>(h->device, optin, nt, &nonportable, &max_dynamic));
   for (int C : {kLeafMaxC, 8, 4, 2, 1}) {
     LeafParams<T> P{};
     P.n = n;
@@ -575,8 +592,9 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     P.RH = (nH + C - 1) / C;
     P.m = h->opt.degree;
     P.nu = h->opt.inner_iters;
+    P.nt = nt;
     int tpr = 8;
-    while (tpr > 1 && P.R * tpr > kLeafThreads) tpr >>= 1;
+    while (tpr > 1 && P.R * tpr > nt) tpr >>= 1;
     // AMG_GB300_LEAF_TPR=1|2|4|8 overrides the lanes per row on level k0
     if (const char *e = getenv("AMG_GB300_LEAF_TPR")) {
       const int v = atoi(e);
@@ -594,7 +612,7 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(kLeafThreads);
+    cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = P.smem;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = C;
@@ -660,7 +678,7 @@ static amg_status launch_t(amg_handle_s *h) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   cfg.gridDim = dim3(P.C);
-  cfg.blockDim = dim3(kLeafThreads);
+  cfg.blockDim = dim3(P.nt);
   cfg.dynamicSmemBytes = P.smem;
   cfg.stream = h->stream;
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -669,7 +687,10 @@ static amg_status launch_t(amg_handle_s *h) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_leaf<T>, P);
+  cudaError_t e;
+  if (P.nt == 1024) e = cudaLaunchKernelEx(&cfg, k_leaf<T, 1024>, P);
+  else if (P.nt == 512) e = cudaLaunchKernelEx(&cfg, k_leaf<T, 512>, P);
+  else e = cudaLaunchKernelEx(&cfg, k_leaf<T, 256>, P);
   ++h->launches;
   if (e != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("leaf kernel launch: ") + cudaGetErrorString(e));
   return AMG_OK;

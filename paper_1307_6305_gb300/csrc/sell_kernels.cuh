@@ -20,8 +20,13 @@ __device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict_
   const int w = (int)((A.sptr[s + 1] - base) >> 5);
   const int32_t *__restrict__ c = A.scol + base + lane;
   const T *__restrict__ v = A.val + base + lane;
+  if (A.stream) {  // uniform over the launch
 #pragma unroll 4
-  for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[c[k * kSlice]], acc);
+    for (int k = 0; k < w; ++k) acc = fma(__ldcs(v + k * kSlice), x[__ldcs(c + k * kSlice)], acc);
+  } else {
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[c[k * kSlice]], acc);
+  }
   return acc;
 }
 

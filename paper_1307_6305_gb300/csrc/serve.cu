@@ -1,20 +1,26 @@
 // serve.cu -- a continuous-batching solve server.
 //
 // Requests (a registered graph + one right-hand side) arrive at any time.
-// `max_active` worker threads (slots) take requests from a FIFO queue as soon
-// as a slot and device memory are free: a request whose graph's hierarchy is
-// resident starts at once; otherwise the hierarchy is set up first, after
-// evicting least-recently-used idle hierarchies until the estimated bytes fit
-// under the memory cap.  Hierarchies stay resident between requests.  Every
-// resident graph owns a CUDA stream, so solves of different graphs overlap
-// on the device; requests for one graph take turns on its hierarchy (a
-// handle is not shared by two solves at once).  All kernels are
-// deterministic, so a request's result does not depend on what else runs.
+// `max_active` worker threads (slots) take work from a FIFO queue as soon as
+// a slot and device memory are free.  A worker takes the oldest request whose
+// graph is idle together with every other queued request for that graph with
+// the same tolerance, up to `batch_max`, and solves them as one
+// multi-right-hand-side solve on the graph's resident hierarchy: requests
+// that arrived while the graph was busy share the next sweep over its levels
+// instead of taking turns.  A graph without a resident hierarchy is set up
+// first, after evicting least-recently-used idle hierarchies until its bytes
+// fit under the memory cap.  Every resident graph owns a CUDA stream, so
+// solves of different graphs overlap on the device.  With batch_max >= 2 every
+// solve -- one request or many -- runs the block kernels at the same fixed
+// width, so a request's result does not depend on what else is in its block
+// or on the device; with batch_max <= 1 requests for one graph take turns on
+// the single-right-hand-side path.
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -67,6 +73,7 @@ size_t reserve_bytes(const GraphEntry &g) {
 
 struct amg_server_s {
   amg_server_config cfg{};
+  int width = 0;                             // block width of batched solves (0: no batching)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::map<int64_t, GraphEntry> graphs;
@@ -77,6 +84,7 @@ struct amg_server_s {
   size_t resident_bytes = 0, peak_bytes = 0;
   int active = 0, peak_active = 0;
   int64_t setups = 0, evictions = 0, completed = 0;
+  int64_t solves = 0, setup_retries = 0;     // solve calls (a batch is one); setups redone to stay under the cap
   bool stop = false;
   int device = 0;
 };
@@ -101,17 +109,33 @@ bool make_room(amg_server_s *s, size_t need) {
   return true;
 }
 
+// finish every request of a batch (under the lock)
+void complete(amg_server_s *s, Request *const *rs, int nr, amg_status st, const std::string &err) {
+  const Clock::time_point now = Clock::now();
+  for (int c = 0; c < nr; ++c) {
+    Request *r = rs[c];
+    if (r->status == AMG_OK) r->status = st;
+    if (r->err.empty()) r->err = err;
+    r->finished = now;
+    r->done = true;
+  }
+  s->completed += nr;
+}
+
 void worker(amg_server_s *s) {
   cudaSetDevice(s->device);
+  const int bmax = std::max(1, std::min(s->cfg.batch_max, amg::kMaxBatchServe));
   for (;;) {
-    int64_t ticket = 0;
+    std::vector<int64_t> batch;
     GraphEntry *g = nullptr;
     bool need_setup = false;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       for (;;) {
         if (s->stop) return;
-        // first queued request whose graph is idle and fits
+        // the oldest queued request whose graph is idle and fits ...
+        int64_t gid = 0;
+        double tol = 0.0;
         for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
           Request &r = s->requests[*it];
           GraphEntry &ge = s->graphs[r.graph];
@@ -127,42 +151,76 @@ void worker(amg_server_s *s) {
           }
           ge.busy = true;
           ge.last_used = ++s->clock;
-          ticket = *it;
           g = &ge;
-          s->queue.erase(it);
+          gid = r.graph;
+          tol = r.tol;
           break;
         }
-        if (ticket) break;
+        if (g) {
+          // ... with the other queued requests of its graph and tolerance
+          for (auto it = s->queue.begin(); it != s->queue.end() && (int)batch.size() < bmax;) {
+            const Request &r = s->requests[*it];
+            if (r.graph == gid && r.tol == tol) {
+              batch.push_back(*it);
+              it = s->queue.erase(it);
+            } else {
+              ++it;
+            }
+          }
+          break;
+        }
         s->cv_work.wait(lk);
       }
       ++s->active;
       s->peak_active = std::max(s->peak_active, s->active);
     }
-    Request *r;
+    const int nr = (int)batch.size();
+    std::vector<Request *> rs(nr);
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      r = &s->requests[ticket];
+      for (int c = 0; c < nr; ++c) rs[c] = &s->requests[batch[c]];
     }
     amg_status st = AMG_OK;
     std::string err;
+    bool retry = false;
     if (need_setup) {
       if (!g->stream) cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
       amg_handle h = nullptr;
       st = amg_setup(g->n, g->rowptr.data(), g->col.data(), g->w.data(), g->has_d ? g->d.data() : nullptr,
                      &s->cfg.opt, AMG_MEM_HOST, g->stream, &h);
       if (st != AMG_OK) err = amg_last_error(nullptr);
+      // the block buffers and the captured block preconditioner are part of
+      // the hierarchy's size: made now, before it is measured
+      if (st == AMG_OK && s->width > 0) {
+        st = amg::prepare_batched(h, s->width);
+        if (st == AMG_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = amg::fail(AMG_ERR_CUDA, "setup");
+        if (st != AMG_OK) {
+          err = amg::thread_error();
+          amg_free(h);
+          h = nullptr;
+        }
+      }
       std::lock_guard<std::mutex> lk(s->mu);
-      s->resident_bytes -= g->bytes;
+      s->resident_bytes -= g->bytes;  // the reservation
       if (st == AMG_OK) {
         g->measured = h->arena.bytes;
         ++s->setups;
         if (g->measured > s->cfg.mem_cap_bytes) {
-          // this hierarchy alone exceeds the cap: the request fails
+          // this hierarchy alone exceeds the cap: the requests fail
           amg_free(h);
           g->bytes = 0;
           st = AMG_ERR_OOM;
           err = "the hierarchy needs " + std::to_string(g->measured) + " device bytes, more than mem_cap_bytes = " +
                 std::to_string(s->cfg.mem_cap_bytes);
+        } else if (!make_room(s, g->measured)) {
+          // larger than its reservation and the difference cannot be freed
+          // now (the other resident hierarchies are busy): give the memory
+          // back and queue the requests again at the front; the next attempt
+          // reserves the measured size
+          amg_free(h);
+          g->bytes = 0;
+          retry = true;
+          ++s->setup_retries;
         } else {
           g->h = h;
           g->bytes = g->measured;
@@ -173,22 +231,63 @@ void worker(amg_server_s *s) {
         g->bytes = 0;
       }
     }
+    if (retry) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (int c = nr - 1; c >= 0; --c) s->queue.push_front(batch[c]);
+      g->busy = false;
+      --s->active;
+      s->cv_work.notify_all();
+      continue;
+    }
     if (st == AMG_OK) {
-      r->x.assign((size_t)g->n, 0.0);
-      memset(&r->info, 0, sizeof(r->info));
-      st = amg_solve(g->h, r->rhs.data(), r->x.data(), 1, g->n, r->tol, &r->info);
-      if (st != AMG_OK) err = amg_last_error(g->h);
+      for (Request *r : rs) {
+        r->x.assign((size_t)g->n, 0.0);
+        memset(&r->info, 0, sizeof(r->info));
+      }
+      const auto t0 = Clock::now();
+      if (s->width == 0) {
+        // no batching: one request per solve on the single-right-hand-side path
+        st = amg_solve(g->h, rs[0]->rhs.data(), rs[0]->x.data(), 1, g->n, rs[0]->tol, &rs[0]->info);
+        if (st != AMG_OK) err = amg_last_error(g->h);
+      } else {
+        std::vector<const double *> bp(nr);
+        std::vector<double *> xp(nr);
+        std::vector<amg::ColumnReport> cols(nr);
+        for (int c = 0; c < nr; ++c) {
+          bp[c] = rs[c]->rhs.data();
+          xp[c] = rs[c]->x.data();
+        }
+        st = amg::solve_host_columns(g->h, bp.data(), xp.data(), nr, rs[0]->tol, s->width, cols.data());
+        if (st != AMG_OK) err = amg::thread_error();
+        const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+        for (int c = 0; c < nr && st == AMG_OK; ++c) {
+          amg_info &inf = rs[c]->info;
+          inf.iterations = cols[c].iterations;
+          inf.converged = cols[c].converged ? 1 : 0;
+          inf.rel_residual = cols[c].rel_residual;
+          inf.true_rel_residual = cols[c].true_rel_residual;
+          inf.n_levels = g->h->L;
+          inf.grid_complexity = g->h->grid_complexity;
+          inf.op_complexity = g->h->op_complexity;
+          inf.setup_ms = g->h->setup_ms;
+          inf.solve_ms = ms;
+          if (cols[c].breakdown) {
+            rs[c]->status = AMG_ERR_BREAKDOWN;
+            rs[c]->err = "flexible CG breakdown";
+          } else if (!cols[c].converged) {
+            rs[c]->status = AMG_ERR_NOT_CONVERGED;
+            rs[c]->err = "max_iters reached before tol";
+          }
+        }
+      }
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      r->status = st;
-      r->err = err;
-      r->finished = Clock::now();
-      r->done = true;
+      ++s->solves;
+      complete(s, rs.data(), nr, st, err);
       g->busy = false;
       g->last_used = ++s->clock;
       --s->active;
-      ++s->completed;
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
@@ -206,6 +305,8 @@ amg_status amg_server_create(const amg_server_config *cfg, amg_server *out) {
   *out = nullptr;
   if (cfg->max_active < 1 || cfg->max_active > 64 || cfg->mem_cap_bytes < ((size_t)1 << 20))
     return fail(AMG_ERR_INVALID_ARG, "max_active must be in [1, 64] and mem_cap_bytes >= 1 MiB");
+  if (cfg->batch_max < 0 || cfg->batch_max > amg::kMaxBatchServe)
+    return fail(AMG_ERR_INVALID_ARG, "batch_max must be in [0, 32]");
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
     cudaGetLastError();
@@ -213,6 +314,10 @@ amg_status amg_server_create(const amg_server_config *cfg, amg_server *out) {
   }
   amg_server_s *s = new amg_server_s();
   s->cfg = *cfg;
+  if (cfg->batch_max >= 2) {  // block width: the smallest power of two >= batch_max
+    s->width = 1;
+    while (s->width < cfg->batch_max) s->width <<= 1;
+  }
   cudaGetDevice(&s->device);
   for (int i = 0; i < cfg->max_active; ++i) s->workers.emplace_back(worker, s);
   *out = s;
@@ -246,6 +351,12 @@ amg_status amg_server_submit(amg_server s, int64_t graph_id, const double *rhs, 
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->graphs.find(graph_id);
     if (it == s->graphs.end()) return fail(AMG_ERR_INVALID_ARG, "unknown graph id");
+    // refused here rather than in the solve, where it would fail the other
+    // requests sharing its block
+    double ss = 0.0;
+    for (int64_t i = 0; i < it->second.n; ++i) ss += rhs[i] * rhs[i];
+    if (!std::isfinite(ss))
+      return fail(AMG_ERR_INVALID_ARG, "right-hand side has a non-finite entry or a norm beyond the fp64 range");
     Request r;
     r.ticket = s->next_ticket++;
     r.graph = graph_id;
@@ -314,6 +425,8 @@ amg_status amg_server_stats(amg_server s, amg_server_stats_t *out) {
   out->completed = s->completed;
   out->setups = s->setups;
   out->evictions = s->evictions;
+  out->solves = s->solves;
+  out->setup_retries = s->setup_retries;
   return AMG_OK;
 }
 

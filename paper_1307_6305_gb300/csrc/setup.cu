@@ -109,16 +109,20 @@ static amg_status scan_rec(const T *in, T *out, int64_t n, cudaStream_t st, T *t
   return AMG_OK;
 }
 
+// exclusive scan; the total is read back (one stream synchronisation) only
+// when the caller asks for it
 template <typename T>
 static amg_status scan_total(const T *in, T *out, int64_t n, cudaStream_t st, int64_t *total_host) {
   T *tot = nullptr;
   AMG_TRY(pool_alloc((void **)&tot, sizeof(T), st));
   AMG_TRY(scan_rec<T>(in, out, n, st, tot));
-  T t = 0;
-  AMG_CUDA_TRY(cudaMemcpyAsync(&t, tot, sizeof(T), cudaMemcpyDeviceToHost, st));
-  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (total_host) {
+    T t = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&t, tot, sizeof(T), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    *total_host = (int64_t)t;
+  }
   pool_free(tot, st);
-  if (total_host) *total_host = (int64_t)t;
   return AMG_OK;
 }
 
@@ -130,6 +134,12 @@ amg_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaSt
                               int64_t *total_host) {
   return scan_total<int>(in, out, n, st, total_host);
 }
+
+// host checks of the iterative setup loops: connectivity rounds per batch,
+// matching rounds per batch (the first batch of a pass may be longer)
+constexpr int kCcBatch = 3;
+constexpr int kMatchBatch = 4;
+constexpr int kMatchMaxBatch = 16;
 
 // ---------------------------------------------------------------------------
 // validation
@@ -175,6 +185,7 @@ __global__ void k_check_symmetry(int n, const int64_t *__restrict__ rp, const in
   bool bad = false;
   for (int64_t p = rp[i]; p < rp[i + 1] && !bad; ++p) {
     const int j = col[p];
+    if (j < 0 || j >= n) continue;  // reported by k_check_entries (launched with this one)
     int64_t lo = rp[j], hi = rp[j + 1] - 1, hit = -1;
     while (lo <= hi) {
       int64_t mid = lo + (hi - lo) / 2;
@@ -365,35 +376,40 @@ __global__ void k_coarse_ids(int n, const int *__restrict__ mate, const int *__r
   }
 }
 
+// One handshake matching pass.  Rounds run in batches between host checks
+// (`first_batch` rounds, then kMatchBatch): a round after one that added no
+// pair is a device-side no-op (the matching is maximal), so the extra rounds
+// of the last batch change nothing.  Every matched pair is counted once by
+// each of its two vertices, so n_H = n - (sum of the counts) / 2 is known on
+// the host without another read-back.
 static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, const int32_t *col,
                              const double *s, uint64_t salt, int32_t *mate, int32_t *agg, int *m0,
-                             int *m1, int *nH_out, int *rounds_out, int64_t *launches) {
+                             int *m1, int *nH_out, int *rounds_out, int64_t *launches, int first_batch) {
   int *ptr = nullptr, *added = nullptr, *rep = nullptr, *id = nullptr;
+  const int maxb = std::max(kMatchBatch, std::min(first_batch, kMatchMaxBatch));
   AMG_TRY(pool_alloc((void **)&ptr, sizeof(int) * (size_t)std::max(n, 1), st));
-  AMG_TRY(pool_alloc((void **)&added, sizeof(int) * 8, st));
+  AMG_TRY(pool_alloc((void **)&added, sizeof(int) * (size_t)maxb, st));
   const unsigned nb = blocks_for(n, 256);
   k_match_init<<<nb, 256, 0, st>>>(n, mate);
   LAUNCH_CHECK(launches);
-  // Rounds are launched in batches between host checks; a round after one
-  // that added no pair is a device-side no-op (the matching is maximal), so
-  // the extra rounds of the last batch change nothing.
   int rounds = 0;
-  const int kBatch = 4;
-  int h_added[kBatch] = {0, 0, 0, 0};
-  for (;;) {
-    AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * kBatch, st));
-    for (int b = 0; b < kBatch; ++b) {
+  int64_t matched = 0;  // vertices matched so far (two per pair)
+  int h_added[kMatchMaxBatch];
+  for (int batch = maxb;; batch = kMatchBatch) {
+    AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * batch, st));
+    for (int b = 0; b < batch; ++b) {
       const int *prev = b ? added + b - 1 : nullptr;
       k_propose<<<nb, 256, 0, st>>>(n, rowptr, col, s, salt, mate, ptr, prev);
       LAUNCH_CHECK(launches);
       k_accept<<<nb, 256, 0, st>>>(n, ptr, mate, added + b, prev);
       LAUNCH_CHECK(launches);
     }
-    AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * kBatch, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
     bool done = false;
-    for (int b = 0; b < kBatch; ++b) {
+    for (int b = 0; b < batch; ++b) {
       ++rounds;
+      matched += h_added[b];
       if (h_added[b] == 0) { done = true; break; }
     }
     if (done) break;
@@ -404,8 +420,7 @@ static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, cons
   AMG_TRY(pool_alloc((void **)&id, sizeof(int) * (size_t)std::max(n, 1), st));
   k_rep_flags<<<nb, 256, 0, st>>>(n, mate, rep);
   LAUNCH_CHECK(launches);
-  int64_t nH = 0;
-  AMG_TRY(exclusive_scan_i32(rep, id, n, st, &nH));
+  AMG_TRY(exclusive_scan_i32(rep, id, n, st, nullptr));
   if (launches) *launches += 2;
   k_coarse_ids<<<nb, 256, 0, st>>>(n, mate, id, agg, m0, m1);
   LAUNCH_CHECK(launches);
@@ -413,7 +428,7 @@ static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, cons
   pool_free(added, st);
   pool_free(rep, st);
   pool_free(id, st);
-  if (nH_out) *nH_out = (int)nH;
+  if (nH_out) *nH_out = (int)(n - matched / 2);
   if (rounds_out) *rounds_out = rounds;
   return AMG_OK;
 }
@@ -422,7 +437,7 @@ amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32
                       const double *s, uint64_t salt, int32_t *mate, int32_t *agg, int *nH_out,
                       int *rounds_out, int64_t *launches) {
   return match_core(st, n, rowptr, col, s, salt, mate, agg, nullptr, nullptr, nH_out, rounds_out,
-                    launches);
+                    launches, kMatchBatch);
 }
 
 __global__ void k_widen(int n, const int *a, int64_t *b) {
@@ -1023,8 +1038,10 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   k_pair_seglen<<<nbH, 256, 0, st>>>(nH, cur.A.rowptr, mb, seglen);
   LAUNCH_CHECK(&h->launches);
   AMG_CUDA_TRY(cudaMemsetAsync(seglen + nH, 0, sizeof(int64_t), st));
-  int64_t segtot = 0;
-  AMG_TRY(exclusive_scan_i64(seglen, seg, nH + 1, st, &segtot));
+  // every fine row belongs to exactly one aggregate: the segments hold the
+  // fine level's entries, cur.A.nnz of them (or fewer when that is a bound)
+  const int64_t segtot = cur.A.nnz;
+  AMG_TRY(exclusive_scan_i64(seglen, seg, nH + 1, st, nullptr));
   int *keyJ = nullptr, *count = nullptr;
   double *kval = nullptr;
   AMG_TRY(pool_alloc((void **)&keyJ, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
@@ -1042,22 +1059,18 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
                                                      kval, count, longrows, huge, hugeoff);
   LAUNCH_CHECK(&h->launches);
   {
-    int nhuge = 0;
-    unsigned long long hugetot = 0;
-    AMG_CUDA_TRY(cudaMemcpyAsync(&nhuge, huge, sizeof(int), cudaMemcpyDeviceToHost, st));
-    AMG_CUDA_TRY(cudaMemcpyAsync(&hugetot, hugeoff, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    AMG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (nhuge > 0) {
-      int *skey = nullptr;
-      double *sval = nullptr;
-      AMG_TRY(pool_alloc((void **)&skey, sizeof(int) * (size_t)hugetot, st));
-      AMG_TRY(pool_alloc((void **)&sval, sizeof(double) * (size_t)hugetot, st));
-      k_gal_sort_huge<<<std::min(nhuge, 152), kRadixThreads, 0, st>>>(seg, keyJ, kval, count, huge, hugeoff, skey,
-                                                                       sval, bits_for(nH));
-      LAUNCH_CHECK(&h->launches);
-      pool_free(skey, st);
-      pool_free(sval, st);
-    }
+    // rows of more than kBlockSort entries, if any: their scratch is bounded
+    // by the segment total, and the kernel reads their count on the device
+    // (no host check; with none, every block returns at once)
+    int *skey = nullptr;
+    double *sval = nullptr;
+    AMG_TRY(pool_alloc((void **)&skey, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
+    AMG_TRY(pool_alloc((void **)&sval, sizeof(double) * (size_t)std::max<int64_t>(segtot, 1), st));
+    k_gal_sort_huge<<<std::max(1, std::min(nH, 152)), kRadixThreads, 0, st>>>(seg, keyJ, kval, count, huge, hugeoff,
+                                                                               skey, sval, bits_for(nH));
+    LAUNCH_CHECK(&h->launches);
+    pool_free(skey, st);
+    pool_free(sval, st);
   }
   pool_free(huge, st);
   pool_free(hugeoff, st);
@@ -1074,8 +1087,11 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   LAUNCH_CHECK(&h->launches);
   next.A.n = nH;
   AMG_TRY(pool_alloc((void **)&next.A.rowptr, sizeof(int64_t) * (size_t)(nH + 1), st));
-  int64_t nnzH = 0;
-  AMG_TRY(exclusive_scan_i64(cnt64, next.A.rowptr, nH + 1, st, &nnzH));
+  // the coarse rows hold at most the segments' entries: allocate for that
+  // bound (the exact count stays on the device, in rowptr[nH], until the
+  // level is complete)
+  const int64_t nnzH = segtot;
+  AMG_TRY(exclusive_scan_i64(cnt64, next.A.rowptr, nH + 1, st, nullptr));
   next.A.nnz = nnzH;
   AMG_TRY(pool_alloc((void **)&next.A.col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnzH, 1), st));
   AMG_TRY(pool_alloc((void **)&next.A.val, sizeof(double) * (size_t)std::max<int64_t>(nnzH, 1), st));
@@ -1109,8 +1125,12 @@ static amg_status coarsen_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuil
   AMG_TRY(pool_alloc((void **)&m0, sizeof(int) * (size_t)std::max(n, 1), st));
   AMG_TRY(pool_alloc((void **)&m1, sizeof(int) * (size_t)std::max(n, 1), st));
   int nH = 0, rounds = 0;
+  // passes of one hierarchy take similar numbers of rounds: the first batch
+  // covers the previous pass's count (one host check per pass, usually)
+  const int first_batch = h->match_rounds_hint > 0 ? h->match_rounds_hint + 1 : 8;
   AMG_TRY(match_core(st, n, cur.A.rowptr, cur.A.col, s, h->opt.hash_salt, mate, aggp, m0, m1, &nH,
-                     &rounds, &h->launches));
+                     &rounds, &h->launches, first_batch));
+  h->match_rounds_hint = rounds;
   pool_free(s, st);
   pool_free(mate, st);
   AMG_TRY(galerkin(h, cur, aggp, PairMembers{m0, m1}, nH, next));
@@ -1278,8 +1298,7 @@ static amg_status coarsen_mis_pass(amg_handle_s *h, const LevelBuild &cur, Level
   AMG_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)(nH + 1), st));
   k_agg_count<<<blocks_for(n, 256), 256, 0, st>>>(n, aggp, cnt);
   LAUNCH_CHECK(&h->launches);
-  int64_t tot = 0;
-  AMG_TRY(exclusive_scan_i32(cnt, ptr, nH + 1, st, &tot));
+  AMG_TRY(exclusive_scan_i32(cnt, ptr, nH + 1, st, nullptr));  // total: n
   k_agg_place<<<blocks_for(n, 256), 256, 0, st>>>(n, aggp, ptr, fill, mem);
   LAUNCH_CHECK(&h->launches);
   AMG_TRY(sort_members(h, n, nH, ptr, mem));
@@ -1322,36 +1341,53 @@ static amg_status persist_level(amg_handle_s *h, const LevelBuild &b, amg::Level
   return AMG_OK;
 }
 
-static amg_status build_sell(amg_handle_s *h, amg::Level &L, bool want32) {
+// SELL-32 layout of every level in two stages, so that one read-back serves
+// all levels: (1) slice widths and their scan (slice pointers) per level,
+// totals left on the device; (2) with the totals known, the padded arrays.
+static amg_status build_sell_all(amg_handle_s *h, bool want32) {
   cudaStream_t st = h->stream;
-  Sell &S = L.S;
-  S.n = L.n;
-  S.nslices = (L.n + kSlice - 1) / kSlice;
-  int64_t *slen = nullptr;
-  AMG_TRY(pool_alloc((void **)&slen, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(slen, 0, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
-  k_sell_width<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(L.n, S.nslices, L.A.rowptr, slen);
-  LAUNCH_CHECK(&h->launches);
-  AMG_TRY(alloc_persist(h, (void **)&S.sptr, sizeof(int64_t) * (size_t)(S.nslices + 1)));
-  int64_t stored = 0;
-  AMG_TRY(exclusive_scan_i64(slen, S.sptr, S.nslices + 1, st, &stored));
-  pool_free(slen, st);
-  S.stored = stored;
-  AMG_TRY(alloc_persist(h, (void **)&S.scol, sizeof(int32_t) * (size_t)std::max<int64_t>(stored, 1)));
-  AMG_TRY(alloc_persist(h, (void **)&S.val64, sizeof(double) * (size_t)std::max<int64_t>(stored, 1)));
-  k_sell_fill<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(L.n, S.nslices, L.A.rowptr, L.A.col,
-                                                                         L.A.val, S.sptr, S.scol, S.val64);
-  LAUNCH_CHECK(&h->launches);
-  S.diag64 = L.diag;
-  if (want32) {
-    AMG_TRY(alloc_persist(h, (void **)&S.val32, sizeof(float) * (size_t)std::max<int64_t>(stored, 1)));
-    AMG_TRY(alloc_persist(h, (void **)&S.diag32, sizeof(float) * (size_t)std::max(L.n, 1)));
-    if (stored) {
-      k_to_f32<<<blocks_for(stored, 256), 256, 0, st>>>(stored, S.val64, S.val32);
+  const int L = h->L;
+  int64_t *totals = nullptr;  // stored entries per level (device)
+  AMG_TRY(pool_alloc((void **)&totals, sizeof(int64_t) * (size_t)L, st));
+  for (int k = 0; k < L; ++k) {
+    amg::Level &V = h->lv[k];
+    Sell &S = V.S;
+    S.n = V.n;
+    S.nslices = (V.n + kSlice - 1) / kSlice;
+    int64_t *slen = nullptr;
+    AMG_TRY(pool_alloc((void **)&slen, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
+    AMG_CUDA_TRY(cudaMemsetAsync(slen, 0, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
+    k_sell_width<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(V.n, S.nslices, V.A.rowptr, slen);
+    LAUNCH_CHECK(&h->launches);
+    AMG_TRY(alloc_persist(h, (void **)&S.sptr, sizeof(int64_t) * (size_t)(S.nslices + 1)));
+    AMG_TRY(exclusive_scan_i64(slen, S.sptr, S.nslices + 1, st, nullptr));
+    AMG_CUDA_TRY(cudaMemcpyAsync(totals + k, S.sptr + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    pool_free(slen, st);
+  }
+  std::vector<int64_t> stored((size_t)L, 0);
+  AMG_CUDA_TRY(cudaMemcpyAsync(stored.data(), totals, sizeof(int64_t) * (size_t)L, cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  pool_free(totals, st);
+  for (int k = 0; k < L; ++k) {
+    amg::Level &V = h->lv[k];
+    Sell &S = V.S;
+    S.stored = stored[k];
+    AMG_TRY(alloc_persist(h, (void **)&S.scol, sizeof(int32_t) * (size_t)std::max<int64_t>(S.stored, 1)));
+    AMG_TRY(alloc_persist(h, (void **)&S.val64, sizeof(double) * (size_t)std::max<int64_t>(S.stored, 1)));
+    k_sell_fill<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(V.n, S.nslices, V.A.rowptr, V.A.col,
+                                                                           V.A.val, S.sptr, S.scol, S.val64);
+    LAUNCH_CHECK(&h->launches);
+    S.diag64 = V.diag;
+    if (want32) {
+      AMG_TRY(alloc_persist(h, (void **)&S.val32, sizeof(float) * (size_t)std::max<int64_t>(S.stored, 1)));
+      AMG_TRY(alloc_persist(h, (void **)&S.diag32, sizeof(float) * (size_t)std::max(V.n, 1)));
+      if (S.stored) {
+        k_to_f32<<<blocks_for(S.stored, 256), 256, 0, st>>>(S.stored, S.val64, S.val32);
+        LAUNCH_CHECK(&h->launches);
+      }
+      k_to_f32<<<blocks_for(V.n, 256), 256, 0, st>>>(V.n, V.diag, S.diag32);
       LAUNCH_CHECK(&h->launches);
     }
-    k_to_f32<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.diag, S.diag32);
-    LAUNCH_CHECK(&h->launches);
   }
   return AMG_OK;
 }
@@ -1367,8 +1403,7 @@ static amg_status build_agg_lists(amg_handle_s *h, amg::Level &L) {
   LAUNCH_CHECK(&h->launches);
   AMG_TRY(alloc_persist(h, (void **)&L.agg_ptr, sizeof(int) * (size_t)(L.nH + 1)));
   AMG_TRY(alloc_persist(h, (void **)&L.agg_mem, sizeof(int) * (size_t)std::max(L.n, 1)));
-  int64_t tot = 0;
-  AMG_TRY(exclusive_scan_i32(cnt, L.agg_ptr, L.nH + 1, st, &tot));
+  AMG_TRY(exclusive_scan_i32(cnt, L.agg_ptr, L.nH + 1, st, nullptr));  // total: L.n
   k_agg_place<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.agg, L.agg_ptr, fill, L.agg_mem);
   LAUNCH_CHECK(&h->launches);
   AMG_TRY(sort_members(h, L.n, L.nH, L.agg_ptr, L.agg_mem));
@@ -1390,7 +1425,9 @@ static amg_status build_coarsest(amg_handle_s *h) {
   k_trace<<<1, 32, 0, st>>>(n, C.diag, tr);
   LAUNCH_CHECK(&h->launches);
   double trace = 0.0;
+  std::vector<double> dg(n);
   AMG_CUDA_TRY(cudaMemcpyAsync(&trace, tr, sizeof(double), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaMemcpyAsync(dg.data(), C.diag, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
   const double alpha = h->pure ? trace / ((double)n * (double)n) : 0.0;
   const int64_t nn = (int64_t)n * n;
@@ -1405,12 +1442,7 @@ static amg_status build_coarsest(amg_handle_s *h) {
   k_dense<<<n, 128, 0, st>>>(n, C.A.rowptr, C.A.col, C.A.val, C.diag, alpha, M);
   LAUNCH_CHECK(&h->launches);
   double maxdiag = 0.0;
-  {
-    std::vector<double> dg(n);
-    AMG_CUDA_TRY(cudaMemcpyAsync(dg.data(), C.diag, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    AMG_CUDA_TRY(cudaStreamSynchronize(st));
-    for (double v : dg) maxdiag = std::max(maxdiag, v);
-  }
+  for (double v : dg) maxdiag = std::max(maxdiag, v);
   const double tiny = 1e-13 * std::max(maxdiag, 1e-300);
   double *a = M, *b = h->Z;
   for (int p = 0; p < n; ++p) {
@@ -1458,55 +1490,62 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
   if (hf & F_ROWPTR) return reject(AMG_ERR_INVALID_ARG, "row_ptr must start at 0 and be non-decreasing");
   if (nnz > 0 && (!col || !w)) return reject(AMG_ERR_INVALID_ARG, "col_idx and w must be non-NULL");
+  // with row_ptr valid, the entry checks, the symmetry check (which skips
+  // out-of-range columns) and the largest |d_i| run together; the flags are
+  // then reported in the documented order
+  unsigned long long *mx = nullptr;
+  if (d) {
+    AMG_TRY(pool_alloc((void **)&mx, sizeof(unsigned long long), st));
+    AMG_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+  }
   k_check_entries<<<nb, 256, 0, st>>>(n, rowptr, col, w, d, flags);
   LAUNCH_CHECK(&h->launches);
+  k_check_symmetry<<<nb, 256, 0, st>>>(n, rowptr, col, w, flags);
+  LAUNCH_CHECK(&h->launches);
+  if (d) {
+    k_max_abs<<<nb, 256, 0, st>>>(n, d, mx);
+    LAUNCH_CHECK(&h->launches);
+  }
+  unsigned long long hm = 0;
   AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  if (d) AMG_CUDA_TRY(cudaMemcpyAsync(&hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  pool_free(mx, st);
   if (hf & (F_RANGE | F_ORDER))
     return reject(AMG_ERR_INVALID_ARG, "column index out of range or row not strictly increasing");
   if (hf & F_SELF) return reject(AMG_ERR_SELF_LOOP, "graph has a self loop");
-  k_check_symmetry<<<nb, 256, 0, st>>>(n, rowptr, col, w, flags);
-  LAUNCH_CHECK(&h->launches);
-  AMG_CUDA_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  AMG_CUDA_TRY(cudaStreamSynchronize(st));
   if (hf & F_SYM) return reject(AMG_ERR_NOT_SYMMETRIC, "graph is not symmetric (pattern or weights)");
   if (hf & F_W) return reject(AMG_ERR_BAD_WEIGHT, "edge weights must be finite and > 0");
   if (hf & F_D) return reject(AMG_ERR_BAD_WEIGHT, "lower-order terms must be finite and >= 0");
   pool_free(flags, st);
   // pure Laplacian?  (d NULL or all zero)
-  h->pure = true;
-  if (d) {
-    unsigned long long *mx = nullptr;
-    AMG_TRY(pool_alloc((void **)&mx, sizeof(unsigned long long), st));
-    AMG_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
-    k_max_abs<<<nb, 256, 0, st>>>(n, d, mx);
-    LAUNCH_CHECK(&h->launches);
-    unsigned long long hm = 0;
-    AMG_CUDA_TRY(cudaMemcpyAsync(&hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, st));
-    AMG_CUDA_TRY(cudaStreamSynchronize(st));
-    pool_free(mx, st);
-    h->pure = (hm == 0ULL);
-  }
+  h->pure = !d || hm == 0ULL;
   phase.next("amg_setup: connectivity");
   // ---- connectivity ----
   {
     int *parent = nullptr, *changed = nullptr, *posd = nullptr, *cnt = nullptr;
     AMG_TRY(pool_alloc((void **)&parent, sizeof(int) * (size_t)n, st));
     AMG_TRY(pool_alloc((void **)&posd, sizeof(int) * (size_t)n, st));
-    AMG_TRY(pool_alloc((void **)&changed, sizeof(int), st));
+    AMG_TRY(pool_alloc((void **)&changed, sizeof(int) * kCcBatch, st));
     AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * 2, st));
     k_cc_init<<<nb, 256, 0, st>>>(n, parent);
     LAUNCH_CHECK(&h->launches);
-    for (int it = 0;; ++it) {
-      int hc = 0;
-      AMG_CUDA_TRY(cudaMemsetAsync(changed, 0, sizeof(int), st));
-      k_cc_hook<<<nb, 256, 0, st>>>(n, rowptr, col, parent, changed);
-      LAUNCH_CHECK(&h->launches);
-      k_cc_jump<<<nb, 256, 0, st>>>(n, parent);
-      LAUNCH_CHECK(&h->launches);
-      AMG_CUDA_TRY(cudaMemcpyAsync(&hc, changed, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // hook + jump rounds in batches between host checks: once a round hooks
+    // nothing the forest is final and later rounds of the batch change nothing
+    for (int it = 0;; it += kCcBatch) {
+      int hc[kCcBatch] = {};
+      AMG_CUDA_TRY(cudaMemsetAsync(changed, 0, sizeof(int) * kCcBatch, st));
+      for (int b = 0; b < kCcBatch; ++b) {
+        k_cc_hook<<<nb, 256, 0, st>>>(n, rowptr, col, parent, changed + b);
+        LAUNCH_CHECK(&h->launches);
+        k_cc_jump<<<nb, 256, 0, st>>>(n, parent);
+        LAUNCH_CHECK(&h->launches);
+      }
+      AMG_CUDA_TRY(cudaMemcpyAsync(hc, changed, sizeof(int) * kCcBatch, cudaMemcpyDeviceToHost, st));
       AMG_CUDA_TRY(cudaStreamSynchronize(st));
-      if (!hc) break;
+      bool done = false;
+      for (int b = 0; b < kCcBatch; ++b) done |= (hc[b] == 0);
+      if (done) break;
       if (it > 64 + n) return fail(AMG_ERR_CUDA, "connectivity check did not converge");
     }
     AMG_CUDA_TRY(cudaMemsetAsync(posd, 0, sizeof(int) * (size_t)n, st));
@@ -1593,6 +1632,14 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     AMG_CUDA_TRY(cudaMemcpyAsync(Lk.agg, comp, sizeof(int) * (size_t)nk, cudaMemcpyDeviceToDevice, st));
     pool_free(comp, st);
     AMG_TRY(build_agg_lists(h, h->lv[k]));
+    // the passes carried an upper bound of the entry count; the exact one is
+    // read once per level
+    {
+      int64_t nnz_exact = 0;
+      AMG_CUDA_TRY(cudaMemcpyAsync(&nnz_exact, cur.A.rowptr + cur.A.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      AMG_CUDA_TRY(cudaStreamSynchronize(st));
+      cur.A.nnz = nnz_exact;
+    }
     amg::Level nl;
     AMG_TRY(persist_level(h, cur, nl));
     free_build(cur, st);
@@ -1601,23 +1648,31 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   h->L = (int)h->lv.size();
   phase.next("amg_setup: smoother intervals and coefficients");
   // ---- smoother interval and polynomial per level (Sec. 3, Sec. 4) ----
-  unsigned long long *nrm = nullptr;
-  AMG_TRY(pool_alloc((void **)&nrm, sizeof(unsigned long long), st));
-  for (int k = 0; k + 1 < h->L; ++k) {
-    amg::Level &L = h->lv[k];
-    AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long), st));
-    k_norm_inf<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.A.rowptr, L.A.val, L.diag, nrm);
-    LAUNCH_CHECK(&h->launches);
-    unsigned long long bits = 0;
-    AMG_CUDA_TRY(cudaMemcpyAsync(&bits, nrm, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  {
+    // ||A_k||_inf of every smoothing level, then one read-back
+    const int nl = std::max(h->L - 1, 0);
+    unsigned long long *nrm = nullptr;
+    AMG_TRY(pool_alloc((void **)&nrm, sizeof(unsigned long long) * (size_t)std::max(nl, 1), st));
+    AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, sizeof(unsigned long long) * (size_t)std::max(nl, 1), st));
+    for (int k = 0; k < nl; ++k) {
+      amg::Level &L = h->lv[k];
+      k_norm_inf<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.A.rowptr, L.A.val, L.diag, nrm + k);
+      LAUNCH_CHECK(&h->launches);
+    }
+    std::vector<unsigned long long> bits((size_t)std::max(nl, 1), 0);
+    AMG_CUDA_TRY(cudaMemcpyAsync(bits.data(), nrm, sizeof(unsigned long long) * (size_t)std::max(nl, 1),
+                                 cudaMemcpyDeviceToHost, st));
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
-    double l1;
-    memcpy(&l1, &bits, sizeof(double));
-    L.lam1 = l1;
-    L.lam0 = h->opt.lambda0_ratio * l1;
-    closed_form_coefficients(h->opt.degree, L.lam0, L.lam1, L.coef);
+    pool_free(nrm, st);
+    for (int k = 0; k < nl; ++k) {
+      amg::Level &L = h->lv[k];
+      double l1;
+      memcpy(&l1, &bits[k], sizeof(double));
+      L.lam1 = l1;
+      L.lam0 = h->opt.lambda0_ratio * l1;
+      closed_form_coefficients(h->opt.degree, L.lam0, L.lam1, L.coef);
+    }
   }
-  pool_free(nrm, st);
   if (h->opt.cycle == AMG_CYCLE_AMLI) {
     // the AMLI polynomial: best approximation of degree nu-1 to 1/t on
     // [alpha, 1], divided by 1 + E (E its error bound) so that 0 < t q(t) <= 1
@@ -1633,7 +1688,7 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   phase.next("amg_setup: solve layouts and coarsest pseudo-inverse");
   // ---- solve layouts ----
   const bool want32 = h->opt.precision == AMG_PREC_FP32;
-  for (int k = 0; k < h->L; ++k) AMG_TRY(build_sell(h, h->lv[k], want32));
+  AMG_TRY(build_sell_all(h, want32));
   AMG_TRY(build_coarsest(h));
   // complexities (Sec. 4)
   double gs = 0, os = 0;

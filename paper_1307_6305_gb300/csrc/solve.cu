@@ -308,10 +308,18 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
   const int32_t *__restrict__ c = A.scol + base + lane;
   const T *__restrict__ v = A.val + base + lane;
   T acc = A.diag[i] * xi;
+  if (A.stream) {
 #pragma unroll 4
-  for (int k = 0; k < w; ++k) {
-    const int j = c[k * kSlice];
-    acc = fma(v[k * kSlice], u[j] + eH[agg[j]], acc);
+    for (int k = 0; k < w; ++k) {
+      const int j = __ldcs(c + k * kSlice);
+      acc = fma(__ldcs(v + k * kSlice), u[j] + eH[agg[j]], acc);
+    }
+  } else {
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const int j = c[k * kSlice];
+      acc = fma(v[k * kSlice], u[j] + eH[agg[j]], acc);
+    }
   }
   s[i] = r[i] - acc;
 }
@@ -434,22 +442,22 @@ template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
 SellView<double> view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream};
 }
 template <>
 SellView<float> view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream};
 }
 
 template <typename T>
 static SellView<T> smoother_view(const amg::Level &L);
 template <>
 SellView<double> smoother_view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64};
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64, L.stream};
 }
 template <>
 SellView<float> smoother_view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32};
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32, L.stream};
 }
 
 template <typename T>
@@ -597,6 +605,8 @@ static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s)
 // kernel, where the extra launch would cost more than it saves.  Both forms
 // compute each x_i and each row's sum in the same operations and order.
 constexpr int kProlongSplitRows = 1 << 17;
+// matrix bytes (stored values + columns) from which a level streams its matrix
+constexpr double kStreamMatrixBytes = 128.0 * (1 << 20);
 
 template <typename T>
 static amg_status prolong_residual(amg_handle_s *h, int k, const T *eH, const T *u, const T *r, T *x, T *s) {
@@ -887,10 +897,17 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   const bool split = !(split_env && split_env[0] == '0');
   int per_sm = 32;
   if (const char *e = getenv("AMG_GB300_WPS_WARPS")) per_sm = std::max(1, std::min(2048, atoi(e)));
+  // AMG_GB300_STREAM=0 reads every level's matrix with the default cache
+  // policy (A/B timing of the streaming loads)
+  const char *stream_env = getenv("AMG_GB300_STREAM");
+  const bool stream_ok = !(stream_env && stream_env[0] == '0');
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     const size_t n = (size_t)std::max(V.n, 1);
     V.wps = split ? choose_wps(V.n, per_sm) : 1;
+    // one pass over the level's stored values and columns is at least the
+    // size of L2: stream it (the vectors and the coarser levels stay cached)
+    V.stream = stream_ok && (double)V.S.stored * (double)(es + 4) >= kStreamMatrixBytes;
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1 && h->opt.degree > 0) {
       // the smoother form 2 t(A) of this level (Chebyshev kernels)

@@ -10,7 +10,9 @@ For hierarchies where the leaf engages (fewer launches per solve):
   * fp32 preconditioner: the same iteration count within 1, every solution
     meets the tolerance;
   * the degenerate settings the kernel branches on: degree 0 and 1, one and
-    three inner steps, a pure Laplacian (d = 0), an irregular random graph.
+    three inner steps, a pure Laplacian (d = 0), an irregular random graph;
+  * each of the CTA sizes the kernel is built for (256, 512 and 1024 threads,
+    AMG_GB300_LEAF_THREADS), whose row-to-lane assignment differs.
 """
 import numpy as np
 import pytest
@@ -33,8 +35,9 @@ def amg():
     return pkg
 
 
-def solve(amg, g, b, monkeypatch, leaf, converge=True, **opts):
+def solve(amg, g, b, monkeypatch, leaf, converge=True, nt=256, **opts):
     monkeypatch.setenv("AMG_GB300_LEAF", "1" if leaf else "0")
+    monkeypatch.setenv("AMG_GB300_LEAF_THREADS", str(nt))
     h = amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, **opts)
     assert h.status == 0, h.error
     x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
@@ -60,14 +63,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("nt", [256, 512, 1024])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_leaf_matches_multikernel_and_oracle(amg, orc, name, monkeypatch):
+def test_leaf_matches_multikernel_and_oracle(amg, orc, name, nt, monkeypatch):
     make, opts = CASES[name]
     g = make()
     b = gg.rhs(g.n, 31, gg.is_pure_laplacian(g))
     ref = orc.Hierarchy(g, **opts).solve(b, tol=1e-8)
     conv = ref.status == 0
-    x1, it1, h1, n1, L = solve(amg, g, b, monkeypatch, True, conv, **opts)
+    x1, it1, h1, n1, L = solve(amg, g, b, monkeypatch, True, conv, nt, **opts)
     x0, it0, h0, n0, _ = solve(amg, g, b, monkeypatch, False, conv, **opts)
     assert L >= 4, "hierarchy too shallow for the leaf level"
     assert n1 < n0, f"leaf kernel not used ({n1} vs {n0} launches)"
@@ -86,12 +90,13 @@ def test_leaf_matches_multikernel_and_oracle(amg, orc, name, monkeypatch):
     assert np.linalg.norm(b - A @ x1) <= 1e-7 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("nt", [256, 512, 1024])
 @pytest.mark.parametrize("name", ["grid3d_20", "grid3d_18_pure", "random_4000"])
-def test_leaf_fp32(amg, name, monkeypatch):
+def test_leaf_fp32(amg, name, nt, monkeypatch):
     make, opts = CASES[name]
     g = make()
     b = gg.rhs(g.n, 32, gg.is_pure_laplacian(g))
-    x1, it1, _, n1, _ = solve(amg, g, b, monkeypatch, True, precision=amg.AMG_PREC_FP32, **opts)
+    x1, it1, _, n1, _ = solve(amg, g, b, monkeypatch, True, nt=nt, precision=amg.AMG_PREC_FP32, **opts)
     x0, it0, _, n0, _ = solve(amg, g, b, monkeypatch, False, precision=amg.AMG_PREC_FP32, **opts)
     assert n1 < n0
     assert abs(it1 - it0) <= 1

@@ -2,13 +2,18 @@
 
 * A request's result is the same alone and in the mix: requests solved one at
   a time (one slot) and the same requests submitted together to four slots,
-  with graphs of uneven size in flight at once, give bit-identical solutions
-  (every kernel is deterministic).
+  with graphs of uneven size in flight at once, give bit-identical solutions.
+  With batching on (batch_max 8), the queued requests of one graph are solved
+  together (fewer solve calls than requests), and every solve -- one request
+  or a batch -- runs the block kernels at the same fixed width, so the
+  columns' arithmetic does not depend on their neighbours; with batching off
+  (batch_max 1) requests for one graph take turns on the single-vector path.
 * Slots overlap (peak active > 1) and every solution meets its tolerance.
 * Under a memory cap that holds only a few hierarchies, idle hierarchies are
-  evicted and re-built and every request still completes.
+  evicted and re-built, resident bytes stay under the cap and every request
+  still completes.
 * A hierarchy larger than the cap fails its request with AMG_ERR_OOM instead
-  of waiting forever.
+  of waiting forever; a non-finite right-hand side is refused at submission.
 """
 import numpy as np
 import pytest
@@ -44,8 +49,8 @@ def requests(graphs, per=3):
     return out
 
 
-def run(amg, graphs, reqs, max_active, cap=8 << 30, **opts):
-    srv = amg.Server(cap, max_active, degree=4, passes=3, **opts)
+def run(amg, graphs, reqs, max_active, cap=8 << 30, batch_max=8, **opts):
+    srv = amg.Server(cap, max_active, batch_max=batch_max, degree=4, passes=3, **opts)
     ids = [srv.add_graph(g) for g in graphs]
     if max_active == 1:
         res = []
@@ -59,14 +64,20 @@ def run(amg, graphs, reqs, max_active, cap=8 << 30, **opts):
     return res, stats
 
 
+@pytest.mark.parametrize("batch_max", [8, 1])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_same_result_alone_and_in_the_mix(amg, precision):
+def test_same_result_alone_and_in_the_mix(amg, precision, batch_max):
     graphs = pool()
     reqs = requests(graphs)
-    alone, _ = run(amg, graphs, reqs, 1, precision=precision)
-    mixed, stats = run(amg, graphs, reqs, 4, precision=precision)
+    alone, sa = run(amg, graphs, reqs, 1, batch_max=batch_max, precision=precision)
+    mixed, stats = run(amg, graphs, reqs, 4, batch_max=batch_max, precision=precision)
+    assert sa.solves == len(reqs)               # one at a time: no batches
     assert stats.peak_active > 1
     assert stats.completed == len(reqs)
+    if batch_max > 1:
+        assert stats.solves < len(reqs)         # same-graph requests shared a solve
+    else:
+        assert stats.solves == len(reqs)
     for (gi, b), (sa, xa, ia, _), (sm, xm, im, _) in zip(reqs, alone, mixed):
         assert sa == sm == amg.AMG_OK
         assert np.array_equal(xa, xm)
@@ -97,7 +108,7 @@ def test_memory_cap_evicts_idle_hierarchies(amg):
     assert cap < sum(sizes)          # not every hierarchy fits at once
     reqs = requests(graphs, per=2)
     res, stats = run(amg, graphs, reqs, 2, cap=cap)
-    assert stats.peak_resident_bytes <= cap
+    assert stats.peak_resident_bytes <= cap and stats.resident_bytes <= cap
     assert stats.evictions > 0 and stats.setups > len(graphs)
     for (gi, b), (st, x, info, lat) in zip(reqs, res):
         assert st == amg.AMG_OK
@@ -114,4 +125,20 @@ def test_hierarchy_larger_than_cap_fails_cleanly(amg):
     assert st == amg.AMG_ERR_OOM
     stats = srv.stats()
     assert stats.resident_bytes == 0 and stats.completed == 1
+    srv.close()
+
+
+def test_non_finite_rhs_is_refused_at_submission(amg):
+    g = gg.grid2d_5pt(40)
+    srv = amg.Server(1 << 30, 2, degree=4, passes=3)
+    gid = srv.add_graph(g)
+    b = gg.rhs(g.n, 3, True)
+    for bad in (np.nan, np.inf):
+        bb = b.copy()
+        bb[7] = bad
+        with pytest.raises(amg.AmgError) as e:
+            srv.submit(gid, bb)
+        assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    st, x, info, lat = srv.wait(srv.submit(gid, b))
+    assert st == amg.AMG_OK and info.rel_residual <= 1e-8
     srv.close()
