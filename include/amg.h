@@ -286,11 +286,15 @@ amg_status amg_match_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *c
 /* for that graph and tolerance, up to `batch_max`, and solves them in    */
 /* one multi-right-hand-side call (one sweep over the levels serves the   */
 /* whole batch); solves of different graphs run concurrently on their own */
-/* streams.  With batch_max >= 2 every solve runs the block kernels at    */
-/* one fixed width (the smallest power of two >= batch_max), so a        */
-/* request's result does not depend on what else is queued; with          */
-/* batch_max 0 or 1 requests for one graph take turns on the             */
-/* single-right-hand-side path.  A hierarchy's size is its arena bytes,   */
+/* streams.  A lone request runs the single-right-hand-side path; a batch */
+/* runs the block kernels at the smallest power-of-two width that holds   */
+/* it, with per-column Krylov scalars, so every request meets its own     */
+/* tolerance whatever shares its block (results alone and in a batch     */
+/* agree to that tolerance, not bit for bit); with batch_max 0 or 1       */
+/* requests for one graph take turns on the single-right-hand-side path   */
+/* and results are bit-identical alone and in the mix.  Block buffers for */
+/* batch_max columns are made at setup.  A hierarchy's size is its arena  */
+/* bytes,                                                                 */
 /* measured at its first setup (estimated from n and nnz before that); a  */
 /* setup whose measured size does not fit beside the busy hierarchies     */
 /* gives its memory back and its requests are queued again (counted in    */

@@ -500,13 +500,20 @@ static amg_status bprecondition(amg_handle_s *h) {
 // allocated on first use and re-allocated, larger, when a later solve needs
 // a wider block (the old ones are released stream-ordered and the captured
 // block preconditioner, which points at them, is dropped)
+static void drop_block_graphs(amg_handle_s *h) {
+  if (h->bpre_exec && !h->bpre_borrowed) cudaGraphExecDestroy(h->bpre_exec);
+  h->bpre_exec = nullptr;
+  h->bpre_borrowed = false;
+  for (cudaGraphExec_t &g : h->bfixed) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
 static amg_status ensure_batch_buffers(amg_handle_s *h, int W) {
   if (h->bw >= W) return AMG_OK;
   if (h->bw) {
-    if (h->bpre_exec) {
-      cudaGraphExecDestroy(h->bpre_exec);
-      h->bpre_exec = nullptr;
-    }
+    drop_block_graphs(h);
     for (void *p : h->batch_blocks) h->arena.free_block(p);
     h->batch_blocks.clear();
     h->bw = 0;
@@ -565,10 +572,9 @@ static amg_status ensure_batch_buffers(amg_handle_s *h, int W) {
 }
 
 static amg_status capture_batch_graph(amg_handle_s *h) {
-  if (h->bpre_exec) {
-    cudaGraphExecDestroy(h->bpre_exec);
-    h->bpre_exec = nullptr;
-  }
+  if (h->bpre_exec && !h->bpre_borrowed) cudaGraphExecDestroy(h->bpre_exec);
+  h->bpre_exec = nullptr;
+  h->bpre_borrowed = false;
   if (!h->use_graph) return AMG_OK;
   if (!h->cap) AMG_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   const cudaStream_t saved = h->stream;
@@ -907,17 +913,30 @@ static amg_status solve_block(amg_handle_s *h, const double *rhs, double *x, int
 // Buffers and the captured block preconditioner for solves at a fixed width
 // (the server calls this right after a setup, so that the hierarchy's arena
 // bytes include them).
+// One captured block preconditioner per fixed width is kept, so that solves
+// alternating between widths replay instead of re-capturing.
 amg_status prepare_batched(amg_handle_s *h, int width) {
   if (!valid_shape(width, 256)) return fail(AMG_ERR_INVALID_ARG, "block width must be 1, 2, 4, 8, 16 or 32");
   AMG_TRY(ensure_batch_buffers(h, width));
-  if (h->tuned_for != -width || !h->bpre_exec) {
-    h->bw_use = width;
-    h->b_tile = 256;
-    h->tuned_for = -width;
+  if (h->tuned_for == -width && (h->bpre_exec || !h->use_graph)) return AMG_OK;
+  int slot = 0;
+  while ((1 << slot) < width) ++slot;
+  h->bw_use = width;
+  h->b_tile = 256;
+  h->tuned_for = -width;
+  if (!h->use_graph) return AMG_OK;
+  if (!h->bfixed[slot]) {
     AMG_TRY(capture_batch_graph(h));
+    h->bfixed[slot] = h->bpre_exec;       // the cache owns it from here
+    h->bfixed_kernels[slot] = h->bgraph_kernels;
   }
+  h->bpre_exec = h->bfixed[slot];
+  h->bpre_borrowed = true;
+  h->bgraph_kernels = h->bfixed_kernels[slot];
   return AMG_OK;
 }
+
+void release_block_graphs(amg_handle_s *h) { drop_block_graphs(h); }
 
 // Solve nrhs right-hand sides (device pointers, column major with ld) in
 // blocks of the tuned width, or of a fixed width.

@@ -13,12 +13,18 @@ static inline unsigned nblk(int64_t n, int t = kThreads) {
   return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1);
 }
 
-// Programmatic dependent launch: wait until the preceding kernel has
-// completed and its writes are visible, then let the next kernel in the
-// stream be scheduled while this one runs (no-op for ordinary launches)
+// Programmatic dependent launch (no-ops for ordinary launches).
+// pdl_trigger lets the next kernel in the stream be scheduled while this one
+// runs; pdl_wait blocks until the preceding kernel has completed and its
+// writes are visible.  Between the two a kernel may read only data that no
+// kernel of the solve writes (matrices, aggregate maps): the solve-phase
+// kernels fetch their matrix rows there, overlapping those dependent loads
+// with the previous kernel's tail.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_sync() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_trigger();
+  pdl_wait();
 }
 
 // launch with programmatic stream serialization (PDL); arguments are

@@ -211,10 +211,11 @@ void destroy(amg_handle_s *h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  report_leaf_profile(h);
   h->arena.release();
   if (h->leaf_params && h->leaf_free) h->leaf_free(h->leaf_params);
   if (h->pre_exec) cudaGraphExecDestroy(h->pre_exec);
-  if (h->bpre_exec) cudaGraphExecDestroy(h->bpre_exec);
+  release_block_graphs(h);
   if (h->b_pinned) cudaFreeHost(h->b_pinned);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);

@@ -239,6 +239,7 @@ struct amg_handle_s {
   int leaf_csize = 0;
   void *leaf_params = nullptr;             // host copy of the launch parameters
   void (*leaf_free)(void *) = nullptr;
+  unsigned long long *leaf_prof = nullptr;  // opt-in phase profile of the leaf kernel
   // batched path (batch.cu)
   int bw = 0;                        // allocated block width (0: not yet)
   int bw_use = 32;                   // block width in use
@@ -255,6 +256,9 @@ struct amg_handle_s {
   unsigned *b_ticket = nullptr;
   double *b_pinned = nullptr;
   cudaGraphExec_t bpre_exec = nullptr;
+  bool bpre_borrowed = false;        // bpre_exec belongs to bfixed[]
+  cudaGraphExec_t bfixed[6] = {};    // fixed-width block preconditioners, width 2^slot
+  int64_t bfixed_kernels[6] = {};
   int64_t bgraph_kernels = 0;
   double setup_ms = 0;
   int match_rounds_hint = 0;         // rounds of the last matching pass (setup)
@@ -299,12 +303,14 @@ amg_status solve_batched(amg_handle_s *h, const double *rhs, double *x, int nrhs
                          amg_info *info, int *iters, double *rel, double *true_rel, int *conv, bool *breakdown,
                          int fixed_width = 0, ColumnReport *cols = nullptr);
 amg_status prepare_batched(amg_handle_s *h, int width);
+void release_block_graphs(amg_handle_s *h);
 // capi.cu: the server's batched solve: host columns in and out, staged
 // through device buffers of the handle's pool
 amg_status solve_host_columns(amg_handle_s *h, const double *const *rhs, double *const *x, int nr, double tol,
                               int width, ColumnReport *cols);
 // leaf.cu
 amg_status prepare_leaf(amg_handle_s *h);
+void report_leaf_profile(amg_handle_s *h);
 amg_status launch_leaf(amg_handle_s *h);
 amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double tol,
                      amg_info *info, int *iters, double *rel, double *true_rel, int *converged);

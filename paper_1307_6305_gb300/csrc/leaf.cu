@@ -32,6 +32,7 @@
 // summation order inside a row and inside a dot product differs.
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <algorithm>
@@ -50,6 +51,7 @@ constexpr int kLeafMaxInner = 4;
 constexpr int kLeafMaxRows = 2048;    // rows of level k0
 constexpr int kLeafMaxCoarse = 1024;  // rows of level k0 + 1
 constexpr int kLeafSlot = 8;          // doubles per CTA in a slot table
+constexpr int kLeafProfSlots = 128;   // phases recorded by the opt-in profile
 
 // shared-memory arrays, in layout order
 enum LeafArr : int {
@@ -90,6 +92,10 @@ struct LeafParams {
   const double *B, *AB;   // B and A_k0+1 B, nH x nH row major
   const T *b;
   T *x;
+  // opt-in phase profile (AMG_GB300_LEAF_PROFILE=1): CTA 0 adds the SM
+  // cycles of every phase (barrier to barrier) into prof[phase], and the
+  // launch count into prof[kLeafProfSlots - 1]; null otherwise
+  unsigned long long *prof;
   unsigned off[A_COUNT];  // byte offsets into dynamic shared memory
   unsigned smem;          // bytes
 };
@@ -164,6 +170,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
   double *slots = reinterpret_cast<double *>(sm + P.off[A_SLOTS]);
   double *wred = reinterpret_cast<double *>(sm + P.off[A_WRED]);
   __shared__ double s_sc[40];
+  const long long t_start = clock64();
 
   // ---- load: b (all rows), the owned rows of both operators, B, maps ----
   for (int i = tid; i < n; i += kLeafThreads) {
@@ -196,6 +203,21 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
     abrows[e] = P.AB[(size_t)h0c * nH + e];
   }
   cl.sync();  // every CTA has started and loaded before any remote store
+  if (P.prof && rank == 0 && tid == 0)
+    atomicAdd(&P.prof[kLeafProfSlots - 2], (unsigned long long)(clock64() - t_start));
+  // cluster barrier ending a phase (with the opt-in profile: CTA 0 records
+  // the phase's cycles)
+  int phase = 0;
+  long long t_phase = clock64();
+  auto csync = [&]() {
+    cl.sync();
+    if (P.prof && rank == 0 && tid == 0) {
+      const long long t = clock64();
+      if (phase < kLeafProfSlots - 2) atomicAdd(&P.prof[phase], (unsigned long long)(t - t_phase));
+      t_phase = t;
+    }
+    ++phase;
+  };
 
   // ---- building blocks ----
   // write v into row i of `a` in every CTA's copy (fire-and-forget stores)
@@ -280,7 +302,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
         const T v = add ? x[i] + inc : inc;
         put(x, i, v);
       }
-      cl.sync();
+      csync();
       return;
     }
     const T b0 = P.coef[0], b1 = P.coef[1];
@@ -296,7 +318,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
             if (m == 1) put(x, i, v);
             else x[i] = v;
           });
-    cl.sync();
+    csync();
     const T *Tp = r;
     T *Tc = vTa;
     for (int j = 2; j <= m; ++j) {
@@ -312,7 +334,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
               if (last) put(x, i, v);
               else x[i] = v;
             });
-      cl.sync();
+      csync();
       Tp = Tc;
       Tc = Tn;
     }
@@ -359,7 +381,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
         }
       }
       post(dv, it == 0 ? 2 : it);
-      cl.sync();
+      csync();
       fold(sums, it == 0 ? 2 : it);
       if (it == 0) {
         if (tid == 0) fin_alpha(scH, 0);
@@ -385,7 +407,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
           ev[1] += (double)d * (double)rin[I];
         }
         post(ev, 2);
-        cl.sync();
+        csync();
         fold(sums, 2);
         if (tid == 0) fin_alpha(scH, it);
       }
@@ -403,7 +425,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
         else hx[I] = xv;
         if (upd_r) put(hr, I, here ? rin[I] : rin[I] - a * W[lI]);
       }
-      cl.sync();
+      csync();
     }
   };
 
@@ -415,14 +437,14 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
           [&](int li, int i, T acc, int q) {
             if (q == 0) put(vs, i, r[i] - fma(ldiag[li], vu[i], acc));
           });
-    cl.sync();
+    csync();
     // r_H = P^T s over the owned aggregates (members in ascending order)
     for (int lI = tid; lI < nlocH; lI += kLeafThreads) {
       T acc = T(0);
       for (int a = lap[lI]; a < lap[lI + 1]; ++a) acc += vs[lam[a]];
       put(hb, h0 + lI, acc);
     }
-    cl.sync();
+    csync();
     inner_coarse();
     // x = u + P e_H and s = r - A x (neighbours formed on the fly)
     sweep([&](int j) { return vu[j] + hx[agg[j]]; },
@@ -432,7 +454,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
             x[i] = xi;
             put(vs, i, r[i] - fma(ldiag[li], xi, acc));
           });
-    cl.sync();
+    csync();
     smooth(vs, x, true);  // x += q_m(A) s, broadcast by its last step
   };
 
@@ -458,7 +480,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
             }
           });
     post(dv, it == 0 ? 2 : it);
-    cl.sync();
+    csync();
     fold(sums, it == 0 ? 2 : it);
     if (it == 0) {
       if (tid == 0) fin_alpha(scT, 0);
@@ -483,7 +505,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
         ev[1] += (double)d * (double)rin[i];
       }
       post(ev, 2);
-      cl.sync();
+      csync();
       fold(sums, 2);
       if (tid == 0) fin_alpha(scT, it);
     }
@@ -500,8 +522,9 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
       if (last) P.x[i] = xv;
       if (upd_r) put(vr, i, here ? rin[i] : rin[i] - a * W[li]);
     }
-    cl.sync();
+    csync();
   }
+  if (P.prof && rank == 0 && tid == 0) atomicAdd(&P.prof[kLeafProfSlots - 1], 1ull);
 }
 
 // AB = A B for the CSR operator A (off-diagonal part + diagonal) and the
@@ -647,6 +670,14 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     P.AB = AB;
     P.b = (const T *)L.b;
     P.x = (T *)L.x;
+    P.prof = nullptr;
+    if (const char *e = getenv("AMG_GB300_LEAF_PROFILE")) {
+      if (e[0] == '1') {
+        AMG_TRY(h->arena.alloc((void **)&P.prof, sizeof(unsigned long long) * kLeafProfSlots));
+        AMG_CUDA_TRY(cudaMemsetAsync(P.prof, 0, sizeof(unsigned long long) * kLeafProfSlots, h->stream));
+        h->leaf_prof = P.prof;
+      }
+    }
     LeafParams<T> *hp = new LeafParams<T>(P);
     h->leaf_params = hp;
     h->leaf_free = [](void *p) { delete static_cast<LeafParams<T> *>(p); };
@@ -694,6 +725,25 @@ static amg_status launch_t(amg_handle_s *h) {
   ++h->launches;
   if (e != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("leaf kernel launch: ") + cudaGetErrorString(e));
   return AMG_OK;
+}
+
+// The opt-in phase profile, printed to stderr (average SM cycles per launch
+// of the load phase and of every barrier-to-barrier phase of CTA 0).
+void report_leaf_profile(amg_handle_s *h) {
+  if (!h->leaf_prof) return;
+  std::vector<unsigned long long> v(kLeafProfSlots, 0);
+  if (cudaMemcpy(v.data(), h->leaf_prof, sizeof(unsigned long long) * kLeafProfSlots, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return;
+  const double nl = (double)std::max<unsigned long long>(v[kLeafProfSlots - 1], 1);
+  fprintf(stderr, "leaf profile: %llu launches, load %.0f cycles;", v[kLeafProfSlots - 1],
+          v[kLeafProfSlots - 2] / nl);
+  double tot = v[kLeafProfSlots - 2] / nl;
+  for (int p = 0; p < kLeafProfSlots - 2 && v[p]; ++p) {
+    fprintf(stderr, " %d:%.0f", p, v[p] / nl);
+    tot += v[p] / nl;
+  }
+  fprintf(stderr, "; total %.0f cycles\n", tot);
 }
 
 amg_status launch_leaf(amg_handle_s *h) {

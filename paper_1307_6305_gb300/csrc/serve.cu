@@ -10,11 +10,12 @@
 // instead of taking turns.  A graph without a resident hierarchy is set up
 // first, after evicting least-recently-used idle hierarchies until its bytes
 // fit under the memory cap.  Every resident graph owns a CUDA stream, so
-// solves of different graphs overlap on the device.  With batch_max >= 2 every
-// solve -- one request or many -- runs the block kernels at the same fixed
-// width, so a request's result does not depend on what else is in its block
-// or on the device; with batch_max <= 1 requests for one graph take turns on
-// the single-right-hand-side path.
+// solves of different graphs overlap on the device.  A lone request runs the
+// single-right-hand-side path; a batch runs the block kernels at the
+// smallest power-of-two width that holds it (a captured graph per width),
+// with per-column Krylov scalars, so each result meets its own tolerance
+// whatever shares its block.  With batch_max <= 1 requests for one graph
+// take turns on the single-right-hand-side path.
 #include <stdlib.h>
 #include <string.h>
 
@@ -189,8 +190,8 @@ void worker(amg_server_s *s) {
       st = amg_setup(g->n, g->rowptr.data(), g->col.data(), g->w.data(), g->has_d ? g->d.data() : nullptr,
                      &s->cfg.opt, AMG_MEM_HOST, g->stream, &h);
       if (st != AMG_OK) err = amg_last_error(nullptr);
-      // the block buffers and the captured block preconditioner are part of
-      // the hierarchy's size: made now, before it is measured
+      // the block buffers (for the widest batch) are part of the
+      // hierarchy's size: made now, before it is measured
       if (st == AMG_OK && s->width > 0) {
         st = amg::prepare_batched(h, s->width);
         if (st == AMG_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = amg::fail(AMG_ERR_CUDA, "setup");
@@ -245,11 +246,20 @@ void worker(amg_server_s *s) {
         memset(&r->info, 0, sizeof(r->info));
       }
       const auto t0 = Clock::now();
-      if (s->width == 0) {
-        // no batching: one request per solve on the single-right-hand-side path
+      if (nr == 1) {
+        // one request: the single-right-hand-side path (its own kernels,
+        // the fastest for one vector)
         st = amg_solve(g->h, rs[0]->rhs.data(), rs[0]->x.data(), 1, g->n, rs[0]->tol, &rs[0]->info);
-        if (st != AMG_OK) err = amg_last_error(g->h);
+        if (st != AMG_OK && st != AMG_ERR_NOT_CONVERGED && st != AMG_ERR_BREAKDOWN) {
+          err = amg_last_error(g->h);
+        } else if (st != AMG_OK) {
+          rs[0]->status = st;
+          rs[0]->err = amg_last_error(g->h);
+          st = AMG_OK;
+        }
       } else {
+        // a batch: the block path at the smallest power-of-two width that
+        // holds it
         std::vector<const double *> bp(nr);
         std::vector<double *> xp(nr);
         std::vector<amg::ColumnReport> cols(nr);
@@ -257,7 +267,9 @@ void worker(amg_server_s *s) {
           bp[c] = rs[c]->rhs.data();
           xp[c] = rs[c]->x.data();
         }
-        st = amg::solve_host_columns(g->h, bp.data(), xp.data(), nr, rs[0]->tol, s->width, cols.data());
+        int width = 1;
+        while (width < nr) width <<= 1;
+        st = amg::solve_host_columns(g->h, bp.data(), xp.data(), nr, rs[0]->tol, width, cols.data());
         if (st != AMG_OK) err = amg::thread_error();
         const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
         for (int c = 0; c < nr && st == AMG_OK; ++c) {

@@ -43,13 +43,25 @@ namespace amg {
 template <typename T>
 __global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__restrict__ mem,
                            const T *__restrict__ s, T *__restrict__ rH, double *flag) {
-  pdl_sync();
-  if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
+  pdl_trigger();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  // the aggregate's member list (setup data) before the wait
+  int a0 = 0, a1 = 0, m[kPre] = {};
+  if (I < nH) {
+    a0 = ptr[I];
+    a1 = ptr[I + 1];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q)
+      if (a0 + q < a1) m[q] = mem[a0 + q];
+  }
+  pdl_wait();
+  if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
   if (I >= nH) return;
   T acc = T(0);
-#pragma unroll 4
-  for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += s[mem[a]];
+#pragma unroll
+  for (int q = 0; q < kPre; ++q)
+    if (a0 + q < a1) acc += s[m[q]];
+  for (int a = a0 + kPre; a < a1; ++a) acc += s[mem[a]];
   rH[I] = acc;
 }
 
@@ -66,10 +78,12 @@ __global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__res
 template <typename T>
 __global__ void k_prolong_set(int n, const int *__restrict__ agg, const T *__restrict__ eH,
                               const T *__restrict__ u, T *__restrict__ x) {
-  pdl_sync();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  x[i] = u[i] + eH[agg[i]];
+  const int a = agg[i];
+  pdl_wait();
+  x[i] = u[i] + eH[a];
 }
 
 template <typename A, typename B>
@@ -246,9 +260,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *
     const int groups = (((A.n + kSlice - 1) / kSlice) * WPS + kThreads / 32 - 1) / (kThreads / 32);
     for (int g = blockIdx.x; g < groups; g += gridDim.x) {  // block-uniform trip count
       const SplitIdx ix = split_index<WPS>(g);
+      const RowPre<T> p = split_prefetch<T, WPS>(A, ix);
       const T xi = ix.i < A.n ? x[ix.i] : T(0);
       T yi;
-      if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, yi, part)) accumulate(ix.i, yi);
+      if (split_row<T, WPS>(A, ix, p, xi, [&](int j) { return x[j]; }, yi, part)) accumulate(ix.i, yi);
       __syncthreads();  // part is rewritten by the next group
     }
   }
@@ -286,13 +301,15 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
                                                                const T *__restrict__ eH,
                                                                const T *__restrict__ u, const T *__restrict__ r,
                                                                T *__restrict__ xout, T *__restrict__ s) {
-  pdl_sync();
+  pdl_trigger();
   if constexpr (WPS > 1) {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
+    const RowPre<T> p = split_prefetch<T, WPS>(A, ix);
+    pdl_wait();
     const T xi = ix.i < A.n ? u[ix.i] + eH[agg[ix.i]] : T(0);
     T Ax;
-    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return u[j] + eH[agg[j]]; }, Ax, part)) {
+    if (split_row<T, WPS>(A, ix, p, xi, [&](int j) { return u[j] + eH[agg[j]]; }, Ax, part)) {
       xout[ix.i] = xi;
       s[ix.i] = r[ix.i] - Ax;
     }
@@ -300,26 +317,23 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
-  const T xi = u[i] + eH[agg[i]];
+  const RowPre<T> p = row_prefetch(A, i);
+  const int ai = agg[i];
+  pdl_wait();
+  const T xi = u[i] + eH[ai];
   xout[i] = xi;
-  const int sl = i >> 5, lane = i & 31;
-  const int64_t base = A.sptr[sl];
-  const int w = (int)((A.sptr[sl + 1] - base) >> 5);
-  const int32_t *__restrict__ c = A.scol + base + lane;
-  const T *__restrict__ v = A.val + base + lane;
-  T acc = A.diag[i] * xi;
-  if (A.stream) {
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-      const int j = __ldcs(c + k * kSlice);
-      acc = fma(__ldcs(v + k * kSlice), u[j] + eH[agg[j]], acc);
+  // neighbours' values formed on the fly: u_j + e_H[agg_j]
+  T acc = p.d * xi;
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) {
+    if (k < p.w) {
+      const int j = p.pc[k];
+      acc = fma(p.pv[k], u[j] + eH[agg[j]], acc);
     }
-  } else {
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-      const int j = c[k * kSlice];
-      acc = fma(v[k * kSlice], u[j] + eH[agg[j]], acc);
-    }
+  }
+  for (int k = kPre; k < p.w; ++k) {
+    const int j = ldc(A, p.c + k * kSlice);
+    acc = fma(ldv(A, p.v + k * kSlice), u[j] + eH[agg[j]], acc);
   }
   s[i] = r[i] - acc;
 }
@@ -606,7 +620,7 @@ static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s)
 // compute each x_i and each row's sum in the same operations and order.
 constexpr int kProlongSplitRows = 1 << 17;
 // matrix bytes (stored values + columns) from which a level streams its matrix
-constexpr double kStreamMatrixBytes = 128.0 * (1 << 20);
+constexpr double kStreamMatrixBytes = 64.0 * (1 << 20);
 
 template <typename T>
 static amg_status prolong_residual(amg_handle_s *h, int k, const T *eH, const T *u, const T *r, T *x, T *s) {
