@@ -13,13 +13,11 @@ static inline unsigned nblk(int64_t n, int t = kThreads) {
   return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1);
 }
 
-// Programmatic dependent launch (no-ops for ordinary launches).
-// pdl_trigger lets the next kernel in the stream be scheduled while this one
-// runs; pdl_wait blocks until the preceding kernel has completed and its
-// writes are visible.  Between the two a kernel may read only data that no
-// kernel of the solve writes (matrices, aggregate maps): the solve-phase
-// kernels fetch their matrix rows there, overlapping those dependent loads
-// with the previous kernel's tail.
+// Programmatic dependent launch (no-ops for ordinary launches, the default;
+// AMG_GB300_PDL=1 launches the solve kernels with it).  pdl_trigger lets the
+// next kernel in the stream be scheduled while this one runs; pdl_wait
+// blocks until the preceding kernel has completed and its writes are
+// visible; every kernel calls both before touching memory.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_sync() {

@@ -69,6 +69,8 @@ enum LeafArr : int {
   A_LRP = A_HW0 + kLeafMaxInner, A_LCOL, A_LVAL, A_LDIAG, A_SVAL, A_SDIAG,
   // aggregate id of every row of level k0
   A_AGG,
+  // destination mask of every owned row (the CTAs that read it)
+  A_MASK,
   // member lists of the owned aggregates
   A_LAP, A_LAM,
   // owned rows of B and of A_k0+1 B (fp64, nH columns)
@@ -90,6 +92,9 @@ struct LeafParams {
   const double *val, *diag;
   const int32_t *agg, *agg_ptr, *agg_mem;
   const double *B, *AB;   // B and A_k0+1 B, nH x nH row major
+  // mask[i]: bit r set if CTA r reads row i of the level-k0 vectors (it owns
+  // i, a neighbour of i, or the aggregate of i); null: every CTA
+  const unsigned *mask;
   const T *b;
   T *x;
   // opt-in phase profile (AMG_GB300_LEAF_PROFILE=1): CTA 0 adds the SM
@@ -125,6 +130,8 @@ static unsigned leaf_layout(LeafParams<T> &P) {
   cnt[A_SDIAG] = P.R;
   cnt[A_AGG] = P.n;
   esz[A_AGG] = sizeof(int);
+  cnt[A_MASK] = P.R;
+  esz[A_MASK] = sizeof(unsigned);
   cnt[A_LAP] = P.RH + 1;
   esz[A_LAP] = sizeof(int);
   cnt[A_LAM] = P.maxmem;
@@ -192,6 +199,8 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
       sval[e] = (T)(P.two_sa * P.val[e0 + e]);
     }
   }
+  unsigned *lmask = reinterpret_cast<unsigned *>(sm + P.off[A_MASK]);
+  for (int li = tid; li < nloc; li += kLeafThreads) lmask[li] = P.mask ? P.mask[r0 + li] : (1u << C) - 1u;
   const int a0 = P.agg_ptr[h0c];
   for (int lI = tid; lI <= nlocH; lI += kLeafThreads) lap[lI] = P.agg_ptr[h0c + lI] - a0;
   {
@@ -220,9 +229,20 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
   };
 
   // ---- building blocks ----
-  // write v into row i of `a` in every CTA's copy (fire-and-forget stores)
+  // write v into row i of `a` in every CTA's copy (fire-and-forget stores):
+  // the coarse vectors, which the dense phases read in full
   auto put = [&](T *a, int i, T v) {
     for (int r = 0; r < C; ++r) *cl.map_shared_rank(a + i, (unsigned)r) = v;
+  };
+  // the same for an owned row i of a level-k0 vector, into the copies of the
+  // CTAs that read that row only
+  auto put0 = [&](T *a, int i, T v) {
+    unsigned mk = lmask[i - r0];
+    while (mk) {
+      const int r = __ffs(mk) - 1;
+      mk &= mk - 1u;
+      *cl.map_shared_rank(a + i, (unsigned)r) = v;
+    }
   };
   // sweep over the owned rows of A_k0: epi(local row, row, sum_j a_ij x_j, q).
   // The tpr lanes of a row share its entries; every lane gets the full sum,
@@ -300,7 +320,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
         const int i = r0 + li;
         const T inc = P.coef[0] * r[i];
         const T v = add ? x[i] + inc : inc;
-        put(x, i, v);
+        put0(x, i, v);
       }
       csync();
       return;
@@ -312,10 +332,10 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
             if (q != 0) return;
             const T ri = r[i];
             const T t1 = T(0.5) * fma(sdiag[li], ri, acc);
-            if (m > 1) put(vTa, i, t1);
+            if (m > 1) put0(vTa, i, t1);
             const T inc = fma(b1, t1, b0 * ri);
             const T v = add ? x[i] + inc : inc;
-            if (m == 1) put(x, i, v);
+            if (m == 1) put0(x, i, v);
             else x[i] = v;
           });
     csync();
@@ -330,8 +350,8 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
               if (q != 0) return;
               const T tn = fma(sdiag[li], Tc[i], acc) - Tp[i];  // Tp[i] read before Tn[i] (may alias) is written
               const T v = fma(bj, tn, x[i]);
-              if (!last) put(Tn, i, tn);
-              if (last) put(x, i, v);
+              if (!last) put0(Tn, i, tn);
+              if (last) put0(x, i, v);
               else x[i] = v;
             });
       csync();
@@ -435,7 +455,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
     // s = r - A u
     sweep([&](int j) { return vu[j]; },
           [&](int li, int i, T acc, int q) {
-            if (q == 0) put(vs, i, r[i] - fma(ldiag[li], vu[i], acc));
+            if (q == 0) put0(vs, i, r[i] - fma(ldiag[li], vu[i], acc));
           });
     csync();
     // r_H = P^T s over the owned aggregates (members in ascending order)
@@ -452,7 +472,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
             if (q != 0) return;
             const T xi = vu[i] + hx[agg[i]];
             x[i] = xi;
-            put(vs, i, r[i] - fma(ldiag[li], xi, acc));
+            put0(vs, i, r[i] - fma(ldiag[li], xi, acc));
           });
     csync();
     smooth(vs, x, true);  // x += q_m(A) s, broadcast by its last step
@@ -520,7 +540,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
       else xv = here ? xo[li] : fma(a, D[i], xo[li]);
       xo[li] = xv;
       if (last) P.x[i] = xv;
-      if (upd_r) put(vr, i, here ? rin[i] : rin[i] - a * W[li]);
+      if (upd_r) put0(vr, i, here ? rin[i] : rin[i] - a * W[li]);
     }
     csync();
   }
@@ -666,6 +686,27 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
                                                                     AB);
     AMG_CUDA_TRY(cudaGetLastError());
     ++h->launches;
+    // destination masks (AMG_GB300_LEAF_MASK=0: every row to every CTA)
+    P.mask = nullptr;
+    const char *menv = getenv("AMG_GB300_LEAF_MASK");
+    if (!(menv && menv[0] == '0')) {
+      std::vector<int32_t> col((size_t)std::max<int64_t>(rp[n], 1)), agg((size_t)n);
+      AMG_CUDA_TRY(cudaMemcpyAsync(col.data(), L.A.col, sizeof(int32_t) * (size_t)rp[n], cudaMemcpyDeviceToHost,
+                                   h->stream));
+      AMG_CUDA_TRY(cudaMemcpyAsync(agg.data(), L.agg, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+      AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+      std::vector<unsigned> mk((size_t)n, 0u);
+      for (int i = 0; i < n; ++i) {
+        unsigned v = (1u << (i / P.R)) | (1u << (agg[i] / P.RH));
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) v |= 1u << (col[e] / P.R);  // symmetric pattern
+        mk[i] = v;
+      }
+      unsigned *dmask = nullptr;
+      AMG_TRY(h->arena.alloc((void **)&dmask, sizeof(unsigned) * (size_t)n));
+      AMG_CUDA_TRY(cudaMemcpyAsync(dmask, mk.data(), sizeof(unsigned) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+      AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));  // mk is released on return
+      P.mask = dmask;
+    }
     P.B = h->Bd;
     P.AB = AB;
     P.b = (const T *)L.b;

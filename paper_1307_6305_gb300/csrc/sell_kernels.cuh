@@ -11,82 +11,76 @@
 namespace amg {
 
 // ---------------------------------------------------------------------------
-// SELL-32 row kernel: off-diagonal part of row `row` times x, in two parts:
-// row_prefetch reads the row's slice metadata, its diagonal and its first
-// kPre stored entries (matrix data only, so it may run before pdl_wait);
-// row_finish gathers x and accumulates in stored order (the same order and
-// operations as a single loop).
+// SELL-32 row kernel: off-diagonal part of row `row` times x
 // ---------------------------------------------------------------------------
-constexpr int kPre = 4;  // stored entries per thread fetched before pdl_wait
-
 template <typename T>
-struct RowPre {
-  int w = 0;                     // stored positions of the row (slice width)
-  const int32_t *c = nullptr;    // the row's first column index (stride kSlice)
-  const T *v = nullptr;
-  T d = T(0);                    // diagonal
-  int pc[kPre] = {};
-  T pv[kPre] = {};
-};
-
-template <typename T>
-__device__ __forceinline__ int ldc(const SellView<T> &A, const int32_t *p) {
-  return A.stream ? __ldcs(p) : *p;
-}
-template <typename T>
-__device__ __forceinline__ T ldv(const SellView<T> &A, const T *p) {
-  return A.stream ? __ldcs(p) : *p;
-}
-
-template <typename T>
-__device__ __forceinline__ RowPre<T> row_prefetch(const SellView<T> &A, int row) {
-  RowPre<T> p;
+__device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict__ x, int row, T acc) {
   const int s = row >> 5, lane = row & 31;
   const int64_t base = A.sptr[s];
-  p.w = (int)((A.sptr[s + 1] - base) >> 5);
-  p.c = A.scol + base + lane;
-  p.v = A.val + base + lane;
-  p.d = A.diag[row];
-#pragma unroll
-  for (int k = 0; k < kPre; ++k) {
-    if (k < p.w) {
-      p.pc[k] = ldc(A, p.c + k * kSlice);
-      p.pv[k] = ldv(A, p.v + k * kSlice);
-    }
-  }
-  return p;
-}
-
-template <typename T>
-__device__ __forceinline__ T row_finish(const SellView<T> &A, const RowPre<T> &p, const T *__restrict__ x, T acc) {
-#pragma unroll
-  for (int k = 0; k < kPre; ++k)
-    if (k < p.w) acc = fma(p.pv[k], x[p.pc[k]], acc);
+  const int w = (int)((A.sptr[s + 1] - base) >> 5);
+  const int32_t *__restrict__ c = A.scol + base + lane;
+  const T *__restrict__ v = A.val + base + lane;
   if (A.stream) {  // uniform over the launch
 #pragma unroll 4
-    for (int k = kPre; k < p.w; ++k) acc = fma(__ldcs(p.v + k * kSlice), x[__ldcs(p.c + k * kSlice)], acc);
+    for (int k = 0; k < w; ++k) acc = fma(__ldcs(v + k * kSlice), x[__ldcs(c + k * kSlice)], acc);
   } else {
 #pragma unroll 4
-    for (int k = kPre; k < p.w; ++k) acc = fma(p.v[k * kSlice], x[p.c[k * kSlice]], acc);
+    for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[c[k * kSlice]], acc);
   }
   return acc;
 }
 
-// diag_i x_i + sum_j a_ij x_j
-template <typename T>
-__device__ __forceinline__ T row_apply(const SellView<T> &A, const RowPre<T> &p, const T *__restrict__ x, int row) {
-  return row_finish(A, p, x, p.d * x[row]);
-}
-
-template <typename T>
-__device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict__ x, int row, T acc) {
-  return row_finish(A, row_prefetch(A, row), x, acc);
-}
-
 template <typename T>
 __device__ __forceinline__ T apply_row(const SellView<T> &A, const T *__restrict__ x, int row) {
-  const RowPre<T> p = row_prefetch(A, row);
-  return row_finish(A, p, x, p.d * x[row]);
+  return sell_row(A, x, row, A.diag[row] * x[row]);
+}
+
+// Two rows per thread (large levels): rows r0 and r1 of different slices
+// (the same lane of consecutive 256-row tiles) run as two interleaved load
+// chains in one loop, so each thread keeps twice the loads in flight.  Each
+// row's sum is taken in the order of apply_row.  r1 < 0: no second row.
+template <typename T>
+__device__ __forceinline__ void apply_rows2(const SellView<T> &A, const T *__restrict__ x, int r0, int r1, T &y0,
+                                            T &y1) {
+  const int s0 = r0 >> 5, s1 = r1 >> 5, lane = r0 & 31;
+  const int64_t b0 = A.sptr[s0];
+  const int w0 = (int)((A.sptr[s0 + 1] - b0) >> 5);
+  int64_t b1 = 0;
+  int w1 = 0;
+  if (r1 >= 0) {
+    b1 = A.sptr[s1];
+    w1 = (int)((A.sptr[s1 + 1] - b1) >> 5);
+  }
+  const int32_t *__restrict__ c0 = A.scol + b0 + lane;
+  const T *__restrict__ v0 = A.val + b0 + lane;
+  const int32_t *__restrict__ c1 = A.scol + b1 + lane;
+  const T *__restrict__ v1 = A.val + b1 + lane;
+  T a0 = A.diag[r0] * x[r0];
+  T a1 = r1 >= 0 ? A.diag[r1] * x[r1] : T(0);
+  const int wm = max(w0, w1);
+  if (A.stream) {
+#pragma unroll 4
+    for (int k = 0; k < wm; ++k) {
+      if (k < w0) a0 = fma(__ldcs(v0 + k * kSlice), x[__ldcs(c0 + k * kSlice)], a0);
+      if (k < w1) a1 = fma(__ldcs(v1 + k * kSlice), x[__ldcs(c1 + k * kSlice)], a1);
+    }
+  } else {
+#pragma unroll 4
+    for (int k = 0; k < wm; ++k) {
+      if (k < w0) a0 = fma(v0[k * kSlice], x[c0[k * kSlice]], a0);
+      if (k < w1) a1 = fma(v1[k * kSlice], x[c1[k * kSlice]], a1);
+    }
+  }
+  y0 = a0;
+  y1 = a1;
+}
+
+// the rows of thread threadIdx.x in block blockIdx.x of a two-rows-per-thread
+// launch: r0 in even 256-row tiles, r1 in the odd tile after it (-1 if past n)
+__device__ __forceinline__ void rows2(int n, int &r0, int &r1) {
+  r0 = (2 * blockIdx.x) * blockDim.x + threadIdx.x;
+  r1 = r0 + blockDim.x;
+  if (r1 >= n) r1 = -1;
 }
 
 // Split rows for small levels.  With one thread per row, a row of w stored
@@ -113,39 +107,16 @@ __device__ __forceinline__ SplitIdx split_index(int group) {
   return ix;
 }
 
-// warp q's first kPre positions (q, q + WPS, ...) and the diagonal
-template <typename T, int WPS>
-__device__ __forceinline__ RowPre<T> split_prefetch(const SellView<T> &A, const SplitIdx &ix) {
-  RowPre<T> p;
-  if (ix.i < A.n) {
-    const int64_t base = A.sptr[ix.s];
-    p.w = (int)((A.sptr[ix.s + 1] - base) >> 5);
-    p.c = A.scol + base + ix.lane;
-    p.v = A.val + base + ix.lane;
-    if (ix.q == 0) p.d = A.diag[ix.i];
-#pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      const int pos = ix.q + k * WPS;
-      if (pos < p.w) {
-        p.pc[k] = ldc(A, p.c + pos * kSlice);
-        p.pv[k] = ldv(A, p.v + pos * kSlice);
-      }
-    }
-  }
-  return p;
-}
-
 // warp q's share of row ix.i's sum, accumulated onto acc; xf(j) gives x_j
 template <typename T, int WPS, typename XF>
-__device__ __forceinline__ T split_partial(const SellView<T> &A, const SplitIdx &ix, const RowPre<T> &p, T acc,
-                                           XF xf) {
+__device__ __forceinline__ T split_partial(const SellView<T> &A, const SplitIdx &ix, T acc, XF xf) {
   if (ix.i < A.n) {
-#pragma unroll
-    for (int k = 0; k < kPre; ++k)
-      if (ix.q + k * WPS < p.w) acc = fma(p.pv[k], xf(p.pc[k]), acc);
+    const int64_t base = A.sptr[ix.s];
+    const int w = (int)((A.sptr[ix.s + 1] - base) >> 5);
+    const int32_t *__restrict__ c = A.scol + base + ix.lane;
+    const T *__restrict__ v = A.val + base + ix.lane;
 #pragma unroll 2
-    for (int pos = ix.q + kPre * WPS; pos < p.w; pos += WPS)
-      acc = fma(ldv(A, p.v + pos * kSlice), xf(ldc(A, p.c + pos * kSlice)), acc);
+    for (int k = ix.q; k < w; k += WPS) acc = fma(v[k * kSlice], xf(c[k * kSlice]), acc);
   }
   return acc;
 }
@@ -168,10 +139,10 @@ __device__ __forceinline__ bool split_combine(T &acc, T (*part)[32]) {
 // row sum (diag_i x_i + sum_j a_ij x_j) of the split layout; valid in lead
 // threads whose row exists (returned flag)
 template <typename T, int WPS, typename XF>
-__device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &ix, const RowPre<T> &p, T xi,
-                                          XF xf, T &out, T (*part)[32]) {
-  T acc = (ix.q == 0 && ix.i < A.n) ? p.d * xi : T(0);
-  acc = split_partial<T, WPS>(A, ix, p, acc, xf);
+__device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &ix, T xi, XF xf, T &out,
+                                          T (*part)[32]) {
+  T acc = (ix.q == 0 && ix.i < A.n) ? A.diag[ix.i] * xi : T(0);
+  acc = split_partial<T, WPS>(A, ix, acc, xf);
   const bool lead = split_combine<T, WPS>(acc, part);
   out = acc;
   return lead && ix.i < A.n;
@@ -181,27 +152,44 @@ __device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &
 // (stored once per level), so that a recurrence step is one SpMV and one
 // subtraction: T_{j+1} = S T_j - T_{j-1}, and T_1 = S r / 2 (exact halving).
 
+// In the kernels below WPS = 0 selects two rows per thread (apply_rows2),
+// WPS = 1 one row per thread, WPS > 1 the split form.
+
 // T_1 = t(A) r; x (=|+=) b0*r + b1*T_1
 template <typename T, bool ADD, int WPS>
 __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> S, const T *__restrict__ r,
                                                          T *__restrict__ T1, T *__restrict__ x, T b0, T b1) {
-  pdl_trigger();
+  pdl_sync();
+  if constexpr (WPS == 0) {
+    int r0, r1;
+    rows2(S.n, r0, r1);
+    if (r0 >= S.n) return;
+    T y[2];
+    apply_rows2(S, r, r0, r1, y[0], y[1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = q ? r1 : r0;
+      if (i < 0) break;
+      const T ri = r[i];
+      const T t1 = T(0.5) * y[q];
+      T1[i] = t1;
+      const T inc = fma(b1, t1, b0 * ri);
+      x[i] = ADD ? x[i] + inc : inc;
+    }
+    return;
+  }
   int i;
   T Sr;
   if constexpr (WPS == 1) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.n) return;
-    const RowPre<T> p = row_prefetch(S, i);
-    pdl_wait();
-    Sr = row_apply(S, p, r, i);
+    Sr = apply_row(S, r, i);
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const RowPre<T> p = split_prefetch<T, WPS>(S, ix);
-    pdl_wait();
     i = ix.i;
     const T xi = i < S.n ? r[i] : T(0);
-    if (!split_row<T, WPS>(S, ix, p, xi, [&](int j) { return r[j]; }, Sr, part)) return;
+    if (!split_row<T, WPS>(S, ix, xi, [&](int j) { return r[j]; }, Sr, part)) return;
   }
   const T ri = r[i];
   const T t1 = T(0.5) * Sr;
@@ -214,23 +202,35 @@ __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> S, const T 
 template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> S, const T *__restrict__ Tc,
                                                         const T *Tp, T *Tn, T *__restrict__ x, T bj) {
-  pdl_trigger();
+  pdl_sync();
+  if constexpr (WPS == 0) {
+    int r0, r1;
+    rows2(S.n, r0, r1);
+    if (r0 >= S.n) return;
+    T y[2];
+    apply_rows2(S, Tc, r0, r1, y[0], y[1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = q ? r1 : r0;
+      if (i < 0) break;
+      const T tn = y[q] - Tp[i];
+      Tn[i] = tn;
+      x[i] = fma(bj, tn, x[i]);
+    }
+    return;
+  }
   int i;
   T St;
   if constexpr (WPS == 1) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.n) return;
-    const RowPre<T> p = row_prefetch(S, i);
-    pdl_wait();
-    St = row_apply(S, p, Tc, i);
+    St = apply_row(S, Tc, i);
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const RowPre<T> p = split_prefetch<T, WPS>(S, ix);
-    pdl_wait();
     i = ix.i;
     const T xi = i < S.n ? Tc[i] : T(0);
-    if (!split_row<T, WPS>(S, ix, p, xi, [&](int j) { return Tc[j]; }, St, part)) return;
+    if (!split_row<T, WPS>(S, ix, xi, [&](int j) { return Tc[j]; }, St, part)) return;
   }
   const T tn = St - Tp[i];
   Tn[i] = tn;
@@ -258,42 +258,50 @@ __global__ void k_scale(int n, const T *__restrict__ r, T *__restrict__ x, T b0)
 template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *__restrict__ x,
                                                        const T *__restrict__ r, T *__restrict__ s) {
-  pdl_trigger();
-  if constexpr (WPS == 1) {
+  pdl_sync();
+  if constexpr (WPS == 0) {
+    int r0, r1;
+    rows2(A.n, r0, r1);
+    if (r0 >= A.n) return;
+    T y0, y1;
+    apply_rows2(A, x, r0, r1, y0, y1);
+    s[r0] = r[r0] - y0;
+    if (r1 >= 0) s[r1] = r[r1] - y1;
+  } else if constexpr (WPS == 1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    const RowPre<T> p = row_prefetch(A, i);
-    pdl_wait();
-    s[i] = r[i] - row_apply(A, p, x, i);
+    s[i] = r[i] - apply_row(A, x, i);
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const RowPre<T> p = split_prefetch<T, WPS>(A, ix);
-    pdl_wait();
     const T xi = ix.i < A.n ? x[ix.i] : T(0);
     T Ax;
-    if (split_row<T, WPS>(A, ix, p, xi, [&](int j) { return x[j]; }, Ax, part)) s[ix.i] = r[ix.i] - Ax;
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) s[ix.i] = r[ix.i] - Ax;
   }
 }
 
 template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_spmv(SellView<T> A, const T *__restrict__ x,
                                                    T *__restrict__ y) {
-  pdl_trigger();
-  if constexpr (WPS == 1) {
+  pdl_sync();
+  if constexpr (WPS == 0) {
+    int r0, r1;
+    rows2(A.n, r0, r1);
+    if (r0 >= A.n) return;
+    T y0, y1;
+    apply_rows2(A, x, r0, r1, y0, y1);
+    y[r0] = y0;
+    if (r1 >= 0) y[r1] = y1;
+  } else if constexpr (WPS == 1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    const RowPre<T> p = row_prefetch(A, i);
-    pdl_wait();
-    y[i] = row_apply(A, p, x, i);
+    y[i] = apply_row(A, x, i);
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const RowPre<T> p = split_prefetch<T, WPS>(A, ix);
-    pdl_wait();
     const T xi = ix.i < A.n ? x[ix.i] : T(0);
     T Ax;
-    if (split_row<T, WPS>(A, ix, p, xi, [&](int j) { return x[j]; }, Ax, part)) y[ix.i] = Ax;
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) y[ix.i] = Ax;
   }
 }
 

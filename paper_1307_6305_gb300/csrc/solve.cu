@@ -43,25 +43,13 @@ namespace amg {
 template <typename T>
 __global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__restrict__ mem,
                            const T *__restrict__ s, T *__restrict__ rH, double *flag) {
-  pdl_trigger();
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  // the aggregate's member list (setup data) before the wait
-  int a0 = 0, a1 = 0, m[kPre] = {};
-  if (I < nH) {
-    a0 = ptr[I];
-    a1 = ptr[I + 1];
-#pragma unroll
-    for (int q = 0; q < kPre; ++q)
-      if (a0 + q < a1) m[q] = mem[a0 + q];
-  }
-  pdl_wait();
+  pdl_sync();
   if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nH) return;
   T acc = T(0);
-#pragma unroll
-  for (int q = 0; q < kPre; ++q)
-    if (a0 + q < a1) acc += s[m[q]];
-  for (int a = a0 + kPre; a < a1; ++a) acc += s[mem[a]];
+#pragma unroll 4
+  for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += s[mem[a]];
   rH[I] = acc;
 }
 
@@ -78,12 +66,10 @@ __global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__res
 template <typename T>
 __global__ void k_prolong_set(int n, const int *__restrict__ agg, const T *__restrict__ eH,
                               const T *__restrict__ u, T *__restrict__ x) {
-  pdl_trigger();
+  pdl_sync();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int a = agg[i];
-  pdl_wait();
-  x[i] = u[i] + eH[a];
+  x[i] = u[i] + eH[agg[i]];
 }
 
 template <typename A, typename B>
@@ -260,10 +246,9 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *
     const int groups = (((A.n + kSlice - 1) / kSlice) * WPS + kThreads / 32 - 1) / (kThreads / 32);
     for (int g = blockIdx.x; g < groups; g += gridDim.x) {  // block-uniform trip count
       const SplitIdx ix = split_index<WPS>(g);
-      const RowPre<T> p = split_prefetch<T, WPS>(A, ix);
       const T xi = ix.i < A.n ? x[ix.i] : T(0);
       T yi;
-      if (split_row<T, WPS>(A, ix, p, xi, [&](int j) { return x[j]; }, yi, part)) accumulate(ix.i, yi);
+      if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, yi, part)) accumulate(ix.i, yi);
       __syncthreads();  // part is rewritten by the next group
     }
   }
@@ -301,15 +286,13 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
                                                                const T *__restrict__ eH,
                                                                const T *__restrict__ u, const T *__restrict__ r,
                                                                T *__restrict__ xout, T *__restrict__ s) {
-  pdl_trigger();
+  pdl_sync();
   if constexpr (WPS > 1) {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
-    const RowPre<T> p = split_prefetch<T, WPS>(A, ix);
-    pdl_wait();
     const T xi = ix.i < A.n ? u[ix.i] + eH[agg[ix.i]] : T(0);
     T Ax;
-    if (split_row<T, WPS>(A, ix, p, xi, [&](int j) { return u[j] + eH[agg[j]]; }, Ax, part)) {
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return u[j] + eH[agg[j]]; }, Ax, part)) {
       xout[ix.i] = xi;
       s[ix.i] = r[ix.i] - Ax;
     }
@@ -317,23 +300,26 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
-  const RowPre<T> p = row_prefetch(A, i);
-  const int ai = agg[i];
-  pdl_wait();
-  const T xi = u[i] + eH[ai];
+  const T xi = u[i] + eH[agg[i]];
   xout[i] = xi;
-  // neighbours' values formed on the fly: u_j + e_H[agg_j]
-  T acc = p.d * xi;
-#pragma unroll
-  for (int k = 0; k < kPre; ++k) {
-    if (k < p.w) {
-      const int j = p.pc[k];
-      acc = fma(p.pv[k], u[j] + eH[agg[j]], acc);
+  const int sl = i >> 5, lane = i & 31;
+  const int64_t base = A.sptr[sl];
+  const int w = (int)((A.sptr[sl + 1] - base) >> 5);
+  const int32_t *__restrict__ c = A.scol + base + lane;
+  const T *__restrict__ v = A.val + base + lane;
+  T acc = A.diag[i] * xi;
+  if (A.stream) {
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const int j = __ldcs(c + k * kSlice);
+      acc = fma(__ldcs(v + k * kSlice), u[j] + eH[agg[j]], acc);
     }
-  }
-  for (int k = kPre; k < p.w; ++k) {
-    const int j = ldc(A, p.c + k * kSlice);
-    acc = fma(ldv(A, p.v + k * kSlice), u[j] + eH[agg[j]], acc);
+  } else {
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const int j = c[k * kSlice];
+      acc = fma(v[k * kSlice], u[j] + eH[agg[j]], acc);
+    }
   }
   s[i] = r[i] - acc;
 }
@@ -450,6 +436,19 @@ static amg_status with_wps(int wps, F f) {
     case 2: return f(std::integral_constant<int, 2>{});
     default: return f(std::integral_constant<int, 1>{});
   }
+}
+
+// The operator kernels that also have a two-rows-per-thread form (smoother
+// steps, residual, SpMV) launch through these: the level's form and grid.
+static inline int row_form(const amg::Level &L) { return L.rows2 ? 0 : L.wps; }
+static inline unsigned row_grid(const amg::Level &L) {
+  if (L.rows2) return (unsigned)std::max<int64_t>(1, ((int64_t)L.n + 2 * kThreads - 1) / (2 * kThreads));
+  return sell_grid(L.n, L.wps);
+}
+template <typename F>
+static amg_status with_form(const amg::Level &L, F f) {
+  if (L.rows2) return f(std::integral_constant<int, 0>{});
+  return with_wps(L.wps, f);
 }
 
 template <typename T>
@@ -574,8 +573,8 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     return AMG_OK;
   }
   T *Ta = (T *)L.Ta, *Tb = (T *)L.Tb;
-  const dim3 grid(sell_grid(L.n, L.wps));
-  AMG_TRY(with_wps(L.wps, [&](auto W) {
+  const dim3 grid(row_grid(L));
+  AMG_TRY(with_form(L, [&](auto W) {
     constexpr int wp = decltype(W)::value;
     if (add) return plaunch(h, st, k_cheb_first<T, true, wp>, grid, dim3(kThreads), S, r, Ta, x, (T)L.coef[0], (T)L.coef[1]);
     return plaunch(h, st, k_cheb_first<T, false, wp>, grid, dim3(kThreads), S, r, Ta, x, (T)L.coef[0], (T)L.coef[1]);
@@ -588,7 +587,7 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     T *Tn = (j == 2) ? Tb : const_cast<T *>(Tp);
     cudaEvent_t e0, e1;
     if (timed) AMG_TRY(timing_record(h, &e0));
-    AMG_TRY(with_wps(L.wps, [&](auto W) {
+    AMG_TRY(with_form(L, [&](auto W) {
       return plaunch(h, st, k_cheb_step<T, decltype(W)::value>, grid, dim3(kThreads), S, Tc, Tp, Tn, x, (T)L.coef[j]);
     }));
     SLAUNCH(h);
@@ -602,9 +601,9 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
 template <typename T>
 static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s) {
   amg::Level &L = h->lv[k];
-  AMG_TRY(with_wps(L.wps, [&](auto W) {
-    return plaunch(h, h->stream, k_residual<T, decltype(W)::value>, dim3(sell_grid(L.n, L.wps)), dim3(kThreads),
-                   view<T>(L), x, r, s);
+  AMG_TRY(with_form(L, [&](auto W) {
+    return plaunch(h, h->stream, k_residual<T, decltype(W)::value>, dim3(row_grid(L)), dim3(kThreads), view<T>(L), x,
+                   r, s);
   }));
   SLAUNCH(h);
   return AMG_OK;
@@ -621,11 +620,13 @@ static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s)
 constexpr int kProlongSplitRows = 1 << 17;
 // matrix bytes (stored values + columns) from which a level streams its matrix
 constexpr double kStreamMatrixBytes = 64.0 * (1 << 20);
+// rows from which a one-warp-per-slice level runs two rows per thread
+constexpr int kRows2MinRows = 1 << 18;
 
 template <typename T>
 static amg_status prolong_residual(amg_handle_s *h, int k, const T *eH, const T *u, const T *r, T *x, T *s) {
   amg::Level &L = h->lv[k];
-  if (h->prolong_split && L.wps == 1 && L.n >= kProlongSplitRows) {
+  if (h->prolong_split && L.wps == 1 && (L.n >= kProlongSplitRows || L.rows2)) {
     AMG_TRY(plaunch(h, h->stream, k_prolong_set<T>, dim3(nblk(L.n)), dim3(kThreads), L.n, L.agg, eH, u, x));
     SLAUNCH(h);
     return residual<T>(h, k, x, r, s);
@@ -915,6 +916,8 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // policy (A/B timing of the streaming loads)
   const char *stream_env = getenv("AMG_GB300_STREAM");
   const bool stream_ok = !(stream_env && stream_env[0] == '0');
+  const char *rows2_env = getenv("AMG_GB300_ROWS2");
+  const int rows2_mode = rows2_env ? atoi(rows2_env) : 2;
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     const size_t n = (size_t)std::max(V.n, 1);
@@ -922,6 +925,10 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     // one pass over the level's stored values and columns is at least the
     // size of L2: stream it (the vectors and the coarser levels stay cached)
     V.stream = stream_ok && (double)V.S.stored * (double)(es + 4) >= kStreamMatrixBytes;
+    // two rows per thread on large one-warp-per-slice levels
+    // (AMG_GB300_ROWS2=0 keeps one row per thread, =1 forces it on every
+    // such level)
+    V.rows2 = V.wps == 1 && rows2_mode != 0 && (rows2_mode == 1 || V.n >= kRows2MinRows);
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1 && h->opt.degree > 0) {
       // the smoother form 2 t(A) of this level (Chebyshev kernels)
@@ -1122,8 +1129,8 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       AMG_TRY(plaunch(h, st, k_axpy_multi<double>, dim3(nblk(n)), dim3(kThreads), n, d, h->oz, vd, sc + 16));
       SLAUNCH(h);
     }
-    AMG_TRY(with_wps(L0.wps, [&](auto W) {
-      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, d, q);
+    AMG_TRY(with_form(L0, [&](auto W) {
+      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(row_grid(L0)), dim3(kThreads), A0, d, q);
     }));
     SLAUNCH(h);
     {
@@ -1164,8 +1171,8 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
   // true residual ||b - A x|| / ||b||
   double true_rel = 0.0;
   if (nb > 0.0) {
-    AMG_TRY(with_wps(L0.wps, [&](auto W) {
-      return plaunch(h, st, k_residual<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, x_dev,
+    AMG_TRY(with_form(L0, [&](auto W) {
+      return plaunch(h, st, k_residual<double, decltype(W)::value>, dim3(row_grid(L0)), dim3(kThreads), A0, x_dev,
                      h->ob, h->oz);
     }));
     SLAUNCH(h);
