@@ -13,16 +13,12 @@ static inline unsigned nblk(int64_t n, int t = kThreads) {
   return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1);
 }
 
-// Programmatic dependent launch (no-ops for ordinary launches, the default;
-// AMG_GB300_PDL=1 launches the solve kernels with it).  pdl_trigger lets the
-// next kernel in the stream be scheduled while this one runs; pdl_wait
-// blocks until the preceding kernel has completed and its writes are
-// visible; every kernel calls both before touching memory.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Programmatic dependent launch: wait until the preceding kernel has
+// completed and its writes are visible, then let the next kernel in the
+// stream be scheduled while this one runs (no-op for ordinary launches)
 __device__ __forceinline__ void pdl_sync() {
-  pdl_trigger();
-  pdl_wait();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // launch with programmatic stream serialization (PDL); arguments are

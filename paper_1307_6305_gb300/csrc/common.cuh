@@ -153,7 +153,6 @@ struct Level {
   int n = 0;
   int wps = 1;           // warps per SELL slice in the solve kernels (1, 2, 4 or 8)
   int stream = 0;        // matrix loads with the streaming cache policy (SellView::stream)
-  bool rows2 = false;    // operator kernels take two rows per thread (wps == 1 only)
   Csr A;                 // setup form
   double *diag = nullptr;
   double *dlow = nullptr;

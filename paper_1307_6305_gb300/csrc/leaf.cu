@@ -15,14 +15,20 @@
 //     (computed once per setup), so a coarse inner step forms D = B r and
 //     W = A_k0+1 D = (A_k0+1 B) r in one phase;
 //   * every vector that some phase reads at another CTA's rows is kept as a
-//     full copy in every CTA's shared memory; the phase that produces it
-//     writes each new entry into all C copies with distributed-shared-memory
-//     stores, so every later read is a local shared-memory load;
+//     copy in every CTA's shared memory; the phase that produces an entry of
+//     a level-k0 vector writes it with distributed-shared-memory stores into
+//     the copies of the CTAs that read that row (the owner, the owners of its
+//     neighbours and of its aggregate: a per-row mask made at setup), an
+//     entry of a coarse vector into every copy;
 //   * a hardware cluster barrier (release/acquire) ends each phase;
-//   * dot products: each CTA posts its partial sums into every CTA's slot
-//     table; after the barrier every CTA adds the C partials in rank order,
-//     so all CTAs hold bit-identical Krylov scalars (the stop/breakdown
-//     decisions are therefore uniform) and no global scalar traffic occurs.
+//   * level-k0 dot products: each CTA posts its partial sums into every CTA's
+//     slot table; after the barrier every CTA adds the C partials in rank
+//     order, so all CTAs hold bit-identical Krylov scalars (the stop/breakdown
+//     decisions are therefore uniform) and no global scalar traffic occurs;
+//   * the coarse inner solve (level k0+1, a few hundred rows): after D and W
+//     are sent to every CTA, each CTA computes the scalars and updates D, W,
+//     x and r over all coarse rows itself, in the same order everywhere, so
+//     its orthogonalisation and updates need no barrier of their own.
 // Every cluster barrier sits in code whose trip counts come from the launch
 // parameters only, so all CTAs meet the same barriers.
 //
@@ -52,6 +58,7 @@ constexpr int kLeafMaxRows = 2048;    // rows of level k0
 constexpr int kLeafMaxCoarse = 1024;  // rows of level k0 + 1
 constexpr int kLeafSlot = 8;          // doubles per CTA in a slot table
 constexpr int kLeafProfSlots = 128;   // phases recorded by the opt-in profile
+constexpr int kDenseLanes = 8;        // lanes per row of the dense coarse products
 
 // shared-memory arrays, in layout order
 enum LeafArr : int {
@@ -61,7 +68,7 @@ enum LeafArr : int {
   A_W0 = A_D0 + kLeafMaxInner, A_XO = A_W0 + kLeafMaxInner,
   // full copies, level k0+1 (nH entries of T)
   A_HB, A_HR, A_HX, A_HD0,
-  // owned rows, level k0+1 (RH entries of T)
+  // full copies, level k0+1 (nH entries of T)
   A_HW0 = A_HD0 + kLeafMaxInner,
   // compact CSR of the owned rows of A_k0 (off-diagonal) and its diagonal,
   // and the values and diagonal of the smoother form S = 2 t(A) on the same
@@ -116,7 +123,7 @@ static unsigned leaf_layout(LeafParams<T> &P) {
     cnt[A_D0 + l] = P.n;
     cnt[A_W0 + l] = P.R;
     cnt[A_HD0 + l] = P.nH;
-    cnt[A_HW0 + l] = P.RH;
+    cnt[A_HW0 + l] = P.nH;
   }
   cnt[A_XO] = P.R;
   cnt[A_HB] = cnt[A_HR] = cnt[A_HX] = P.nH;
@@ -266,13 +273,23 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
   // dot products: post this CTA's nd partial sums (nd <= kLeafSlot, static
   // register indices) to every CTA's slot table
   int sb = 0;
-  auto post = [&](const double (&v)[kLeafSlot], int nd) {
+  // Every shuffle-add step is a full-warp FP64 add (2 lanes per clock on
+  // this part), so the tree is cut short: the partials sit only in lanes
+  // that are multiples of `stride` (the caller's lane grouping), and a warp
+  // whose partials are all zero writes zeros without a tree.
+  auto post = [&](const double (&v)[kLeafSlot], int nd, int stride) {
+    bool nz = false;
+#pragma unroll
+    for (int q = 0; q < kLeafSlot; ++q)
+      if (q < nd) nz |= v[q] != 0.0;
+    const bool active = __any_sync(0xffffffffu, nz);
 #pragma unroll
     for (int q = 0; q < kLeafSlot; ++q) {
       if (q < nd) {
         double t = v[q];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) wred[warp * kLeafSlot + q] = t;
+        if (active)
+          for (int o = 16; o >= stride; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) wred[warp * kLeafSlot + q] = active ? t : 0.0;
       }
     }
     __syncthreads();
@@ -362,92 +379,121 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
 
   // the inner flexible CG at level k0+1 (nu steps, preconditioner B) on
   // hb; result in hx (full copy)
+  // dot products over all nH coarse rows of data every CTA holds in full,
+  // in a fixed order (thread I's products, then the warp tree, then warps in
+  // order): every CTA gets the same bits, so no cluster exchange is needed.
+  // out[q] = sum_I f(I, q) for q < nd, in shared memory; ends with a CTA
+  // barrier.
+  auto local_dots = [&](double *out, int nd, auto f) {
+    double v[kLeafSlot] = {};
+    for (int I = tid; I < nH; I += kLeafThreads) {
+#pragma unroll
+      for (int q = 0; q < kLeafSlot; ++q)
+        if (q < nd) v[q] += f(I, q);
+    }
+    const bool active = __any_sync(0xffffffffu, tid < nH);
+#pragma unroll
+    for (int q = 0; q < kLeafSlot; ++q) {
+      if (q < nd) {
+        double t = v[q];
+        if (active)
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) wred[warp * kLeafSlot + q] = active ? t : 0.0;
+      }
+    }
+    __syncthreads();
+    if (tid < nd) {
+      double t = 0.0;
+      for (int w = 0; w < kLeafWarps; ++w) t += wred[w * kLeafSlot + tid];
+      out[tid] = t;
+    }
+    __syncthreads();
+  };
+
+  // the inner flexible CG at level k0+1 (nu steps, preconditioner B) on
+  // hb; result in hx (full copy).  A step forms D = B rin and W = A D =
+  // (A B) rin at the owned rows and sends both to every CTA (one cluster
+  // barrier); every CTA then derives the Krylov scalars and updates D, W,
+  // x and r over all nH rows itself (nH is a few hundred), identically, so
+  // the orthogonalisation and the update need no further barrier.
   auto inner_coarse = [&]() {
-    if (tid == 0) scH[12] = 0.0;  // stop flag (read after the next barrier)
+    if (tid == 0) scH[12] = 0.0;  // stop flag
     for (int it = 0; it < nu; ++it) {
       const T *rin = (it == 0) ? hb : hr;
       T *D = vec(A_HD0 + it), *W = vec(A_HW0 + it);
-      // D = B rin and W = A D = (A B) rin in one pass (fp64, one warp per
-      // owned row; both only at owned rows, so no copy is broadcast), with
-      // rho = D.W, sigma = rin.D (step 0) or D_l.W (step > 0)
-      double dv[kLeafSlot] = {};
-      for (int base = 0; base < P.RH; base += kLeafWarps) {
-        const int lI = base + warp;
+      // D = B rin and W = (A B) rin at the owned rows (fp64).  kDenseLanes
+      // lanes per row, 32 / kDenseLanes rows per warp: on this part the FP64
+      // pipe issues 2 lanes per clock, so a shuffle-add tree over 32 lanes
+      // (every step a full-warp FP64 add) costs as much as the products;
+      // 3 steps that serve 4 rows at once cost a tenth of it.
+      const int sub = lane / kDenseLanes, dq = lane % kDenseLanes;
+      constexpr int kRowsPerPass = kLeafWarps * (32 / kDenseLanes);
+      for (int base = 0; base < P.RH; base += kRowsPerPass) {
+        const int lI = base + warp * (32 / kDenseLanes) + sub;
         const bool ok = lI < nlocH;
         double ad = 0.0, aw = 0.0;
         if (ok)
-          for (int j = lane; j < nH; j += 32) {
+          for (int j = dq; j < nH; j += kDenseLanes) {
             const double rj = (double)rin[j];
             ad = fma(brows[(size_t)lI * nH + j], rj, ad);
             aw = fma(abrows[(size_t)lI * nH + j], rj, aw);
           }
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = kDenseLanes / 2; o > 0; o >>= 1) {  // within the row's lane group
           ad += __shfl_xor_sync(0xffffffffu, ad, o);
           aw += __shfl_xor_sync(0xffffffffu, aw, o);
         }
-        if (ok && lane == 0) {
+        if (ok && dq == 0) {
           const int I = h0 + lI;
-          const T d = (T)ad, w = (T)aw;
-          D[I] = d;
-          W[lI] = w;
-          if (it == 0) {
-            dv[0] += (double)d * (double)w;
-            dv[1] += (double)rin[I] * (double)d;
-          } else {
-#pragma unroll
-            for (int l = 0; l < kLeafMaxInner; ++l)
-              if (l < it) dv[l] += (double)vec(A_HD0 + l)[I] * (double)w;
-          }
+          put(D, I, (T)ad);
+          put(W, I, (T)aw);
         }
       }
-      post(dv, it == 0 ? 2 : it);
       csync();
-      fold(sums, it == 0 ? 2 : it);
       if (it == 0) {
+        // rho = D.W, sigma = rin.D
+        local_dots(sums, 2, [&](int I, int q) {
+          return q == 0 ? (double)D[I] * (double)W[I] : (double)rin[I] * (double)D[I];
+        });
         if (tid == 0) fin_alpha(scH, 0);
       } else {
-        if (tid < it) scH[8 + tid] = sums[tid] / scH[tid];  // beta_l
+        // beta_l = D_l.W / rho_l; D -= sum beta_l D_l, W -= sum beta_l W_l;
+        // rho = D.W, sigma = D.rin
+        local_dots(sums, it, [&](int I, int l) { return (double)vec(A_HD0 + l)[I] * (double)W[I]; });
+        if (tid < it) scH[8 + tid] = sums[tid] / scH[tid];
         __syncthreads();
-        // D -= sum beta_l D_l, W -= sum beta_l W_l; rho = D.W, sigma = D.rin
-        double ev[kLeafSlot] = {};
-        for (int lI = tid; lI < nlocH; lI += kLeafThreads) {
-          const int I = h0 + lI;
-          T d = D[I], w = W[lI];
+        for (int I = tid; I < nH; I += kLeafThreads) {
+          T d = D[I], w = W[I];
 #pragma unroll
           for (int l = 0; l < kLeafMaxInner; ++l) {
             if (l < it) {
               const T bl = (T)scH[8 + l];
               d -= bl * vec(A_HD0 + l)[I];
-              w -= bl * vec(A_HW0 + l)[lI];
+              w -= bl * vec(A_HW0 + l)[I];
             }
           }
           D[I] = d;
-          W[lI] = w;
-          ev[0] += (double)d * (double)w;
-          ev[1] += (double)d * (double)rin[I];
+          W[I] = w;
         }
-        post(ev, 2);
-        csync();
-        fold(sums, 2);
+        __syncthreads();
+        local_dots(sums, 2, [&](int I, int q) {
+          return q == 0 ? (double)D[I] * (double)W[I] : (double)D[I] * (double)rin[I];
+        });
         if (tid == 0) fin_alpha(scH, it);
       }
       __syncthreads();
       // x = alpha D (it 0) or x += alpha D; r = rin - alpha W before another step
       const bool here = scH[12] != 0.0 && scH[4 + it] == 0.0;
       const T a = (T)scH[4 + it];
-      const bool upd_r = it + 1 < nu, last = it + 1 == nu;
-      for (int lI = tid; lI < nlocH; lI += kLeafThreads) {
-        const int I = h0 + lI;
-        T xv;
-        if (it == 0) xv = here ? T(0) : a * D[I];
-        else xv = here ? hx[I] : fma(a, D[I], hx[I]);
-        if (last) put(hx, I, xv);
-        else hx[I] = xv;
-        if (upd_r) put(hr, I, here ? rin[I] : rin[I] - a * W[lI]);
+      const bool upd_r = it + 1 < nu;
+      for (int I = tid; I < nH; I += kLeafThreads) {
+        if (it == 0) hx[I] = here ? T(0) : a * D[I];
+        else if (!here) hx[I] = fma(a, D[I], hx[I]);
+        if (upd_r) hr[I] = here ? rin[I] : rin[I] - a * W[I];
       }
-      csync();
+      __syncthreads();
     }
   };
+
 
   // x = K_k0(r): the W(1,1) cycle at level k0; r, x full copies
   auto kcycle = [&](const T *r, T *x) {
@@ -499,7 +545,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
                 if (l < it) dv[l] += (double)vec(A_D0 + l)[i] * (double)w;
             }
           });
-    post(dv, it == 0 ? 2 : it);
+    post(dv, it == 0 ? 2 : it, P.tpr);
     csync();
     fold(sums, it == 0 ? 2 : it);
     if (it == 0) {
@@ -524,7 +570,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
         ev[0] += (double)d * (double)w;
         ev[1] += (double)d * (double)rin[i];
       }
-      post(ev, 2);
+      post(ev, 2, 1);
       csync();
       fold(sums, 2);
       if (tid == 0) fin_alpha(scT, it);
@@ -542,7 +588,10 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
       if (last) P.x[i] = xv;
       if (upd_r) put0(vr, i, here ? rin[i] : rin[i] - a * W[li]);
     }
-    csync();
+    // the last step sends nothing to other CTAs (x goes to global memory):
+    // every remote store of the launch completed at an earlier barrier, so
+    // the CTAs may exit without another one
+    if (upd_r) csync();
   }
   if (P.prof && rank == 0 && tid == 0) atomicAdd(&P.prof[kLeafProfSlots - 1], 1ull);
 }

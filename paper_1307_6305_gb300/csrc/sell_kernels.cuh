@@ -35,54 +35,6 @@ __device__ __forceinline__ T apply_row(const SellView<T> &A, const T *__restrict
   return sell_row(A, x, row, A.diag[row] * x[row]);
 }
 
-// Two rows per thread (large levels): rows r0 and r1 of different slices
-// (the same lane of consecutive 256-row tiles) run as two interleaved load
-// chains in one loop, so each thread keeps twice the loads in flight.  Each
-// row's sum is taken in the order of apply_row.  r1 < 0: no second row.
-template <typename T>
-__device__ __forceinline__ void apply_rows2(const SellView<T> &A, const T *__restrict__ x, int r0, int r1, T &y0,
-                                            T &y1) {
-  const int s0 = r0 >> 5, s1 = r1 >> 5, lane = r0 & 31;
-  const int64_t b0 = A.sptr[s0];
-  const int w0 = (int)((A.sptr[s0 + 1] - b0) >> 5);
-  int64_t b1 = 0;
-  int w1 = 0;
-  if (r1 >= 0) {
-    b1 = A.sptr[s1];
-    w1 = (int)((A.sptr[s1 + 1] - b1) >> 5);
-  }
-  const int32_t *__restrict__ c0 = A.scol + b0 + lane;
-  const T *__restrict__ v0 = A.val + b0 + lane;
-  const int32_t *__restrict__ c1 = A.scol + b1 + lane;
-  const T *__restrict__ v1 = A.val + b1 + lane;
-  T a0 = A.diag[r0] * x[r0];
-  T a1 = r1 >= 0 ? A.diag[r1] * x[r1] : T(0);
-  const int wm = max(w0, w1);
-  if (A.stream) {
-#pragma unroll 4
-    for (int k = 0; k < wm; ++k) {
-      if (k < w0) a0 = fma(__ldcs(v0 + k * kSlice), x[__ldcs(c0 + k * kSlice)], a0);
-      if (k < w1) a1 = fma(__ldcs(v1 + k * kSlice), x[__ldcs(c1 + k * kSlice)], a1);
-    }
-  } else {
-#pragma unroll 4
-    for (int k = 0; k < wm; ++k) {
-      if (k < w0) a0 = fma(v0[k * kSlice], x[c0[k * kSlice]], a0);
-      if (k < w1) a1 = fma(v1[k * kSlice], x[c1[k * kSlice]], a1);
-    }
-  }
-  y0 = a0;
-  y1 = a1;
-}
-
-// the rows of thread threadIdx.x in block blockIdx.x of a two-rows-per-thread
-// launch: r0 in even 256-row tiles, r1 in the odd tile after it (-1 if past n)
-__device__ __forceinline__ void rows2(int n, int &r0, int &r1) {
-  r0 = (2 * blockIdx.x) * blockDim.x + threadIdx.x;
-  r1 = r0 + blockDim.x;
-  if (r1 >= n) r1 = -1;
-}
-
 // Split rows for small levels.  With one thread per row, a row of w stored
 // entries costs about w/4 dependent round trips to L2 (column index, then
 // x[col]), and a level of a few thousand rows keeps only a few SMs busy on
@@ -152,32 +104,11 @@ __device__ __forceinline__ bool split_row(const SellView<T> &A, const SplitIdx &
 // (stored once per level), so that a recurrence step is one SpMV and one
 // subtraction: T_{j+1} = S T_j - T_{j-1}, and T_1 = S r / 2 (exact halving).
 
-// In the kernels below WPS = 0 selects two rows per thread (apply_rows2),
-// WPS = 1 one row per thread, WPS > 1 the split form.
-
 // T_1 = t(A) r; x (=|+=) b0*r + b1*T_1
 template <typename T, bool ADD, int WPS>
 __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> S, const T *__restrict__ r,
                                                          T *__restrict__ T1, T *__restrict__ x, T b0, T b1) {
   pdl_sync();
-  if constexpr (WPS == 0) {
-    int r0, r1;
-    rows2(S.n, r0, r1);
-    if (r0 >= S.n) return;
-    T y[2];
-    apply_rows2(S, r, r0, r1, y[0], y[1]);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = q ? r1 : r0;
-      if (i < 0) break;
-      const T ri = r[i];
-      const T t1 = T(0.5) * y[q];
-      T1[i] = t1;
-      const T inc = fma(b1, t1, b0 * ri);
-      x[i] = ADD ? x[i] + inc : inc;
-    }
-    return;
-  }
   int i;
   T Sr;
   if constexpr (WPS == 1) {
@@ -203,22 +134,6 @@ template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> S, const T *__restrict__ Tc,
                                                         const T *Tp, T *Tn, T *__restrict__ x, T bj) {
   pdl_sync();
-  if constexpr (WPS == 0) {
-    int r0, r1;
-    rows2(S.n, r0, r1);
-    if (r0 >= S.n) return;
-    T y[2];
-    apply_rows2(S, Tc, r0, r1, y[0], y[1]);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = q ? r1 : r0;
-      if (i < 0) break;
-      const T tn = y[q] - Tp[i];
-      Tn[i] = tn;
-      x[i] = fma(bj, tn, x[i]);
-    }
-    return;
-  }
   int i;
   T St;
   if constexpr (WPS == 1) {
@@ -259,15 +174,7 @@ template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *__restrict__ x,
                                                        const T *__restrict__ r, T *__restrict__ s) {
   pdl_sync();
-  if constexpr (WPS == 0) {
-    int r0, r1;
-    rows2(A.n, r0, r1);
-    if (r0 >= A.n) return;
-    T y0, y1;
-    apply_rows2(A, x, r0, r1, y0, y1);
-    s[r0] = r[r0] - y0;
-    if (r1 >= 0) s[r1] = r[r1] - y1;
-  } else if constexpr (WPS == 1) {
+  if constexpr (WPS == 1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     s[i] = r[i] - apply_row(A, x, i);
@@ -284,15 +191,7 @@ template <typename T, int WPS>
 __global__ void __launch_bounds__(kThreads) k_spmv(SellView<T> A, const T *__restrict__ x,
                                                    T *__restrict__ y) {
   pdl_sync();
-  if constexpr (WPS == 0) {
-    int r0, r1;
-    rows2(A.n, r0, r1);
-    if (r0 >= A.n) return;
-    T y0, y1;
-    apply_rows2(A, x, r0, r1, y0, y1);
-    y[r0] = y0;
-    if (r1 >= 0) y[r1] = y1;
-  } else if constexpr (WPS == 1) {
+  if constexpr (WPS == 1) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     y[i] = apply_row(A, x, i);

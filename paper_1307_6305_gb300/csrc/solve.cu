@@ -438,19 +438,6 @@ static amg_status with_wps(int wps, F f) {
   }
 }
 
-// The operator kernels that also have a two-rows-per-thread form (smoother
-// steps, residual, SpMV) launch through these: the level's form and grid.
-static inline int row_form(const amg::Level &L) { return L.rows2 ? 0 : L.wps; }
-static inline unsigned row_grid(const amg::Level &L) {
-  if (L.rows2) return (unsigned)std::max<int64_t>(1, ((int64_t)L.n + 2 * kThreads - 1) / (2 * kThreads));
-  return sell_grid(L.n, L.wps);
-}
-template <typename F>
-static amg_status with_form(const amg::Level &L, F f) {
-  if (L.rows2) return f(std::integral_constant<int, 0>{});
-  return with_wps(L.wps, f);
-}
-
 template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
@@ -573,8 +560,8 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     return AMG_OK;
   }
   T *Ta = (T *)L.Ta, *Tb = (T *)L.Tb;
-  const dim3 grid(row_grid(L));
-  AMG_TRY(with_form(L, [&](auto W) {
+  const dim3 grid(sell_grid(L.n, L.wps));
+  AMG_TRY(with_wps(L.wps, [&](auto W) {
     constexpr int wp = decltype(W)::value;
     if (add) return plaunch(h, st, k_cheb_first<T, true, wp>, grid, dim3(kThreads), S, r, Ta, x, (T)L.coef[0], (T)L.coef[1]);
     return plaunch(h, st, k_cheb_first<T, false, wp>, grid, dim3(kThreads), S, r, Ta, x, (T)L.coef[0], (T)L.coef[1]);
@@ -587,7 +574,7 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
     T *Tn = (j == 2) ? Tb : const_cast<T *>(Tp);
     cudaEvent_t e0, e1;
     if (timed) AMG_TRY(timing_record(h, &e0));
-    AMG_TRY(with_form(L, [&](auto W) {
+    AMG_TRY(with_wps(L.wps, [&](auto W) {
       return plaunch(h, st, k_cheb_step<T, decltype(W)::value>, grid, dim3(kThreads), S, Tc, Tp, Tn, x, (T)L.coef[j]);
     }));
     SLAUNCH(h);
@@ -601,9 +588,9 @@ static amg_status smooth(amg_handle_s *h, int k, const T *r, T *x, bool add) {
 template <typename T>
 static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s) {
   amg::Level &L = h->lv[k];
-  AMG_TRY(with_form(L, [&](auto W) {
-    return plaunch(h, h->stream, k_residual<T, decltype(W)::value>, dim3(row_grid(L)), dim3(kThreads), view<T>(L), x,
-                   r, s);
+  AMG_TRY(with_wps(L.wps, [&](auto W) {
+    return plaunch(h, h->stream, k_residual<T, decltype(W)::value>, dim3(sell_grid(L.n, L.wps)), dim3(kThreads),
+                   view<T>(L), x, r, s);
   }));
   SLAUNCH(h);
   return AMG_OK;
@@ -620,13 +607,11 @@ static amg_status residual(amg_handle_s *h, int k, const T *x, const T *r, T *s)
 constexpr int kProlongSplitRows = 1 << 17;
 // matrix bytes (stored values + columns) from which a level streams its matrix
 constexpr double kStreamMatrixBytes = 64.0 * (1 << 20);
-// rows from which a one-warp-per-slice level runs two rows per thread
-constexpr int kRows2MinRows = 1 << 18;
 
 template <typename T>
 static amg_status prolong_residual(amg_handle_s *h, int k, const T *eH, const T *u, const T *r, T *x, T *s) {
   amg::Level &L = h->lv[k];
-  if (h->prolong_split && L.wps == 1 && (L.n >= kProlongSplitRows || L.rows2)) {
+  if (h->prolong_split && L.wps == 1 && L.n >= kProlongSplitRows) {
     AMG_TRY(plaunch(h, h->stream, k_prolong_set<T>, dim3(nblk(L.n)), dim3(kThreads), L.n, L.agg, eH, u, x));
     SLAUNCH(h);
     return residual<T>(h, k, x, r, s);
@@ -916,8 +901,6 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // policy (A/B timing of the streaming loads)
   const char *stream_env = getenv("AMG_GB300_STREAM");
   const bool stream_ok = !(stream_env && stream_env[0] == '0');
-  const char *rows2_env = getenv("AMG_GB300_ROWS2");
-  const int rows2_mode = rows2_env ? atoi(rows2_env) : 2;
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     const size_t n = (size_t)std::max(V.n, 1);
@@ -925,10 +908,6 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     // one pass over the level's stored values and columns is at least the
     // size of L2: stream it (the vectors and the coarser levels stay cached)
     V.stream = stream_ok && (double)V.S.stored * (double)(es + 4) >= kStreamMatrixBytes;
-    // two rows per thread on large one-warp-per-slice levels
-    // (AMG_GB300_ROWS2=0 keeps one row per thread, =1 forces it on every
-    // such level)
-    V.rows2 = V.wps == 1 && rows2_mode != 0 && (rows2_mode == 1 || V.n >= kRows2MinRows);
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1 && h->opt.degree > 0) {
       // the smoother form 2 t(A) of this level (Chebyshev kernels)
@@ -1129,8 +1108,8 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       AMG_TRY(plaunch(h, st, k_axpy_multi<double>, dim3(nblk(n)), dim3(kThreads), n, d, h->oz, vd, sc + 16));
       SLAUNCH(h);
     }
-    AMG_TRY(with_form(L0, [&](auto W) {
-      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(row_grid(L0)), dim3(kThreads), A0, d, q);
+    AMG_TRY(with_wps(L0.wps, [&](auto W) {
+      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, d, q);
     }));
     SLAUNCH(h);
     {
@@ -1171,8 +1150,8 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
   // true residual ||b - A x|| / ||b||
   double true_rel = 0.0;
   if (nb > 0.0) {
-    AMG_TRY(with_form(L0, [&](auto W) {
-      return plaunch(h, st, k_residual<double, decltype(W)::value>, dim3(row_grid(L0)), dim3(kThreads), A0, x_dev,
+    AMG_TRY(with_wps(L0.wps, [&](auto W) {
+      return plaunch(h, st, k_residual<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, x_dev,
                      h->ob, h->oz);
     }));
     SLAUNCH(h);
