@@ -141,11 +141,23 @@ __device__ __forceinline__ void breduce(const double (&acc)[ND], int kb, double 
   if (t == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
-  if (t < ND * kb) {
-    const int q = t / kb, c = t % kb;
+  {
+    // G threads per (dot, column) pair, each over every G-th CTA's partial
+    // (one round of independent loads), then the G sums in thread order
+    const int npair = ND * kb, G = kThreads / npair;
     double v = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&partial[(size_t)b * kBRed + q * kb + c]);
-    tot[q][c] = v;
+    if (t < npair * G) {
+      const int p = t % npair, g = t / npair;
+      const int q = p / kb, c = p % kb;
+      for (unsigned b = g; b < gridDim.x; b += G) v += __ldcg(&partial[(size_t)b * kBRed + q * kb + c]);
+    }
+    sh[0][t] = v;
+    __syncthreads();
+    if (t < npair) {
+      double s = 0.0;
+      for (int g = 0; g < G; ++g) s += sh[0][g * npair + t];
+      tot[t / kb][t % kb] = s;
+    }
   }
   __syncthreads();
   if (t < kb) {

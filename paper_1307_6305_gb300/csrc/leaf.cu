@@ -62,18 +62,12 @@ constexpr int kDenseLanes = 8;        // lanes per row of the dense coarse produ
 
 // shared-memory arrays, in layout order
 enum LeafArr : int {
-  // full copies, level k0 (n entries of T)
-  A_B = 0, A_R, A_TA, A_TB, A_U, A_S, A_D0,
-  // owned rows, level k0 (R entries of T)
-  A_W0 = A_D0 + kLeafMaxInner, A_XO = A_W0 + kLeafMaxInner,
-  // full copies, level k0+1 (nH entries of T)
-  A_HB, A_HR, A_HX, A_HD0,
-  // full copies, level k0+1 (nH entries of T)
-  A_HW0 = A_HD0 + kLeafMaxInner,
+  // ---- static: fixed per setup, built once in global memory in this
+  // layout (one image per CTA) and copied in by every launch ----
   // compact CSR of the owned rows of A_k0 (off-diagonal) and its diagonal,
   // and the values and diagonal of the smoother form S = 2 t(A) on the same
   // pattern (2 sa a_ij; 2 sa a_ii - 2 ca)
-  A_LRP = A_HW0 + kLeafMaxInner, A_LCOL, A_LVAL, A_LDIAG, A_SVAL, A_SDIAG,
+  A_LRP = 0, A_LCOL, A_LVAL, A_LDIAG, A_SVAL, A_SDIAG,
   // aggregate id of every row of level k0
   A_AGG,
   // destination mask of every owned row (the CTAs that read it)
@@ -82,8 +76,16 @@ enum LeafArr : int {
   A_LAP, A_LAM,
   // owned rows of B and of A_k0+1 B (fp64, nH columns)
   A_BROWS, A_ABROWS,
+  // ---- per launch ----
+  // full copies, level k0 (n entries of T)
+  A_B, A_R, A_TA, A_TB, A_U, A_S, A_D0,
+  // owned rows, level k0 (R entries of T)
+  A_W0 = A_D0 + kLeafMaxInner, A_XO = A_W0 + kLeafMaxInner,
+  // full copies, level k0+1 (nH entries of T)
+  A_HB, A_HR, A_HX, A_HD0,
+  A_HW0 = A_HD0 + kLeafMaxInner,
   // dot-product slot tables [2][C][kLeafSlot] and per-warp partials
-  A_SLOTS, A_WRED,
+  A_SLOTS = A_HW0 + kLeafMaxInner, A_WRED,
   A_COUNT
 };
 
@@ -108,6 +110,10 @@ struct LeafParams {
   // cycles of every phase (barrier to barrier) into prof[phase], and the
   // launch count into prof[kLeafProfSlots - 1]; null otherwise
   unsigned long long *prof;
+  // the static arrays of every CTA: CTA c's image is the first
+  // static_bytes of its shared memory, at image + c * static_bytes
+  const unsigned char *image;
+  unsigned static_bytes;
   unsigned off[A_COUNT];  // byte offsets into dynamic shared memory
   unsigned smem;          // bytes
 };
@@ -156,7 +162,56 @@ static unsigned leaf_layout(LeafParams<T> &P) {
     o += cnt[a] * esz[a];
   }
   P.smem = (unsigned)((o + 15) & ~(size_t)15);
+  P.static_bytes = P.off[A_B];  // a multiple of 16: every offset is
   return P.smem;
+}
+
+// 16-byte asynchronous global -> shared copy (completion: cp.async.wait_all)
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// The static image of CTA blockIdx.x (one block per cluster rank): its rows
+// of the level-k0 operator and smoother form, the aggregate map, masks,
+// member lists and its rows of B and A_k0+1 B, laid out as in shared memory.
+template <typename T>
+__global__ void k_leaf_image(const __grid_constant__ LeafParams<T> P, unsigned char *image) {
+  unsigned char *im = image + (size_t)blockIdx.x * P.static_bytes;
+  const int rank = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int n = P.n, nH = P.nH;
+  const int r0 = rank * P.R, nloc = max(0, min(n, r0 + P.R) - r0), r0c = min(r0, n);
+  const int h0 = rank * P.RH, nlocH = max(0, min(nH, h0 + P.RH) - h0), h0c = min(h0, nH);
+  auto vec = [&](int a) { return reinterpret_cast<T *>(im + P.off[a]); };
+  auto ivec = [&](int a) { return reinterpret_cast<int *>(im + P.off[a]); };
+  int *lrp = ivec(A_LRP), *lcol = ivec(A_LCOL), *agg = ivec(A_AGG), *lap = ivec(A_LAP), *lam = ivec(A_LAM);
+  unsigned *lmask = reinterpret_cast<unsigned *>(im + P.off[A_MASK]);
+  T *lval = vec(A_LVAL), *ldiag = vec(A_LDIAG), *sval = vec(A_SVAL), *sdiag = vec(A_SDIAG);
+  double *brows = reinterpret_cast<double *>(im + P.off[A_BROWS]);
+  double *abrows = reinterpret_cast<double *>(im + P.off[A_ABROWS]);
+  for (int i = tid; i < n; i += nt) agg[i] = P.agg[i];
+  const int64_t e0 = P.rp[r0c];
+  for (int li = tid; li <= nloc; li += nt) lrp[li] = (int)(P.rp[r0c + li] - e0);
+  for (int li = tid; li < nloc; li += nt) {
+    const double dg = P.diag[r0 + li];
+    ldiag[li] = (T)dg;
+    sdiag[li] = (T)(P.two_sa * dg - P.two_ca);  // as the multi-kernel path stores it
+    lmask[li] = P.mask ? P.mask[r0 + li] : (1u << P.C) - 1u;
+  }
+  const int cnt = (int)(P.rp[r0c + nloc] - e0);
+  for (int e = tid; e < cnt; e += nt) {
+    lcol[e] = P.col[e0 + e];
+    lval[e] = (T)P.val[e0 + e];
+    sval[e] = (T)(P.two_sa * P.val[e0 + e]);
+  }
+  const int a0 = P.agg_ptr[h0c];
+  for (int lI = tid; lI <= nlocH; lI += nt) lap[lI] = P.agg_ptr[h0c + lI] - a0;
+  const int mc = P.agg_ptr[h0c + nlocH] - a0;
+  for (int e = tid; e < mc; e += nt) lam[e] = P.agg_mem[a0 + e];
+  for (int e = tid; e < nlocH * nH; e += nt) {
+    brows[e] = P.B[(size_t)h0c * nH + e];
+    abrows[e] = P.AB[(size_t)h0c * nH + e];
+  }
 }
 
 template <typename T, int kLeafThreads>
@@ -186,38 +241,17 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(const __grid_constant_
   __shared__ double s_sc[40];
   const long long t_start = clock64();
 
-  // ---- load: b (all rows), the owned rows of both operators, B, maps ----
-  for (int i = tid; i < n; i += kLeafThreads) {
-    vb[i] = P.b[i];
-    agg[i] = P.agg[i];
-  }
-  const int64_t e0 = P.rp[r0c];
-  for (int li = tid; li <= nloc; li += kLeafThreads) lrp[li] = (int)(P.rp[r0c + li] - e0);
-  for (int li = tid; li < nloc; li += kLeafThreads) {
-    const double dg = P.diag[r0 + li];
-    ldiag[li] = (T)dg;
-    sdiag[li] = (T)(P.two_sa * dg - P.two_ca);  // as the multi-kernel path stores it
-  }
+  // ---- load: this CTA's static image (one round of 16-byte asynchronous
+  // copies) and b (all rows) ----
   {
-    const int cnt = (int)(P.rp[r0c + nloc] - e0);
-    for (int e = tid; e < cnt; e += kLeafThreads) {
-      lcol[e] = P.col[e0 + e];
-      lval[e] = (T)P.val[e0 + e];
-      sval[e] = (T)(P.two_sa * P.val[e0 + e]);
-    }
+    const unsigned char *src = P.image + (size_t)rank * P.static_bytes;
+    for (unsigned o = (unsigned)tid * 16u; o < P.static_bytes; o += (unsigned)kLeafThreads * 16u)
+      cp_async16(sm + o, src + o);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int i = tid; i < n; i += kLeafThreads) vb[i] = P.b[i];
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
   unsigned *lmask = reinterpret_cast<unsigned *>(sm + P.off[A_MASK]);
-  for (int li = tid; li < nloc; li += kLeafThreads) lmask[li] = P.mask ? P.mask[r0 + li] : (1u << C) - 1u;
-  const int a0 = P.agg_ptr[h0c];
-  for (int lI = tid; lI <= nlocH; lI += kLeafThreads) lap[lI] = P.agg_ptr[h0c + lI] - a0;
-  {
-    const int mc = P.agg_ptr[h0c + nlocH] - a0;
-    for (int e = tid; e < mc; e += kLeafThreads) lam[e] = P.agg_mem[a0 + e];
-  }
-  for (int e = tid; e < nlocH * nH; e += kLeafThreads) {
-    brows[e] = P.B[(size_t)h0c * nH + e];
-    abrows[e] = P.AB[(size_t)h0c * nH + e];
-  }
   cl.sync();  // every CTA has started and loaded before any remote store
   if (P.prof && rank == 0 && tid == 0)
     atomicAdd(&P.prof[kLeafProfSlots - 2], (unsigned long long)(clock64() - t_start));
@@ -760,6 +794,14 @@ static amg_status prepare_t(amg_handle_s *h, int k0) {
     P.AB = AB;
     P.b = (const T *)L.b;
     P.x = (T *)L.x;
+    {
+      unsigned char *image = nullptr;
+      AMG_TRY(h->arena.alloc((void **)&image, (size_t)P.static_bytes * C));
+      k_leaf_image<T><<<C, 256, 0, h->stream>>>(P, image);
+      AMG_CUDA_TRY(cudaGetLastError());
+      ++h->launches;
+      P.image = image;
+    }
     P.prof = nullptr;
     if (const char *e = getenv("AMG_GB300_LEAF_PROFILE")) {
       if (e[0] == '1') {

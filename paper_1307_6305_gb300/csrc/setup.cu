@@ -280,14 +280,50 @@ __device__ __forceinline__ uint64_t edge_hash(uint64_t salt, int a, int b) {
   return splitmix64(salt ^ ((lo << 32) | hi));
 }
 
-// matching weight of each stored edge: |a_ij| / sqrt(a_ii a_jj)
-__global__ void k_strength(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ diag,
-                           double *__restrict__ s) {
+// matching weight of each stored edge: |a_ij| / sqrt(a_ii a_jj), correctly
+// rounded (the square root and the division are IEEE).  The square root and
+// division dominate on this part's FP64 pipe, so each undirected edge is
+// evaluated once: k_strength_upper takes the entries with j > i, and
+// k_strength_lower gives entry (i, j), j < i, the value of (j, i) whenever the
+// two stored values are equal bit for bit -- the formula then has identical
+// operands (a_ii a_jj = a_jj a_ii exactly) -- and evaluates it otherwise
+// (coarse operators with non-integer weights sum a_IJ and a_JI in different
+// orders).
+__device__ __forceinline__ double strength(double a, double di, double dj) { return -a / sqrt(di * dj); }
+
+__global__ void k_strength_upper(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const double *__restrict__ val, const double *__restrict__ diag,
+                                 double *__restrict__ s) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double di = diag[i];
-  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s[p] = -val[p] / sqrt(di * diag[col[p]]);
+  for (int64_t p = rp[i + 1] - 1; p >= rp[i]; --p) {  // columns ascending: the upper part is the tail
+    const int j = col[p];
+    if (j < i) break;
+    s[p] = strength(val[p], di, diag[j]);
+  }
+}
+
+__global__ void k_strength_lower(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const double *__restrict__ val, const double *__restrict__ diag,
+                                 double *__restrict__ s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double di = diag[i];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = col[p];
+    if (j > i) break;
+    // (j, i) in row j: the pattern is symmetric and rows are sorted
+    int64_t lo = rp[j], hi = rp[j + 1] - 1, t = -1;
+    while (lo <= hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      const int c = col[mid];
+      if (c == i) { t = mid; break; }
+      if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    const double a = val[p];
+    s[p] = (t >= 0 && val[t] == a) ? s[t] : strength(a, di, diag[j]);
+  }
 }
 
 __global__ void k_match_init(int n, int *mate) {
@@ -1118,7 +1154,9 @@ static amg_status coarsen_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuil
   double *s = nullptr;
   int *mate = nullptr;
   AMG_TRY(pool_alloc((void **)&s, sizeof(double) * (size_t)std::max<int64_t>(cur.A.nnz, 1), st));
-  k_strength<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
+  k_strength_upper<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
+  LAUNCH_CHECK(&h->launches);
+  k_strength_lower<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
   LAUNCH_CHECK(&h->launches);
   AMG_TRY(pool_alloc((void **)&mate, sizeof(int) * (size_t)std::max(n, 1), st));
   int *m0 = nullptr, *m1 = nullptr;

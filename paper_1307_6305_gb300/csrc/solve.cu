@@ -39,18 +39,45 @@ namespace amg {
 
 
 // r_H = P^T s; `flag`, when given, is the next level's inner-CG stop flag,
-// cleared here because the inner solve on r_H starts right after
+// cleared here because the inner solve on r_H starts right after.  One warp
+// per 32 consecutive aggregates: their member lists are one contiguous run
+// of mem[], read coalesced, and the gathered s values are staged in shared
+// memory (all loads of the warp in flight at once); each lane then adds its
+// aggregate's members in ascending order, as the one-thread-per-aggregate
+// form did (a warp whose run is longer than the buffer keeps that form).
+constexpr int kRestrictBuf = 384;  // staged members per warp (~12 per aggregate)
+constexpr int kRestrictAggs = kThreads;  // aggregates per block (32 per warp)
+
 template <typename T>
-__global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__restrict__ mem,
-                           const T *__restrict__ s, T *__restrict__ rH, double *flag) {
+__global__ void __launch_bounds__(kThreads) k_restrict(int nH, const int *__restrict__ ptr,
+                                                       const int *__restrict__ mem, const T *__restrict__ s,
+                                                       T *__restrict__ rH, double *flag) {
   pdl_sync();
+  __shared__ T sv[kThreads / 32][kRestrictBuf];
   if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nH) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I0 = blockIdx.x * kRestrictAggs + warp * 32;
+  if (I0 >= nH) return;  // uniform over the warp
+  const int I = I0 + lane, Iend = min(I0 + 32, nH);
+  const int lo = I < nH ? ptr[I] : 0, hi = I < nH ? ptr[I + 1] : 0;
+  const int run0 = __shfl_sync(0xffffffffu, lo, 0);
+  const int run1 = __shfl_sync(0xffffffffu, hi, Iend - I0 - 1);
+  const int total = run1 - run0;
   T acc = T(0);
+  if (total <= kRestrictBuf) {
+    T *buf = sv[warp];
 #pragma unroll 4
-  for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += s[mem[a]];
-  rH[I] = acc;
+    for (int e = lane; e < total; e += 32) buf[e] = s[mem[run0 + e]];
+    __syncwarp();
+    for (int a = lo; a < hi; ++a) acc += buf[a - run0];
+  } else {
+    for (int a = lo; a < hi; ++a) acc += s[mem[a]];
+  }
+  if (I < nH) rH[I] = acc;
+}
+
+static inline unsigned restrict_grid(int nH) {
+  return (unsigned)std::max(1, (nH + kRestrictAggs - 1) / kRestrictAggs);
 }
 
 template <typename T>
@@ -63,13 +90,34 @@ __global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__res
 }
 
 // x = u + P e_H (the prolonged coarse correction added to the pre-smoothed u)
+// four rows per thread with 16-byte loads and stores of agg, u and x when
+// all three start on a 16-byte boundary (the library's own buffers do; a
+// caller's vector passed to a single-step entry point may not), the tail of
+// n mod 4 rows and unaligned vectors one by one
 template <typename T>
 __global__ void k_prolong_set(int n, const int *__restrict__ agg, const T *__restrict__ eH,
                               const T *__restrict__ u, T *__restrict__ x) {
   pdl_sync();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  x[i] = u[i] + eH[agg[i]];
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= n) return;
+  const bool aligned =
+      ((reinterpret_cast<uintptr_t>(agg) | reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(x)) & 15u) == 0;
+  if (aligned && i0 + 3 < n) {
+    const int4 a = *reinterpret_cast<const int4 *>(agg + i0);
+    if constexpr (sizeof(T) == 8) {
+      const double2 u0 = *reinterpret_cast<const double2 *>(u + i0);
+      const double2 u1 = *reinterpret_cast<const double2 *>(u + i0 + 2);
+      const double2 x0 = make_double2(u0.x + eH[a.x], u0.y + eH[a.y]);
+      const double2 x1 = make_double2(u1.x + eH[a.z], u1.y + eH[a.w]);
+      *reinterpret_cast<double2 *>(x + i0) = x0;
+      *reinterpret_cast<double2 *>(x + i0 + 2) = x1;
+    } else {
+      const float4 uv = *reinterpret_cast<const float4 *>(u + i0);
+      *reinterpret_cast<float4 *>(x + i0) = make_float4(uv.x + eH[a.x], uv.y + eH[a.y], uv.z + eH[a.z], uv.w + eH[a.w]);
+    }
+    return;
+  }
+  for (int i = i0; i < min(n, i0 + 4); ++i) x[i] = u[i] + eH[agg[i]];
 }
 
 template <typename A, typename B>
@@ -188,18 +236,34 @@ __device__ __forceinline__ void reduce_and_finalize(const double (&acc)[ND], dou
   if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
-  if (warp == 0) {
+  // the last block folds the partials with all its threads (each loads at
+  // most gridDim / kThreads of them, in one round of independent loads),
+  // then a fixed tree: thread partials -> warp sums -> warps in order
+  double v[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) v[q] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] += __ldcg(&partial[b * kMaxDots + q]);
+  }
+  const bool active = (unsigned)(warp * 32) < gridDim.x;  // warps holding partials
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    const double t = active ? warp_sum(v[q]) : 0.0;
+    if (lane == 0) sh[warp][q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double sums[ND];
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
-      double v = 0.0;
-      for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(&partial[b * kMaxDots + q]);
-      sums[q] = warp_sum(v);
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) t += sh[w][q];
+      sums[q] = t;
     }
-    if (lane == 0) {
-      finalize(fin, sums, ND);
-      *ticket = 0u;
-    }
+    finalize(fin, sums, ND);
+    *ticket = 0u;
   }
 }
 
@@ -612,7 +676,7 @@ template <typename T>
 static amg_status prolong_residual(amg_handle_s *h, int k, const T *eH, const T *u, const T *r, T *x, T *s) {
   amg::Level &L = h->lv[k];
   if (h->prolong_split && L.wps == 1 && L.n >= kProlongSplitRows) {
-    AMG_TRY(plaunch(h, h->stream, k_prolong_set<T>, dim3(nblk(L.n)), dim3(kThreads), L.n, L.agg, eH, u, x));
+    AMG_TRY(plaunch(h, h->stream, k_prolong_set<T>, dim3(nblk((L.n + 3) / 4)), dim3(kThreads), L.n, L.agg, eH, u, x));
     SLAUNCH(h);
     return residual<T>(h, k, x, r, s);
   }
@@ -732,8 +796,8 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   T *s = (T *)L.s, *u = (T *)L.u;
   AMG_TRY(smooth<T>(h, k, r, u, false));
   AMG_TRY(residual<T>(h, k, u, r, s));
-  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b,
-                  N.scal + 24));
+  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s,
+                  (T *)N.b, N.scal + 24));
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else if (k + 1 == h->leaf_k) AMG_TRY(launch_leaf(h));
@@ -759,8 +823,8 @@ static amg_status amli_cycle(amg_handle_s *h, int k, const T *r, T *x) {
   T *s = (T *)L.s, *u = (T *)L.u;
   AMG_TRY(smooth<T>(h, k, r, u, false));
   AMG_TRY(residual<T>(h, k, u, r, s));
-  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s, (T *)N.b,
-                  (double *)nullptr));
+  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s,
+                  (T *)N.b, (double *)nullptr));
   SLAUNCH(h);
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else AMG_TRY(amli_coarse<T>(h, k + 1));
@@ -1237,8 +1301,8 @@ amg_status apply_smoother(amg_handle_s *h, int k, const double *r, double *x) {
 amg_status apply_restrict(amg_handle_s *h, int k, const double *s, double *rH) {
   amg::Level &L = h->lv[k];
   AMG_TRY(run_conv(h, s, L.n, rH, L.nH, false, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_restrict<float>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const float *)a, (float *)b, nullptr));
-    else AMG_TRY(plaunch(h, h->stream, k_restrict<double>, dim3(nblk(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const double *)a, (double *)b, nullptr));
+    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_restrict<float>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const float *)a, (float *)b, nullptr));
+    else AMG_TRY(plaunch(h, h->stream, k_restrict<double>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const double *)a, (double *)b, nullptr));
     SLAUNCH(h);
     return AMG_OK;
   }));
