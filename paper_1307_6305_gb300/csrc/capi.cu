@@ -1,5 +1,6 @@
 // capi.cu -- the C ABI declared in include/amg.h: argument checks, handle
 // lifecycle, host/device staging, introspection and measurement hooks.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -20,6 +21,40 @@ amg_status fail(amg_status code, const std::string &msg) {
   return code;
 }
 const std::string &thread_error() { return t_err; }
+
+static double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+NvtxPhase::NvtxPhase(cudaStream_t s) : st(s) {
+  const char *e = getenv("AMG_GB300_SETUP_PROFILE");
+  timed = e && e[0] == '1';
+  if (timed) {
+    cudaStreamSynchronize(st);
+    t0 = wall_ms();
+  }
+}
+
+void NvtxPhase::next(const char *name) {
+  if (timed) {
+    cudaStreamSynchronize(st);
+    const double t = wall_ms();
+    if (cur) fprintf(stderr, "setup phase %-62s %8.3f ms\n", cur, t - t0);
+    t0 = t;
+    cur = name;
+  }
+  if (open) nvtxRangePop();
+  nvtxRangePushA(name);
+  open = true;
+}
+
+NvtxPhase::~NvtxPhase() {
+  if (timed && cur) {
+    cudaStreamSynchronize(st);
+    fprintf(stderr, "setup phase %-62s %8.3f ms\n", cur, wall_ms() - t0);
+  }
+  if (open) nvtxRangePop();
+}
 
 // one library-owned stream-ordered pool per device; memory is kept in the
 // pool between setups (release threshold = max) so repeated setup/free
@@ -336,9 +371,12 @@ amg_status amg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
   if (!s) s = build_hierarchy(h, n, drp, dcol, dw, dd);
   for (void *p : tmp) pool_free(p, h->stream);
   {
-    const NvtxRange r("amg_setup: solve buffers, dense two-level operator, leaf kernel");
+    NvtxPhase ph(h->stream);
+    ph.next("amg_setup: solve buffers");
     if (!s) s = allocate_solve_buffers(h);
+    ph.next("amg_setup: dense two-level operator");
     if (!s) s = build_dense_two_level(h);
+    ph.next("amg_setup: leaf kernel data");
     if (!s) s = prepare_leaf(h);
   }
   if (!s) {

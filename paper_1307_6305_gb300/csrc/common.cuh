@@ -76,17 +76,19 @@ struct NvtxRange {
   NvtxRange &operator=(const NvtxRange &) = delete;
 };
 // consecutive phases of one function: next() closes the open range and opens
-// the next one; the destructor closes the last
+// the next one; the destructor closes the last.  With AMG_GB300_SETUP_PROFILE=1
+// the stream given at construction is synchronised at every phase boundary
+// and each phase's wall time is printed to stderr (diagnostics only: the
+// synchronisations change the timing they measure by a little).
 struct NvtxPhase {
   bool open = false;
-  void next(const char *name) {
-    if (open) nvtxRangePop();
-    nvtxRangePushA(name);
-    open = true;
-  }
-  ~NvtxPhase() {
-    if (open) nvtxRangePop();
-  }
+  bool timed = false;
+  cudaStream_t st = nullptr;
+  const char *cur = nullptr;
+  double t0 = 0.0;
+  explicit NvtxPhase(cudaStream_t s = nullptr);
+  void next(const char *name);
+  ~NvtxPhase();
 };
 
 // ---------------------------------------------------------------------------
@@ -162,6 +164,10 @@ struct Level {
   int32_t *agg = nullptr;
   int32_t *agg_ptr = nullptr;
   int32_t *agg_mem = nullptr;
+  // matching hierarchies: the members again as a fixed-width table, column
+  // major ([memw_width][nH], ascending, -1 after the last), for the restriction
+  int32_t *memw = nullptr;
+  int memw_width = 0;
   // smoother: q_m on [lam0, lam1] in the Chebyshev basis of t(x)
   double lam0 = 0, lam1 = 0;
   double coef[kMaxDegree + 1] = {};

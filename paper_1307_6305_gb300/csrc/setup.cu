@@ -280,50 +280,14 @@ __device__ __forceinline__ uint64_t edge_hash(uint64_t salt, int a, int b) {
   return splitmix64(salt ^ ((lo << 32) | hi));
 }
 
-// matching weight of each stored edge: |a_ij| / sqrt(a_ii a_jj), correctly
-// rounded (the square root and the division are IEEE).  The square root and
-// division dominate on this part's FP64 pipe, so each undirected edge is
-// evaluated once: k_strength_upper takes the entries with j > i, and
-// k_strength_lower gives entry (i, j), j < i, the value of (j, i) whenever the
-// two stored values are equal bit for bit -- the formula then has identical
-// operands (a_ii a_jj = a_jj a_ii exactly) -- and evaluates it otherwise
-// (coarse operators with non-integer weights sum a_IJ and a_JI in different
-// orders).
-__device__ __forceinline__ double strength(double a, double di, double dj) { return -a / sqrt(di * dj); }
-
-__global__ void k_strength_upper(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                 const double *__restrict__ val, const double *__restrict__ diag,
-                                 double *__restrict__ s) {
+// matching weight of each stored edge: |a_ij| / sqrt(a_ii a_jj)
+__global__ void k_strength(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ diag,
+                           double *__restrict__ s) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double di = diag[i];
-  for (int64_t p = rp[i + 1] - 1; p >= rp[i]; --p) {  // columns ascending: the upper part is the tail
-    const int j = col[p];
-    if (j < i) break;
-    s[p] = strength(val[p], di, diag[j]);
-  }
-}
-
-__global__ void k_strength_lower(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                 const double *__restrict__ val, const double *__restrict__ diag,
-                                 double *__restrict__ s) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double di = diag[i];
-  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-    const int j = col[p];
-    if (j > i) break;
-    // (j, i) in row j: the pattern is symmetric and rows are sorted
-    int64_t lo = rp[j], hi = rp[j + 1] - 1, t = -1;
-    while (lo <= hi) {
-      const int64_t mid = lo + (hi - lo) / 2;
-      const int c = col[mid];
-      if (c == i) { t = mid; break; }
-      if (c < i) lo = mid + 1; else hi = mid - 1;
-    }
-    const double a = val[p];
-    s[p] = (t >= 0 && val[t] == a) ? s[t] : strength(a, di, diag[j]);
-  }
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s[p] = -val[p] / sqrt(di * diag[col[p]]);
 }
 
 __global__ void k_match_init(int n, int *mate) {
@@ -1154,9 +1118,7 @@ static amg_status coarsen_pass(amg_handle_s *h, const LevelBuild &cur, LevelBuil
   double *s = nullptr;
   int *mate = nullptr;
   AMG_TRY(pool_alloc((void **)&s, sizeof(double) * (size_t)std::max<int64_t>(cur.A.nnz, 1), st));
-  k_strength_upper<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
-  LAUNCH_CHECK(&h->launches);
-  k_strength_lower<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
+  k_strength<<<nb, 256, 0, st>>>(n, cur.A.rowptr, cur.A.col, cur.A.val, cur.diag, s);
   LAUNCH_CHECK(&h->launches);
   AMG_TRY(pool_alloc((void **)&mate, sizeof(int) * (size_t)std::max(n, 1), st));
   int *m0 = nullptr, *m1 = nullptr;
@@ -1430,6 +1392,15 @@ static amg_status build_sell_all(amg_handle_s *h, bool want32) {
   return AMG_OK;
 }
 
+// member k of aggregate I at memw[k * nH + I] (k < W), -1 after the last
+__global__ void k_agg_table(int nH, int W, const int *__restrict__ ptr, const int *__restrict__ mem,
+                            int *__restrict__ memw) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  const int a0 = ptr[I], cnt = ptr[I + 1] - a0;
+  for (int k = 0; k < W; ++k) memw[(size_t)k * nH + I] = k < cnt ? mem[a0 + k] : -1;
+}
+
 static amg_status build_agg_lists(amg_handle_s *h, amg::Level &L) {
   cudaStream_t st = h->stream;
   int *cnt = nullptr, *fill = nullptr;
@@ -1447,6 +1418,13 @@ static amg_status build_agg_lists(amg_handle_s *h, amg::Level &L) {
   AMG_TRY(sort_members(h, L.n, L.nH, L.agg_ptr, L.agg_mem));
   pool_free(cnt, st);
   pool_free(fill, st);
+  // p matching passes make aggregates of at most 2^p members
+  if (h->opt.aggregation == AMG_AGG_MATCHING && h->opt.passes >= 1 && h->opt.passes <= 3) {
+    L.memw_width = 1 << h->opt.passes;
+    AMG_TRY(alloc_persist(h, (void **)&L.memw, sizeof(int32_t) * (size_t)L.memw_width * (size_t)std::max(L.nH, 1)));
+    k_agg_table<<<blocks_for(L.nH, 256), 256, 0, st>>>(L.nH, L.memw_width, L.agg_ptr, L.agg_mem, L.memw);
+    LAUNCH_CHECK(&h->launches);
+  }
   return AMG_OK;
 }
 
@@ -1508,7 +1486,7 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
   cudaStream_t st = h->stream;
   const int n = (int)n64;
   const unsigned nb = blocks_for(n, 256);
-  NvtxPhase phase;
+  NvtxPhase phase(st);
   phase.next("amg_setup: validation");
   // ---- validation (order of the C ABI's error list) ----
   unsigned *flags = nullptr;
@@ -1723,10 +1701,11 @@ amg_status build_hierarchy(amg_handle_s *h, int64_t n64, const int64_t *rowptr, 
     h->amli_sA = 2.0 / (1.0 - al);
     h->amli_sB = (1.0 + al) / (1.0 - al);
   }
-  phase.next("amg_setup: solve layouts and coarsest pseudo-inverse");
+  phase.next("amg_setup: solve layouts (SELL-32)");
   // ---- solve layouts ----
   const bool want32 = h->opt.precision == AMG_PREC_FP32;
   AMG_TRY(build_sell_all(h, want32));
+  phase.next("amg_setup: coarsest pseudo-inverse");
   AMG_TRY(build_coarsest(h));
   // complexities (Sec. 4)
   double gs = 0, os = 0;

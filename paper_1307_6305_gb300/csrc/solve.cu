@@ -39,46 +39,46 @@ namespace amg {
 
 
 // r_H = P^T s; `flag`, when given, is the next level's inner-CG stop flag,
-// cleared here because the inner solve on r_H starts right after.  One warp
-// per 32 consecutive aggregates: their member lists are one contiguous run
-// of mem[], read coalesced, and the gathered s values are staged in shared
-// memory (all loads of the warp in flight at once); each lane then adds its
-// aggregate's members in ascending order, as the one-thread-per-aggregate
-// form did (a warp whose run is longer than the buffer keeps that form).
-constexpr int kRestrictBuf = 384;  // staged members per warp (~12 per aggregate)
-constexpr int kRestrictAggs = kThreads;  // aggregates per block (32 per warp)
-
+// cleared here because the inner solve on r_H starts right after.  One
+// thread per aggregate, members in ascending order.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_restrict(int nH, const int *__restrict__ ptr,
-                                                       const int *__restrict__ mem, const T *__restrict__ s,
-                                                       T *__restrict__ rH, double *flag) {
+__global__ void k_restrict(int nH, const int *__restrict__ ptr, const int *__restrict__ mem,
+                           const T *__restrict__ s, T *__restrict__ rH, double *flag) {
   pdl_sync();
-  __shared__ T sv[kThreads / 32][kRestrictBuf];
   if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int I0 = blockIdx.x * kRestrictAggs + warp * 32;
-  if (I0 >= nH) return;  // uniform over the warp
-  const int I = I0 + lane, Iend = min(I0 + 32, nH);
-  const int lo = I < nH ? ptr[I] : 0, hi = I < nH ? ptr[I + 1] : 0;
-  const int run0 = __shfl_sync(0xffffffffu, lo, 0);
-  const int run1 = __shfl_sync(0xffffffffu, hi, Iend - I0 - 1);
-  const int total = run1 - run0;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
   T acc = T(0);
-  if (total <= kRestrictBuf) {
-    T *buf = sv[warp];
 #pragma unroll 4
-    for (int e = lane; e < total; e += 32) buf[e] = s[mem[run0 + e]];
-    __syncwarp();
-    for (int a = lo; a < hi; ++a) acc += buf[a - run0];
-  } else {
-    for (int a = lo; a < hi; ++a) acc += s[mem[a]];
-  }
-  if (I < nH) rH[I] = acc;
+  for (int a = ptr[I]; a < ptr[I + 1]; ++a) acc += s[mem[a]];
+  rH[I] = acc;
 }
 
-static inline unsigned restrict_grid(int nH) {
-  return (unsigned)std::max(1, (nH + kRestrictAggs - 1) / kRestrictAggs);
+// The same with the member table of a matching hierarchy: at most W = 2^passes
+// members per aggregate, stored column-major (member k of aggregate I at
+// memw[k * nH + I], ascending, -1 after the last), so a thread issues its W
+// member loads at once, coalesced across the warp, with no row-pointer load
+// before them; the sum is taken in the same order as k_restrict.
+template <typename T, int W>
+__global__ void k_restrict_w(int nH, const int *__restrict__ memw, const T *__restrict__ s, T *__restrict__ rH,
+                             double *flag) {
+  pdl_sync();
+  if (flag && blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nH) return;
+  int m[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) m[k] = memw[(size_t)k * nH + I];
+  T v[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) v[k] = m[k] >= 0 ? s[m[k]] : T(0);
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (m[k] >= 0) acc += v[k];
+  rH[I] = acc;
 }
+
 
 template <typename T>
 __global__ void k_prolong_add(int n, const int *__restrict__ agg, const T *__restrict__ eH,
@@ -524,6 +524,22 @@ SellView<float> smoother_view<float>(const amg::Level &L) {
   return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32, L.stream};
 }
 
+// r_H = P^T s on level k (the fixed-width member table when the level has one)
+template <typename T>
+static amg_status restrict_to(amg_handle_s *h, int k, const T *s, T *rH, double *flag) {
+  amg::Level &L = h->lv[k];
+  cudaStream_t st = h->stream;
+  const dim3 g(nblk(L.nH));
+  switch (L.memw ? L.memw_width : 0) {
+    case 2: AMG_TRY(plaunch(h, st, k_restrict_w<T, 2>, g, dim3(kThreads), L.nH, L.memw, s, rH, flag)); break;
+    case 4: AMG_TRY(plaunch(h, st, k_restrict_w<T, 4>, g, dim3(kThreads), L.nH, L.memw, s, rH, flag)); break;
+    case 8: AMG_TRY(plaunch(h, st, k_restrict_w<T, 8>, g, dim3(kThreads), L.nH, L.memw, s, rH, flag)); break;
+    default: AMG_TRY(plaunch(h, st, k_restrict<T>, g, dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s, rH, flag));
+  }
+  SLAUNCH(h);
+  return AMG_OK;
+}
+
 template <typename T>
 static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin fin) {
   const unsigned g = red_grid(n);
@@ -796,9 +812,7 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   T *s = (T *)L.s, *u = (T *)L.u;
   AMG_TRY(smooth<T>(h, k, r, u, false));
   AMG_TRY(residual<T>(h, k, u, r, s));
-  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s,
-                  (T *)N.b, N.scal + 24));
-  SLAUNCH(h);
+  AMG_TRY(restrict_to<T>(h, k, s, (T *)N.b, N.scal + 24));
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else if (k + 1 == h->leaf_k) AMG_TRY(launch_leaf(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
@@ -823,9 +837,7 @@ static amg_status amli_cycle(amg_handle_s *h, int k, const T *r, T *x) {
   T *s = (T *)L.s, *u = (T *)L.u;
   AMG_TRY(smooth<T>(h, k, r, u, false));
   AMG_TRY(residual<T>(h, k, u, r, s));
-  AMG_TRY(plaunch(h, st, k_restrict<T>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, s,
-                  (T *)N.b, (double *)nullptr));
-  SLAUNCH(h);
+  AMG_TRY(restrict_to<T>(h, k, s, (T *)N.b, (double *)nullptr));
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else AMG_TRY(amli_coarse<T>(h, k + 1));
   AMG_TRY(prolong_residual<T>(h, k, (const T *)N.x, u, r, x, s));
@@ -965,10 +977,22 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // policy (A/B timing of the streaming loads)
   const char *stream_env = getenv("AMG_GB300_STREAM");
   const bool stream_ok = !(stream_env && stream_env[0] == '0');
+  // AMG_GB300_WPS=w0,w1,...: warps per slice of levels 0, 1, ... (1, 2, 4 or
+  // 8; A/B timing), the rule above for levels not listed
+  std::vector<int> wps_force;
+  if (const char *e = getenv("AMG_GB300_WPS")) {
+    for (const char *c = e; *c;) {
+      const int v = atoi(c);
+      wps_force.push_back((v == 1 || v == 2 || v == 4 || v == 8) ? v : 0);
+      while (*c && *c != ',') ++c;
+      if (*c == ',') ++c;
+    }
+  }
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     const size_t n = (size_t)std::max(V.n, 1);
     V.wps = split ? choose_wps(V.n, per_sm) : 1;
+    if (k < (int)wps_force.size() && wps_force[k] > 0) V.wps = wps_force[k];
     // one pass over the level's stored values and columns is at least the
     // size of L2: stream it (the vectors and the coarser levels stay cached)
     V.stream = stream_ok && (double)V.S.stored * (double)(es + 4) >= kStreamMatrixBytes;
@@ -1301,10 +1325,8 @@ amg_status apply_smoother(amg_handle_s *h, int k, const double *r, double *x) {
 amg_status apply_restrict(amg_handle_s *h, int k, const double *s, double *rH) {
   amg::Level &L = h->lv[k];
   AMG_TRY(run_conv(h, s, L.n, rH, L.nH, false, [&](const void *a, void *b) -> amg_status {
-    if (f32(h)) AMG_TRY(plaunch(h, h->stream, k_restrict<float>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const float *)a, (float *)b, nullptr));
-    else AMG_TRY(plaunch(h, h->stream, k_restrict<double>, dim3(restrict_grid(L.nH)), dim3(kThreads), L.nH, L.agg_ptr, L.agg_mem, (const double *)a, (double *)b, nullptr));
-    SLAUNCH(h);
-    return AMG_OK;
+    if (f32(h)) return restrict_to<float>(h, k, (const float *)a, (float *)b, nullptr);
+    return restrict_to<double>(h, k, (const double *)a, (double *)b, nullptr);
   }));
   AMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
   return AMG_OK;
