@@ -298,18 +298,20 @@ def kernel_roofline(amg, P, opts, sp, precision, steps=2):
     timing nodes."""
     import ctypes as C
 
-    nl_tot, ms_tot, bpl = 0, 0.0, 0.0
+    acc = {kind: [0, 0.0, 0.0] for kind in (0, 1, 2)}   # launches, ms, bytes per launch
     for _ in range(steps):
         st, h = amg.amg_setup(P.g.n, P.rp, P.col, P.w, P.d, opts, amg.AMG_MEM_DEVICE, sp)
         assert st == 0, amg.amg_last_error(None)
         amg.lib().amg_kernel_timing(h, 1)
         assert amg.amg_solve(h, P.bd, P.xd, P.nrhs, P.g.n, 1e-8, None) == 0
-        nl, ms, b = C.c_int64(), C.c_double(), C.c_double()
-        amg.lib().amg_kernel_timing_read(h, C.byref(nl), C.byref(ms), C.byref(b))
-        nl_tot += nl.value
-        ms_tot += ms.value
-        bpl = b.value
+        for kind in acc:
+            nl, ms, b = C.c_int64(), C.c_double(), C.c_double()
+            amg.lib().amg_kernel_timing_read_kind(h, kind, C.byref(nl), C.byref(ms), C.byref(b))
+            acc[kind][0] += nl.value
+            acc[kind][1] += ms.value
+            acc[kind][2] = b.value
         amg.amg_free(h)
+    nl_tot, ms_tot, bpl = acc[0]
     if nl_tot == 0:
         return None
     avg_ms = ms_tot / nl_tot
@@ -335,6 +337,17 @@ def kernel_roofline(amg, P, opts, sp, precision, steps=2):
             roof["alu_view"] = alu_view
     roof.update({"kernel": kname, "launches_timed": nl_tot, "avg_launch_us": avg_ms * 1e3,
                  "algorithmic_bytes_per_launch": bpl, "algorithmic_flops_per_launch": flops})
+    # the level-0 transfer kernels, timed in the same pass
+    tr = {}
+    for kind, name in ((1, "restriction r_H = P^T s (level 0)"), (2, "prolongation x = u + P e_H (level 0)")):
+        nl, ms, b = acc[kind]
+        if nl:
+            us = ms / nl * 1e3
+            gb = b / (us * 1e-6) / 1e9
+            tr["restrict" if kind == 1 else "prolong"] = {
+                "kernel": name, "launches_timed": nl, "avg_launch_us": us, "algorithmic_bytes_per_launch": b,
+                "achieved": gb, "peak": hbm_peak, "unit": "GB/s", "frac": gb / hbm_peak}
+    roof["transfers"] = tr or None
     return roof
 
 

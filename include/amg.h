@@ -352,8 +352,9 @@ void amg_server_destroy(amg_server s);
 /* Measurement hooks.                                                      */
 /* ---------------------------------------------------------------------- */
 
-/* Enable (1) or disable (0) CUDA-event timing of every launch of the fused
- * smoother-step kernel on level 0 (the dominant kernel) during amg_solve;
+/* Enable (1) or disable (0) CUDA-event timing, during amg_solve, of every
+ * launch on level 0 of the fused smoother-step kernel (the dominant kernel),
+ * of the restriction and of the prolongation when it runs as its own kernel;
  * enabling resets the accumulators. */
 amg_status amg_kernel_timing(amg_handle h, int enable);
 /* Accumulated launches, total device milliseconds and the algorithmic bytes
@@ -362,6 +363,12 @@ amg_status amg_kernel_timing(amg_handle h, int enable);
  * x read and written once; v = 8, or 4 for AMG_PREC_FP32). */
 amg_status amg_kernel_timing_read(amg_handle h, int64_t *launches, double *total_ms,
                                   double *bytes_per_launch);
+/* The same for `kind` 0 (the smoother step, as amg_kernel_timing_read), 1
+ * (the level-0 restriction r_H = P^T s of Eq. (coarse); bytes: its member
+ * lists, s and r_H once) or 2 (the level-0 prolongation x = u + P e_H;
+ * bytes: n (4 + 2 v) + n_H v).  AMG_ERR_INVALID_ARG for another kind. */
+amg_status amg_kernel_timing_read_kind(amg_handle h, int kind, int64_t *launches, double *total_ms,
+                                       double *bytes_per_launch);
 /* Number of kernel launches issued by the last amg_setup/amg_solve on h. */
 int64_t amg_launch_count(amg_handle h);
 

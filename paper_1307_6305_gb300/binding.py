@@ -43,7 +43,7 @@ SYMBOLS = [
     "amg_num_levels", "amg_level_n", "amg_level_nnz", "amg_level_csr", "amg_level_agg",
     "amg_level_smoother", "amg_apply_spmv", "amg_apply_smoother", "amg_apply_restrict",
     "amg_apply_prolong_add", "amg_apply_coarse_solve", "amg_apply_kcycle", "amg_match", "amg_match_noalloc",
-    "amg_kernel_timing", "amg_kernel_timing_read", "amg_launch_count",
+    "amg_kernel_timing", "amg_kernel_timing_read", "amg_kernel_timing_read_kind", "amg_launch_count",
     "amg_server_create", "amg_server_add_graph", "amg_server_submit", "amg_server_poll", "amg_server_wait",
     "amg_server_stats", "amg_server_destroy",
 ]
@@ -121,6 +121,8 @@ def lib(build_if_missing: bool = True):
             L.amg_match_noalloc.argtypes = [I64, P, P, P, C.c_uint64, P, P, C.POINTER(I64), C.POINTER(I), P]
             L.amg_kernel_timing.argtypes = [P, I]
             L.amg_kernel_timing_read.argtypes = [P, C.POINTER(I64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.amg_kernel_timing_read_kind.argtypes = [P, I, C.POINTER(I64), C.POINTER(C.c_double),
+                                                      C.POINTER(C.c_double)]
             L.amg_launch_count.argtypes = [P]
             L.amg_launch_count.restype = I64
             L.amg_server_create.argtypes = [C.POINTER(amg_server_config), C.POINTER(C.c_void_p)]

@@ -621,28 +621,46 @@ amg_status amg_match(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
 amg_status amg_kernel_timing(amg_handle h, int enable) {
   if (!h) return fail(AMG_ERR_INVALID_ARG, "handle is NULL");
   h->timing.enabled = enable != 0;
-  h->timing.launches = 0;
-  h->timing.total_ms = 0.0;
+  for (int k = 0; k < kTimedKinds; ++k) {
+    h->timing.launches[k] = 0;
+    h->timing.total_ms[k] = 0.0;
+  }
   h->timing.used = 0;
+  return AMG_OK;
+}
+
+amg_status amg_kernel_timing_read_kind(amg_handle h, int kind, int64_t *launches, double *total_ms,
+                                       double *bytes_per_launch) {
+  if (!h) return fail(AMG_ERR_INVALID_ARG, "handle is NULL");
+  if (kind < 0 || kind >= kTimedKinds) return record(h, fail(AMG_ERR_INVALID_ARG, "kind must be 0, 1 or 2"));
+  if (launches) *launches = h->timing.launches[kind];
+  if (total_ms) *total_ms = h->timing.total_ms[kind];
+  if (bytes_per_launch) {
+    const amg::Level &L = h->lv[0];
+    const bool f32 = h->opt.precision == AMG_PREC_FP32;
+    const double vs = f32 ? 4.0 : 8.0;
+    const double nnz = (double)L.A.nnz, n = (double)L.n, nH = (double)L.nH;
+    if (kind == 0) {
+      // one fused smoother step on level 0: the stored SELL entries (value +
+      // column index) and diagonal once, the gathered vector T_j once, and
+      // the row-wise vectors T_{j-1} (read), T_{j+1} (write), x (read + write)
+      *bytes_per_launch = nnz * (vs + 4.0) + (double)(L.S.nslices + 1) * 8.0 + n * vs * 6.0;
+    } else if (kind == 1) {
+      // r_H = P^T s: the member lists (the fixed-width table, or offsets +
+      // members), s once, r_H written
+      const double lists = L.memw ? (double)L.memw_width * nH * 4.0 : (nH + 1.0) * 4.0 + n * 4.0;
+      *bytes_per_launch = lists + n * vs + nH * vs;
+    } else {
+      // x = u + P e_H: agg and u read, x written, e_H read once
+      *bytes_per_launch = n * (4.0 + 2.0 * vs) + nH * vs;
+    }
+  }
   return AMG_OK;
 }
 
 amg_status amg_kernel_timing_read(amg_handle h, int64_t *launches, double *total_ms,
                                   double *bytes_per_launch) {
-  if (!h) return fail(AMG_ERR_INVALID_ARG, "handle is NULL");
-  if (launches) *launches = h->timing.launches;
-  if (total_ms) *total_ms = h->timing.total_ms;
-  if (bytes_per_launch) {
-    // one fused smoother step on level 0: the stored SELL entries (value +
-    // column index) and diagonal once, the gathered vector T_j once, and the
-    // row-wise vectors T_{j-1} (read), T_{j+1} (write), x (read + write)
-    const amg::Level &L = h->lv[0];
-    const bool f32 = h->opt.precision == AMG_PREC_FP32;
-    const double vs = f32 ? 4.0 : 8.0;
-    const double nnz = (double)L.A.nnz, n = (double)L.n;
-    *bytes_per_launch = nnz * (vs + 4.0) + (double)(L.S.nslices + 1) * 8.0 + n * vs * 6.0;
-  }
-  return AMG_OK;
+  return amg_kernel_timing_read_kind(h, 0, launches, total_ms, bytes_per_launch);
 }
 
 int64_t amg_launch_count(amg_handle h) { return h ? h->launches : 0; }

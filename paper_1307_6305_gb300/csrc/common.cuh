@@ -32,7 +32,8 @@ constexpr int kMaxDegree = 16;    // largest smoother degree
 constexpr int kMaxInner = 8;      // largest nu
 constexpr int kMaxWindow = 16;    // largest outer restart window
 constexpr int kMaxDots = 8;       // dots per fused reduction
-constexpr int kRedBlocks = 608;   // partial sums per reduction = 4 x 152 SMs
+constexpr int kRedBlocks = 608;   // smallest partials buffer of a reduction = 4 x 152 SMs
+constexpr int kRedElems = 4;      // elements per thread of a streaming reduction
 constexpr int kMaxBatchServe = 32; // largest server batch (the widest block)
 constexpr int kStallMaxCoarse = 4096;
 constexpr double kStallRatio = 0.95;
@@ -190,16 +191,20 @@ struct BatchLevel {
 // fused reduction state (deterministic two-stage: per-block partials, last
 // block folds them in block order)
 struct RedState {
-  double *partial = nullptr;   // [kRedBlocks * kMaxDots]
+  double *partial = nullptr;   // [red_cap * kMaxDots]
   unsigned int *ticket = nullptr;
 };
 
+// CUDA-event timing of chosen level-0 launches (amg_kernel_timing): kind 0
+// the fused smoother step, 1 the restriction, 2 the prolongation
+constexpr int kTimedKinds = 3;
 struct Timing {
   bool enabled = false;
   std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> kind;        // kind of each pair (indexed by pair)
   size_t used = 0;
-  int64_t launches = 0;
-  double total_ms = 0;
+  int64_t launches[kTimedKinds] = {};
+  double total_ms[kTimedKinds] = {};
 };
 
 struct Options {
@@ -219,6 +224,7 @@ struct amg_handle_s {
   std::vector<amg::Level> lv;
   amg::Arena arena;
   amg::RedState red;
+  int red_cap = amg::kRedBlocks;     // blocks the reduction partials buffer holds
   // coarsest pseudo-inverse
   int nc = 0;
   double *Z = nullptr;

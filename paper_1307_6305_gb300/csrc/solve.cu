@@ -242,6 +242,7 @@ __device__ __forceinline__ void reduce_and_finalize(const double (&acc)[ND], dou
   double v[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) v[q] = 0.0;
+#pragma unroll 4
   for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads) {
 #pragma unroll
     for (int q = 0; q < ND; ++q) v[q] += __ldcg(&partial[b * kMaxDots + q]);
@@ -274,11 +275,21 @@ __global__ void __launch_bounds__(kThreads) k_dots(int64_t n, DotSpec<T> spec, d
   double acc[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) acc[q] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  // kRedElems elements per thread and trip, kThreads apart (coalesced, all
+  // loads of a trip in flight together); a grid of n / (kThreads kRedElems)
+  // blocks makes one trip
+  for (int64_t base = (int64_t)blockIdx.x * (kThreads * kRedElems) + threadIdx.x; base < n;
+       base += (int64_t)gridDim.x * (kThreads * kRedElems)) {
 #pragma unroll
-    for (int q = 0; q < ND; ++q) {
-      const double a = (double)spec.a[q][i];
-      acc[q] += spec.b[q] ? a * (double)spec.b[q][i] : a;
+    for (int u = 0; u < kRedElems; ++u) {
+      const int64_t i = base + (int64_t)u * kThreads;
+      if (i < n) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+          const double a = (double)spec.a[q][i];
+          acc[q] += spec.b[q] ? a * (double)spec.b[q][i] : a;
+        }
+      }
     }
   }
   reduce_and_finalize<ND>(acc, partial, ticket, fin);
@@ -327,17 +338,24 @@ __global__ void __launch_bounds__(kThreads) k_orth_dots(int64_t n, T *D, T *W, D
                                                         double *partial, unsigned *ticket, Fin fin) {
   pdl_sync();
   double acc[2] = {0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T d = D[i], w = W[i];
-    for (int l = 0; l < prev.nd; ++l) {
-      const T bl = (T)beta[l];
-      d -= bl * prev.a[l][i];
-      w -= bl * prev.b[l][i];
+  for (int64_t base = (int64_t)blockIdx.x * (kThreads * kRedElems) + threadIdx.x; base < n;
+       base += (int64_t)gridDim.x * (kThreads * kRedElems)) {
+#pragma unroll
+    for (int u = 0; u < kRedElems; ++u) {
+      const int64_t i = base + (int64_t)u * kThreads;
+      if (i < n) {
+        T d = D[i], w = W[i];
+        for (int l = 0; l < prev.nd; ++l) {
+          const T bl = (T)beta[l];
+          d -= bl * prev.a[l][i];
+          w -= bl * prev.b[l][i];
+        }
+        D[i] = d;
+        W[i] = w;
+        acc[0] += (double)d * (double)w;
+        acc[1] += (double)d * (double)rin[i];
+      }
     }
-    D[i] = d;
-    W[i] = w;
-    acc[0] += (double)d * (double)w;
-    acc[1] += (double)d * (double)rin[i];
   }
   reduce_and_finalize<2>(acc, partial, ticket, fin);
 }
@@ -421,11 +439,18 @@ __global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const doub
   pdl_sync();
   double acc[1] = {0.0};
   const double a = sc[32];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(a, d[i], x[i]);
-    const double ri = fma(-a, q[i], r[i]);
-    r[i] = ri;
-    acc[0] += ri * ri;
+  for (int64_t base = (int64_t)blockIdx.x * (kThreads * kRedElems) + threadIdx.x; base < n;
+       base += (int64_t)gridDim.x * (kThreads * kRedElems)) {
+#pragma unroll
+    for (int u = 0; u < kRedElems; ++u) {
+      const int64_t i = base + (int64_t)u * kThreads;
+      if (i < n) {
+        x[i] = fma(a, d[i], x[i]);
+        const double ri = fma(-a, q[i], r[i]);
+        r[i] = ri;
+        acc[0] += ri * ri;
+      }
+    }
   }
   reduce_and_finalize<1>(acc, partial, ticket, fin);
 }
@@ -469,8 +494,11 @@ __global__ void k_identity(int n, double *__restrict__ X) {
 
 // ---------------------------------------------------------------------------
 // host side
-static inline unsigned red_grid(int64_t n) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kThreads - 1) / kThreads));
+// blocks of a streaming reduction over n elements: one trip of kRedElems
+// elements per thread, capped by the partials buffer
+static inline unsigned red_grid(const amg_handle_s *h, int64_t n) {
+  const int64_t per = (int64_t)kThreads * kRedElems;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->red_cap, (n + per - 1) / per));
 }
 
 // blocks of the SELL kernels: (slices x WPS) warps, kThreads / 32 per block
@@ -542,7 +570,7 @@ static amg_status restrict_to(amg_handle_s *h, int k, const T *s, T *rH, double 
 
 template <typename T>
 static amg_status dots(amg_handle_s *h, int64_t n, const DotSpec<T> &spec, Fin fin) {
-  const unsigned g = red_grid(n);
+  const unsigned g = red_grid(h, n);
   double *P = h->red.partial;
   unsigned *tk = h->red.ticket;
   cudaStream_t st = h->stream;
@@ -568,7 +596,7 @@ static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotS
   cudaStream_t st = h->stream;
   const SellView<T> A = view<T>(L);
   if (L.wps > 1 && spec.nd <= 2) {  // the inner solve's shapes (nu = 2) take the split form
-    const unsigned g = std::min<unsigned>(kRedBlocks, sell_grid(L.n, L.wps));
+    const unsigned g = std::min<unsigned>((unsigned)h->red_cap, sell_grid(L.n, L.wps));
     AMG_TRY(with_wps(L.wps, [&](auto W) {
       constexpr int wp = decltype(W)::value;
       if (spec.nd == 1) return plaunch(h, st, k_spmv_dots<T, 1, wp>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin);
@@ -577,7 +605,8 @@ static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotS
     SLAUNCH(h);
     return AMG_OK;
   }
-  const unsigned g = red_grid(L.n);
+  // one row per thread: the SELL grid (the partials buffer holds it)
+  const unsigned g = std::min<unsigned>((unsigned)h->red_cap, sell_grid(L.n, 1));
   switch (spec.nd) {
     case 1: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 1, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
     case 2: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 2, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
@@ -592,12 +621,18 @@ static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotS
   return AMG_OK;
 }
 
-static amg_status timing_record(amg_handle_s *h, cudaEvent_t *ev) {
+// record the next timing event; `kind` is stored with the first event of a pair
+static amg_status timing_record(amg_handle_s *h, cudaEvent_t *ev, int kind = 0) {
   Timing &tm = h->timing;
   if (tm.used >= tm.ev.size()) {
     cudaEvent_t e;
     AMG_CUDA_TRY(cudaEventCreate(&e));
     tm.ev.push_back(e);
+  }
+  if (tm.used % 2 == 0) {
+    const size_t pair = tm.used / 2;
+    if (tm.kind.size() <= pair) tm.kind.resize(pair + 1, 0);
+    tm.kind[pair] = kind;
   }
   *ev = tm.ev[tm.used++];
   if (h->capturing) AMG_CUDA_TRY(cudaEventRecordWithFlags(*ev, h->stream, cudaEventRecordExternal));
@@ -611,8 +646,9 @@ static amg_status timing_accumulate(amg_handle_s *h, size_t count) {
   for (size_t i = 0; i + 1 < count; i += 2) {
     float ms = 0.f;
     AMG_CUDA_TRY(cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]));
-    tm.total_ms += ms;
-    ++tm.launches;
+    const int k = tm.kind[i / 2];
+    tm.total_ms[k] += ms;
+    ++tm.launches[k];
   }
   return AMG_OK;
 }
@@ -692,8 +728,12 @@ template <typename T>
 static amg_status prolong_residual(amg_handle_s *h, int k, const T *eH, const T *u, const T *r, T *x, T *s) {
   amg::Level &L = h->lv[k];
   if (h->prolong_split && L.wps == 1 && L.n >= kProlongSplitRows) {
+    const bool timed = h->timing.enabled && k == 0;
+    cudaEvent_t e0, e1;
+    if (timed) AMG_TRY(timing_record(h, &e0, 2));
     AMG_TRY(plaunch(h, h->stream, k_prolong_set<T>, dim3(nblk((L.n + 3) / 4)), dim3(kThreads), L.n, L.agg, eH, u, x));
     SLAUNCH(h);
+    if (timed) AMG_TRY(timing_record(h, &e1, 2));
     return residual<T>(h, k, x, r, s);
   }
   AMG_TRY(with_wps(L.wps, [&](auto W) {
@@ -766,7 +806,7 @@ static amg_status inner_fcg(amg_handle_s *h, int k) {
         prev.b[l] = (const T *)L.W[l];
       }
       prev.nd = it;
-      AMG_TRY(plaunch(h, st, k_orth_dots<T>, dim3(red_grid(n)), dim3(kThreads), n, D, W, prev, L.scal + 16, rin, h->red.partial,
+      AMG_TRY(plaunch(h, st, k_orth_dots<T>, dim3(red_grid(h, n)), dim3(kThreads), n, D, W, prev, L.scal + 16, rin, h->red.partial,
                                                         h->red.ticket, Fin{FIN_IALPHA, it, 0.0, L.scal}));
       SLAUNCH(h);
     }
@@ -812,7 +852,13 @@ static amg_status kcycle(amg_handle_s *h, int k, const T *r, T *x) {
   T *s = (T *)L.s, *u = (T *)L.u;
   AMG_TRY(smooth<T>(h, k, r, u, false));
   AMG_TRY(residual<T>(h, k, u, r, s));
-  AMG_TRY(restrict_to<T>(h, k, s, (T *)N.b, N.scal + 24));
+  {
+    const bool timed = h->timing.enabled && k == 0;
+    cudaEvent_t e0, e1;
+    if (timed) AMG_TRY(timing_record(h, &e0, 1));
+    AMG_TRY(restrict_to<T>(h, k, s, (T *)N.b, N.scal + 24));
+    if (timed) AMG_TRY(timing_record(h, &e1, 1));
+  }
   if (k + 1 == h->L - 1) AMG_TRY(coarse_solve<T>(h, (const T *)N.b, (T *)N.x));
   else if (k + 1 == h->leaf_k) AMG_TRY(launch_leaf(h));
   else AMG_TRY(inner_fcg<T>(h, k + 1));
@@ -1043,7 +1089,10 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     AMG_TRY(h->arena.get(&h->oQ[j], n0));
   }
   AMG_TRY(h->arena.get(&h->oscal, 256));
-  AMG_TRY(h->arena.get(&h->red.partial, (size_t)kRedBlocks * kMaxDots));
+  // partials for the largest reduction grid: one row per thread on level 0
+  h->red_cap = (int)std::max<int64_t>({(int64_t)kRedBlocks, (int64_t)sell_grid((int)h->n, 1),
+                                       ((int64_t)h->n + kThreads * kRedElems - 1) / (kThreads * kRedElems)});
+  AMG_TRY(h->arena.get(&h->red.partial, (size_t)h->red_cap * kMaxDots));
   AMG_TRY(h->arena.get(&h->red.ticket, 1));
   AMG_CUDA_TRY(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
   if (f32 && h->L >= 2) {
@@ -1196,20 +1245,17 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       AMG_TRY(plaunch(h, st, k_axpy_multi<double>, dim3(nblk(n)), dim3(kThreads), n, d, h->oz, vd, sc + 16));
       SLAUNCH(h);
     }
-    AMG_TRY(with_wps(L0.wps, [&](auto W) {
-      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, d, q);
-    }));
-    SLAUNCH(h);
     {
+      // q = A d with rho = d.q and sigma = d.r in the same pass
       DotSpec<double> sp{};
       sp.a[0] = d;
-      sp.b[0] = q;
+      sp.b[0] = nullptr;  // d . (A d)
       sp.a[1] = d;
       sp.b[1] = h->or_;
       sp.nd = 2;
-      AMG_TRY(dots<double>(h, n, sp, Fin{FIN_OALPHA, nwin, 0.0, sc}));
+      AMG_TRY(spmv_dots<double>(h, 0, d, q, sp, Fin{FIN_OALPHA, nwin, 0.0, sc}));
     }
-    AMG_TRY(plaunch(h, st, k_outer_update, dim3(red_grid(n)), dim3(kThreads), n, sc, d, q, x_dev, h->or_, h->red.partial,
+    AMG_TRY(plaunch(h, st, k_outer_update, dim3(red_grid(h, n)), dim3(kThreads), n, sc, d, q, x_dev, h->or_, h->red.partial,
                                                       h->red.ticket, Fin{FIN_STORE, 33, 0.0, sc}));
     SLAUNCH(h);
     AMG_CUDA_TRY(cudaMemcpyAsync(hp, sc + 33, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
