@@ -191,7 +191,7 @@ struct BatchLevel {
 // fused reduction state (deterministic two-stage: per-block partials, last
 // block folds them in block order)
 struct RedState {
-  double *partial = nullptr;   // [red_cap * kMaxDots]
+  double *partial = nullptr;   // [kRedBlocks * kMaxDots]
   unsigned int *ticket = nullptr;
 };
 
@@ -224,7 +224,6 @@ struct amg_handle_s {
   std::vector<amg::Level> lv;
   amg::Arena arena;
   amg::RedState red;
-  int red_cap = amg::kRedBlocks;     // blocks the reduction partials buffer holds
   // coarsest pseudo-inverse
   int nc = 0;
   double *Z = nullptr;

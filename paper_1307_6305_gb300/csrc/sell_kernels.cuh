@@ -110,23 +110,26 @@ __global__ void __launch_bounds__(kThreads) k_cheb_first(SellView<T> S, const T 
                                                          T *__restrict__ T1, T *__restrict__ x, T b0, T b1) {
   pdl_sync();
   int i;
-  T Sr;
+  T Sr, ri, xo = T(0);
   if constexpr (WPS == 1) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.n) return;
     Sr = apply_row(S, r, i);
+    ri = r[i];
+    if (ADD) xo = x[i];
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
     i = ix.i;
-    const T xi = i < S.n ? r[i] : T(0);
-    if (!split_row<T, WPS>(S, ix, xi, [&](int j) { return r[j]; }, Sr, part)) return;
+    // the row's own entries, read before the row sum (they do not depend on it)
+    ri = i < S.n ? r[i] : T(0);
+    if (ADD && ix.q == 0 && i < S.n) xo = x[i];
+    if (!split_row<T, WPS>(S, ix, ri, [&](int j) { return r[j]; }, Sr, part)) return;
   }
-  const T ri = r[i];
   const T t1 = T(0.5) * Sr;
   T1[i] = t1;
   const T inc = fma(b1, t1, b0 * ri);
-  x[i] = ADD ? x[i] + inc : inc;
+  x[i] = ADD ? xo + inc : inc;
 }
 
 // T_{j+1} = S T_j - T_{j-1}; x += bj * T_{j+1}.  Tn may alias Tp.
@@ -135,21 +138,29 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step(SellView<T> S, const T *
                                                         const T *Tp, T *Tn, T *__restrict__ x, T bj) {
   pdl_sync();
   int i;
-  T St;
+  T St, tp = T(0), xo = T(0);
   if constexpr (WPS == 1) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.n) return;
     St = apply_row(S, Tc, i);
+    tp = Tp[i];
+    xo = x[i];
   } else {
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
     i = ix.i;
+    // the row's own entries, read before the row sum (they do not depend on
+    // it); Tp[i] is read before Tn[i], which may alias it, is written
+    if (ix.q == 0 && i < S.n) {
+      tp = Tp[i];
+      xo = x[i];
+    }
     const T xi = i < S.n ? Tc[i] : T(0);
     if (!split_row<T, WPS>(S, ix, xi, [&](int j) { return Tc[j]; }, St, part)) return;
   }
-  const T tn = St - Tp[i];
+  const T tn = St - tp;
   Tn[i] = tn;
-  x[i] = fma(bj, tn, x[i]);
+  x[i] = fma(bj, tn, xo);
 }
 
 // smoother form of one level: sval = 2 sa val, sdiag = 2 sa diag - 2 ca
@@ -182,8 +193,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(SellView<T> A, const T *_
     __shared__ T part[kThreads / 32][32];
     const SplitIdx ix = split_index<WPS>(blockIdx.x);
     const T xi = ix.i < A.n ? x[ix.i] : T(0);
+    const T ri = (ix.q == 0 && ix.i < A.n) ? r[ix.i] : T(0);  // before the row sum
     T Ax;
-    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) s[ix.i] = r[ix.i] - Ax;
+    if (split_row<T, WPS>(A, ix, xi, [&](int j) { return x[j]; }, Ax, part)) s[ix.i] = ri - Ax;
   }
 }
 

@@ -213,23 +213,28 @@ __device__ void finalize(const Fin &f, const double *sums, int nd) {
 
 // per-thread partial sums -> per-block partials -> last block folds the
 // partials in block order (deterministic for a fixed grid) and finalises
+// (every step of a warp shuffle tree is a full-warp FP64 add, and this part's
+// FP64 pipe issues 2 lanes per clock: the block's partials go through shared
+// memory and one warp adds them -- 8 sequential adds and one 5-step tree per
+// dot instead of a tree in each of the 8 warps)
 template <int ND>
 __device__ __forceinline__ void reduce_and_finalize(const double (&acc)[ND], double *partial,
                                                     unsigned *ticket, const Fin &fin) {
-  __shared__ double sh[kThreads / 32][ND];
+  __shared__ double sh[ND][kThreads];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < ND; ++q) {
-    const double v = warp_sum(acc[q]);
-    if (lane == 0) sh[warp][q] = v;
-  }
+  for (int q = 0; q < ND; ++q) sh[q][threadIdx.x] = acc[q];
   __syncthreads();
-  if (threadIdx.x < ND) {
-    double v = 0.0;
+  if (warp == 0) {
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) v += sh[w][threadIdx.x];
-    partial[blockIdx.x * kMaxDots + threadIdx.x] = v;
+    for (int q = 0; q < ND; ++q) {
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) v += sh[q][w * 32 + lane];
+      v = warp_sum(v);
+      if (lane == 0) partial[blockIdx.x * kMaxDots + q] = v;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -247,24 +252,22 @@ __device__ __forceinline__ void reduce_and_finalize(const double (&acc)[ND], dou
 #pragma unroll
     for (int q = 0; q < ND; ++q) v[q] += __ldcg(&partial[b * kMaxDots + q]);
   }
-  const bool active = (unsigned)(warp * 32) < gridDim.x;  // warps holding partials
 #pragma unroll
-  for (int q = 0; q < ND; ++q) {
-    const double t = active ? warp_sum(v[q]) : 0.0;
-    if (lane == 0) sh[warp][q] = t;
-  }
+  for (int q = 0; q < ND; ++q) sh[q][threadIdx.x] = v[q];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     double sums[ND];
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
       double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) t += sh[w][q];
-      sums[q] = t;
+      for (int w = 0; w < kThreads / 32; ++w) t += sh[q][w * 32 + lane];
+      sums[q] = warp_sum(t);
     }
-    finalize(fin, sums, ND);
-    *ticket = 0u;
+    if (lane == 0) {
+      finalize(fin, sums, ND);
+      *ticket = 0u;
+    }
   }
 }
 
@@ -494,11 +497,13 @@ __global__ void k_identity(int n, double *__restrict__ X) {
 
 // ---------------------------------------------------------------------------
 // host side
-// blocks of a streaming reduction over n elements: one trip of kRedElems
-// elements per thread, capped by the partials buffer
+// blocks of a streaming reduction over n elements: trips of kRedElems
+// elements per thread, at most kRedBlocks blocks (each block ends with FP64
+// reduction work, so fewer, fuller blocks are cheaper on this part)
 static inline unsigned red_grid(const amg_handle_s *h, int64_t n) {
+  (void)h;
   const int64_t per = (int64_t)kThreads * kRedElems;
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->red_cap, (n + per - 1) / per));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + per - 1) / per));
 }
 
 // blocks of the SELL kernels: (slices x WPS) warps, kThreads / 32 per block
@@ -596,7 +601,7 @@ static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotS
   cudaStream_t st = h->stream;
   const SellView<T> A = view<T>(L);
   if (L.wps > 1 && spec.nd <= 2) {  // the inner solve's shapes (nu = 2) take the split form
-    const unsigned g = std::min<unsigned>((unsigned)h->red_cap, sell_grid(L.n, L.wps));
+    const unsigned g = std::min<unsigned>(kRedBlocks, sell_grid(L.n, L.wps));
     AMG_TRY(with_wps(L.wps, [&](auto W) {
       constexpr int wp = decltype(W)::value;
       if (spec.nd == 1) return plaunch(h, st, k_spmv_dots<T, 1, wp>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin);
@@ -605,8 +610,7 @@ static amg_status spmv_dots(amg_handle_s *h, int k, const T *x, T *y, const DotS
     SLAUNCH(h);
     return AMG_OK;
   }
-  // one row per thread: the SELL grid (the partials buffer holds it)
-  const unsigned g = std::min<unsigned>((unsigned)h->red_cap, sell_grid(L.n, 1));
+  const unsigned g = std::min<unsigned>(kRedBlocks, sell_grid(L.n, 1));
   switch (spec.nd) {
     case 1: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 1, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
     case 2: AMG_TRY(plaunch(h, st, k_spmv_dots<T, 2, 1>, dim3(g), dim3(kThreads), A, x, y, spec, P, tk, fin)); break;
@@ -1089,10 +1093,7 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     AMG_TRY(h->arena.get(&h->oQ[j], n0));
   }
   AMG_TRY(h->arena.get(&h->oscal, 256));
-  // partials for the largest reduction grid: one row per thread on level 0
-  h->red_cap = (int)std::max<int64_t>({(int64_t)kRedBlocks, (int64_t)sell_grid((int)h->n, 1),
-                                       ((int64_t)h->n + kThreads * kRedElems - 1) / (kThreads * kRedElems)});
-  AMG_TRY(h->arena.get(&h->red.partial, (size_t)h->red_cap * kMaxDots));
+  AMG_TRY(h->arena.get(&h->red.partial, (size_t)kRedBlocks * kMaxDots));
   AMG_TRY(h->arena.get(&h->red.ticket, 1));
   AMG_CUDA_TRY(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
   if (f32 && h->L >= 2) {
@@ -1245,15 +1246,21 @@ amg_status solve_one(amg_handle_s *h, const double *b_dev, double *x_dev, double
       AMG_TRY(plaunch(h, st, k_axpy_multi<double>, dim3(nblk(n)), dim3(kThreads), n, d, h->oz, vd, sc + 16));
       SLAUNCH(h);
     }
+    // q = A d (the one-row-per-thread SpMV), then rho = d.q and sigma = d.r:
+    // fused into one kernel the SpMV would run as a 608-block grid-stride
+    // loop, measured slower than the two
+    AMG_TRY(with_wps(L0.wps, [&](auto W) {
+      return plaunch(h, st, k_spmv<double, decltype(W)::value>, dim3(sell_grid(n, L0.wps)), dim3(kThreads), A0, d, q);
+    }));
+    SLAUNCH(h);
     {
-      // q = A d with rho = d.q and sigma = d.r in the same pass
       DotSpec<double> sp{};
       sp.a[0] = d;
-      sp.b[0] = nullptr;  // d . (A d)
+      sp.b[0] = q;
       sp.a[1] = d;
       sp.b[1] = h->or_;
       sp.nd = 2;
-      AMG_TRY(spmv_dots<double>(h, 0, d, q, sp, Fin{FIN_OALPHA, nwin, 0.0, sc}));
+      AMG_TRY(dots<double>(h, n, sp, Fin{FIN_OALPHA, nwin, 0.0, sc}));
     }
     AMG_TRY(plaunch(h, st, k_outer_update, dim3(red_grid(h, n)), dim3(kThreads), n, sc, d, q, x_dev, h->or_, h->red.partial,
                                                       h->red.ticket, Fin{FIN_STORE, 33, 0.0, sc}));
