@@ -287,7 +287,24 @@ __global__ void k_strength(int n, const int64_t *__restrict__ rp, const int32_t 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double di = diag[i];
-  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s[p] = -val[p] / sqrt(di * diag[col[p]]);
+  // chunks of entries whose loads are issued together
+  constexpr int kChunk = 8;
+  const int64_t end = rp[i + 1];
+  for (int64_t p0 = rp[i]; p0 < end; p0 += kChunk) {
+    int jj[kChunk];
+    double vv[kChunk], dd[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      const bool in = p0 + k < end;
+      jj[k] = in ? col[p0 + k] : -1;
+      vv[k] = in ? val[p0 + k] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) dd[k] = jj[k] >= 0 ? diag[jj[k]] : 1.0;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k)
+      if (p0 + k < end) s[p0 + k] = -vv[k] / sqrt(di * dd[k]);
+  }
 }
 
 __global__ void k_match_init(int n, int *mate) {
@@ -310,28 +327,45 @@ __global__ void k_propose(int n, const int64_t *__restrict__ rp, const int32_t *
     double bw = 0.0;
     uint64_t bh = 0;
     bool bh_ok = false;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      const int j = col[p];
-      if (mate[j] >= 0) continue;
-      const double wj = s[p];
-      if (best < 0) { best = j; bw = wj; bh_ok = false; continue; }
-      bool take;
-      if (wj != bw) {
-        take = wj > bw;
-      } else {
-        if (!bh_ok) { bh = edge_hash(salt, i, best); bh_ok = true; }
-        const uint64_t hj = edge_hash(salt, i, j);
-        if (hj != bh) {
-          take = hj > bh;
-        } else {
-          const int lj = min(i, j), hj2 = max(i, j), lb = min(i, best), hb = max(i, best);
-          take = (lj != lb) ? (lj > lb) : (hj2 > hb);
-        }
+    // entries are taken in stored order, in chunks whose loads (columns and
+    // strengths, then the neighbours' mates) are issued together
+    constexpr int kChunk = 8;
+    const int64_t end = rp[i + 1];
+    for (int64_t p0 = rp[i]; p0 < end; p0 += kChunk) {
+      int jj[kChunk], mm[kChunk];
+      double ww[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        const bool in = p0 + k < end;
+        jj[k] = in ? col[p0 + k] : -1;
+        ww[k] = in ? s[p0 + k] : 0.0;
       }
-      if (take) {
-        best = j;
-        bw = wj;
-        bh_ok = false;
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) mm[k] = jj[k] >= 0 ? mate[jj[k]] : 0;
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        const int j = jj[k];
+        if (j < 0 || mm[k] >= 0) continue;
+        const double wj = ww[k];
+        if (best < 0) { best = j; bw = wj; bh_ok = false; continue; }
+        bool take;
+        if (wj != bw) {
+          take = wj > bw;
+        } else {
+          if (!bh_ok) { bh = edge_hash(salt, i, best); bh_ok = true; }
+          const uint64_t hj = edge_hash(salt, i, j);
+          if (hj != bh) {
+            take = hj > bh;
+          } else {
+            const int lj = min(i, j), hj2 = max(i, j), lb = min(i, best), hb = max(i, best);
+            take = (lj != lb) ? (lj > lb) : (hj2 > hb);
+          }
+        }
+        if (take) {
+          best = j;
+          bw = wj;
+          bh_ok = false;
+        }
       }
     }
   }
@@ -484,58 +518,65 @@ __global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, M mb, int6
   len[I] = l;
 }
 // gather mapped entries of the coarse row into its segment, stable-sort by J,
-// count distinct J != I.  Rows of up to kLocalSort entries are sorted here by
-// their thread; longer rows are listed for k_gal_sort_long (up to kBlockSort,
-// bitonic in shared memory) or k_gal_sort_huge (radix through scratch).
+// count distinct J != I.  One thread per coarse row.  Rows of up to
+// kLocalSort entries keep their keys J in shared memory (the thread's own
+// column of the block's key table) and write each entry straight to its
+// place in the stable order: the number of entries with a smaller J, or the
+// same J and an earlier gather position.  Longer rows are written in gather
+// order and listed for k_gal_sort_long (up to kBlockSort entries, bitonic in
+// shared memory) or k_gal_sort_huge (radix through scratch).
 constexpr int kLocalSort = 64;
 constexpr int kBlockSort = 8192;  // longest row sorted in shared memory (128 KB)
+constexpr int kGatherThreads = 128;
 template <typename M>
-__global__ void k_pair_gather(int nH, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                              const double *__restrict__ val, const int *__restrict__ agg, M mb,
-                              const int64_t *__restrict__ seg, int *__restrict__ keyJ,
-                              double *__restrict__ kval, int *__restrict__ count, int *longrows, int *huge,
-                              unsigned long long *hugeoff) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kGatherThreads)
+    k_pair_gather(int nH, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                  const double *__restrict__ val, const int *__restrict__ agg, M mb,
+                  const int64_t *__restrict__ seg, int *__restrict__ keyJ, double *__restrict__ kval,
+                  int *__restrict__ count, int *longrows, int *huge, unsigned long long *hugeoff) {
+  __shared__ int sk[kLocalSort][kGatherThreads];  // 32 KB
+  const int t = threadIdx.x;
+  const int I = blockIdx.x * kGatherThreads + t;
   if (I >= nH) return;
   const int64_t s0 = seg[I];
-  int64_t t = s0;
-  for (int q = 0; q < mb.count(I); ++q) {
-    const int v = mb.get(I, q);
-    for (int64_t p = rp[v]; p < rp[v + 1]; ++p) {
-      keyJ[t] = agg[col[p]];
-      kval[t] = val[p];
-      ++t;
-    }
-  }
-  const int64_t len = t - s0;
+  const int64_t len = seg[I + 1] - s0;
+  const int nm = mb.count(I);
   if (len <= kLocalSort) {
-    // short row (the usual case): sort in a thread-local array
-    int lk[kLocalSort];
-    double lv[kLocalSort];
-    for (int a = 0; a < len; ++a) {
-      lk[a] = keyJ[s0 + a];
-      lv[a] = kval[s0 + a];
+    int a = 0;
+    for (int q = 0; q < nm; ++q) {
+      const int v = mb.get(I, q);
+      for (int64_t p = rp[v]; p < rp[v + 1]; ++p) sk[a++][t] = agg[col[p]];
     }
-    for (int a = 1; a < len; ++a) {  // stable insertion sort by J
-      const int kj = lk[a];
-      const double kv = lv[a];
-      int b = a - 1;
-      while (b >= 0 && lk[b] > kj) {
-        lk[b + 1] = lk[b];
-        lv[b + 1] = lv[b];
-        --b;
-      }
-      lk[b + 1] = kj;
-      lv[b + 1] = kv;
-    }
+    const int n = (int)len;
     int c = 0;
-    for (int a = 0; a < len; ++a) {
-      keyJ[s0 + a] = lk[a];
-      kval[s0 + a] = lv[a];
-      if (lk[a] != I && (a == 0 || lk[a - 1] != lk[a])) ++c;
+    a = 0;
+    for (int q = 0; q < nm; ++q) {
+      const int v = mb.get(I, q);
+      for (int64_t p = rp[v]; p < rp[v + 1]; ++p, ++a) {
+        const int Ja = sk[a][t];
+        int r = 0;
+        bool first = true;
+        for (int b = 0; b < n; ++b) {
+          const int Jb = sk[b][t];
+          const bool earlier_same = Jb == Ja && b < a;
+          r += (Jb < Ja || earlier_same) ? 1 : 0;
+          first = first && !earlier_same;
+        }
+        keyJ[s0 + r] = Ja;
+        kval[s0 + r] = val[p];
+        if (first && Ja != I) ++c;
+      }
     }
     count[I] = c;
     return;
+  }
+  int64_t o = s0;
+  for (int q = 0; q < nm; ++q) {
+    const int v = mb.get(I, q);
+    for (int64_t p = rp[v]; p < rp[v + 1]; ++p, ++o) {
+      keyJ[o] = agg[col[p]];
+      kval[o] = val[p];
+    }
   }
   if (longrows && len <= kBlockSort) {
     // long row: sorted by k_gal_sort_long, one block per row
@@ -958,9 +999,59 @@ __global__ void k_gj_step(int n, int p, const double *__restrict__ Min, double *
     out = (j == p) ? inv : Min[(int64_t)p * n + j] * inv;
   } else {
     const double f = Min[(int64_t)i * n + p];
-    out = (j == p) ? -f * inv : Min[(int64_t)i * n + j] - f * (Min[(int64_t)p * n + j] * inv);
+    out = (j == p) ? -f * inv : fma(-f, Min[(int64_t)p * n + j] * inv, Min[(int64_t)i * n + j]);
   }
   Mout[idx] = out;
+}
+
+// all n pivot steps of k_gj_step in one block with the matrix in shared
+// memory (coarsest levels of up to kGjShared rows).  Per step the pivot
+// column and the scaled pivot row t_j = a_pj / a_pp are formed once, then
+// every entry is replaced in place by the formula of k_gj_step (the same
+// operations in the same order, so the same result); thread (ty, tx) owns
+// column tx of rows ty, ty + 8, ...
+constexpr int kGjThreads = 512;
+constexpr int kGjShared = 64;
+__global__ void __launch_bounds__(kGjThreads) k_gj_shared(int n, const double *__restrict__ Min,
+                                                          double *__restrict__ Zout, double tiny,
+                                                          int *singular) {
+  __shared__ double a[kGjShared][kGjShared];
+  __shared__ double trow[kGjShared], pcol[kGjShared];
+  __shared__ double sinv;
+  const int tx = threadIdx.x % kGjShared, ty = threadIdx.x / kGjShared;
+  constexpr int kRowStep = kGjThreads / kGjShared;
+  for (int i = ty; i < n; i += kRowStep)
+    if (tx < n) a[i][tx] = Min[(int64_t)i * n + tx];
+  __syncthreads();
+  for (int p = 0; p < n; ++p) {
+    if (threadIdx.x == 0) {
+      const double piv = a[p][p];
+      if (!(piv > tiny)) *singular = 1;
+      sinv = 1.0 / piv;
+    }
+    __syncthreads();
+    const double inv = sinv;
+    if (threadIdx.x < n) {
+      trow[threadIdx.x] = a[p][threadIdx.x] * inv;
+      pcol[threadIdx.x] = a[threadIdx.x][p];
+    }
+    __syncthreads();
+    if (tx < n) {
+      for (int i = ty; i < n; i += kRowStep) {
+        double out;
+        if (i == p) {
+          out = (tx == p) ? inv : trow[tx];
+        } else {
+          const double f = pcol[i];
+          out = (tx == p) ? -f * inv : fma(-f, trow[tx], a[i][tx]);
+        }
+        a[i][tx] = out;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = ty; i < n; i += kRowStep)
+    if (tx < n) Zout[(int64_t)i * n + tx] = a[i][tx];
 }
 
 __global__ void k_unshift(int64_t nn, double c, double *__restrict__ Z) {
@@ -1055,8 +1146,8 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   AMG_CUDA_TRY(cudaMemsetAsync(longrows, 0, sizeof(int), st));
   AMG_CUDA_TRY(cudaMemsetAsync(huge, 0, sizeof(int), st));
   AMG_CUDA_TRY(cudaMemsetAsync(hugeoff, 0, sizeof(unsigned long long), st));
-  k_pair_gather<<<blocks_for(nH, 128), 128, 0, st>>>(nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, mb, seg, keyJ,
-                                                     kval, count, longrows, huge, hugeoff);
+  k_pair_gather<<<blocks_for(nH, kGatherThreads), kGatherThreads, 0, st>>>(
+      nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, mb, seg, keyJ, kval, count, longrows, huge, hugeoff);
   LAUNCH_CHECK(&h->launches);
   {
     // rows of more than kBlockSort entries, if any: their scratch is bounded
@@ -1461,10 +1552,16 @@ static amg_status build_coarsest(amg_handle_s *h) {
   for (double v : dg) maxdiag = std::max(maxdiag, v);
   const double tiny = 1e-13 * std::max(maxdiag, 1e-300);
   double *a = M, *b = h->Z;
-  for (int p = 0; p < n; ++p) {
-    k_gj_step<<<blocks_for(nn, 256), 256, 0, st>>>(n, p, a, b, tiny, sing);
+  if (n <= kGjShared) {
+    k_gj_shared<<<1, kGjThreads, 0, st>>>(n, M, h->Z, tiny, sing);
     LAUNCH_CHECK(&h->launches);
-    std::swap(a, b);
+    a = h->Z;
+  } else {
+    for (int p = 0; p < n; ++p) {
+      k_gj_step<<<blocks_for(nn, 256), 256, 0, st>>>(n, p, a, b, tiny, sing);
+      LAUNCH_CHECK(&h->launches);
+      std::swap(a, b);
+    }
   }
   if (a != h->Z) AMG_CUDA_TRY(cudaMemcpyAsync(h->Z, a, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
   if (h->pure) {

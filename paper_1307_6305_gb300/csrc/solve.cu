@@ -278,20 +278,29 @@ __global__ void __launch_bounds__(kThreads) k_dots(int64_t n, DotSpec<T> spec, d
   double acc[ND];
 #pragma unroll
   for (int q = 0; q < ND; ++q) acc[q] = 0.0;
-  // kRedElems elements per thread and trip, kThreads apart (coalesced, all
-  // loads of a trip in flight together); a grid of n / (kThreads kRedElems)
-  // blocks makes one trip
-  for (int64_t base = (int64_t)blockIdx.x * (kThreads * kRedElems) + threadIdx.x; base < n;
-       base += (int64_t)gridDim.x * (kThreads * kRedElems)) {
+  // E elements per thread and trip, kThreads apart (coalesced); all loads of
+  // a trip are issued before the first product (a null b operand reads as 1:
+  // a * 1 == a exactly).  Fewer elements per trip for many dots keep the
+  // registers of a thread below 128.
+  constexpr int E = ND <= 2 ? kRedElems : 2;
+  for (int64_t base = (int64_t)blockIdx.x * (kThreads * E) + threadIdx.x; base < n;
+       base += (int64_t)gridDim.x * (kThreads * E)) {
+    T av[ND][E], bv[ND][E];
 #pragma unroll
-    for (int u = 0; u < kRedElems; ++u) {
+    for (int u = 0; u < E; ++u) {
       const int64_t i = base + (int64_t)u * kThreads;
-      if (i < n) {
+      const bool in = i < n;
 #pragma unroll
-        for (int q = 0; q < ND; ++q) {
-          const double a = (double)spec.a[q][i];
-          acc[q] += spec.b[q] ? a * (double)spec.b[q][i] : a;
-        }
+      for (int q = 0; q < ND; ++q) {
+        av[q][u] = in ? spec.a[q][i] : T(0);
+        bv[q][u] = (in && spec.b[q]) ? spec.b[q][i] : T(1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      if (base + (int64_t)u * kThreads < n) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) acc[q] += (double)av[q][u] * (double)bv[q][u];
       }
     }
   }
@@ -334,29 +343,50 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dots(SellView<T> A, const T *
 }
 
 // inner step it > 0: D -= sum_l beta_l D_l, W -= sum_l beta_l W_l, then
-// rho = D.W and sigma = D.rin (FIN_IALPHA)
+// rho = D.W and sigma = D.rin (FIN_IALPHA); a trip's loads are issued before
+// its arithmetic
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_orth_dots(int64_t n, T *D, T *W, DotSpec<T> prev,
-                                                        const double *beta, const T *__restrict__ rin,
-                                                        double *partial, unsigned *ticket, Fin fin) {
+__global__ void __launch_bounds__(kThreads) k_orth_dots(int64_t n, T *__restrict__ D, T *__restrict__ W,
+                                                        DotSpec<T> prev, const double *beta,
+                                                        const T *__restrict__ rin, double *partial,
+                                                        unsigned *ticket, Fin fin) {
   pdl_sync();
   double acc[2] = {0.0, 0.0};
   for (int64_t base = (int64_t)blockIdx.x * (kThreads * kRedElems) + threadIdx.x; base < n;
        base += (int64_t)gridDim.x * (kThreads * kRedElems)) {
+    T d[kRedElems], w[kRedElems], ri[kRedElems];
+#pragma unroll
+    for (int u = 0; u < kRedElems; ++u) {
+      const int64_t i = base + (int64_t)u * kThreads;
+      const bool in = i < n;
+      d[u] = in ? D[i] : T(0);
+      w[u] = in ? W[i] : T(0);
+      ri[u] = in ? rin[i] : T(0);
+    }
+    for (int l = 0; l < prev.nd; ++l) {
+      const T bl = (T)beta[l];
+      T pa[kRedElems], pb[kRedElems];
+#pragma unroll
+      for (int u = 0; u < kRedElems; ++u) {
+        const int64_t i = base + (int64_t)u * kThreads;
+        const bool in = i < n;
+        pa[u] = in ? prev.a[l][i] : T(0);
+        pb[u] = in ? prev.b[l][i] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kRedElems; ++u) {
+        d[u] -= bl * pa[u];
+        w[u] -= bl * pb[u];
+      }
+    }
 #pragma unroll
     for (int u = 0; u < kRedElems; ++u) {
       const int64_t i = base + (int64_t)u * kThreads;
       if (i < n) {
-        T d = D[i], w = W[i];
-        for (int l = 0; l < prev.nd; ++l) {
-          const T bl = (T)beta[l];
-          d -= bl * prev.a[l][i];
-          w -= bl * prev.b[l][i];
-        }
-        D[i] = d;
-        W[i] = w;
-        acc[0] += (double)d * (double)w;
-        acc[1] += (double)d * (double)rin[i];
+        D[i] = d[u];
+        W[i] = w[u];
+        acc[0] += (double)d[u] * (double)w[u];
+        acc[1] += (double)d[u] * (double)ri[u];
       }
     }
   }
@@ -435,21 +465,33 @@ __global__ void k_inner_update(int64_t n, int it, bool upd_r, const double *sc, 
   if (upd_r) r[i] = stopped_here ? rin[i] : rin[i] - a * W[i];
 }
 
-// outer update: x += alpha d, r -= alpha q, then r.r
-__global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const double *sc, const double *d,
-                                                           const double *q, double *x, double *r,
-                                                           double *partial, unsigned *ticket, Fin fin) {
+// outer update: x += alpha d, r -= alpha q, then r.r (a trip's loads first)
+__global__ void __launch_bounds__(kThreads) k_outer_update(int64_t n, const double *sc,
+                                                           const double *__restrict__ d,
+                                                           const double *__restrict__ q, double *__restrict__ x,
+                                                           double *__restrict__ r, double *partial,
+                                                           unsigned *ticket, Fin fin) {
   pdl_sync();
   double acc[1] = {0.0};
   const double a = sc[32];
   for (int64_t base = (int64_t)blockIdx.x * (kThreads * kRedElems) + threadIdx.x; base < n;
        base += (int64_t)gridDim.x * (kThreads * kRedElems)) {
+    double dv[kRedElems], qv[kRedElems], xv[kRedElems], rv[kRedElems];
+#pragma unroll
+    for (int u = 0; u < kRedElems; ++u) {
+      const int64_t i = base + (int64_t)u * kThreads;
+      const bool in = i < n;
+      dv[u] = in ? d[i] : 0.0;
+      qv[u] = in ? q[i] : 0.0;
+      xv[u] = in ? x[i] : 0.0;
+      rv[u] = in ? r[i] : 0.0;
+    }
 #pragma unroll
     for (int u = 0; u < kRedElems; ++u) {
       const int64_t i = base + (int64_t)u * kThreads;
       if (i < n) {
-        x[i] = fma(a, d[i], x[i]);
-        const double ri = fma(-a, q[i], r[i]);
+        x[i] = fma(a, dv[u], xv[u]);
+        const double ri = fma(-a, qv[u], rv[u]);
         r[i] = ri;
         acc[0] += ri * ri;
       }
@@ -539,11 +581,11 @@ template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
 SellView<double> view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream_a};
 }
 template <>
 SellView<float> view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream_a};
 }
 
 template <typename T>
@@ -1027,6 +1069,10 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // policy (A/B timing of the streaming loads)
   const char *stream_env = getenv("AMG_GB300_STREAM");
   const bool stream_ok = !(stream_env && stream_env[0] == '0');
+  // AMG_GB300_STREAM_A=0: the operator's values stream only where the
+  // matrix alone reaches the threshold (A/B timing of the rule below)
+  const char *stream_a_env = getenv("AMG_GB300_STREAM_A");
+  const bool stream_a_ok = !(stream_a_env && stream_a_env[0] == '0');
   // AMG_GB300_WPS=w0,w1,...: warps per slice of levels 0, 1, ... (1, 2, 4 or
   // 8; A/B timing), the rule above for levels not listed
   std::vector<int> wps_force;
@@ -1046,6 +1092,13 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     // one pass over the level's stored values and columns is at least the
     // size of L2: stream it (the vectors and the coarser levels stay cached)
     V.stream = stream_ok && (double)V.S.stored * (double)(es + 4) >= kStreamMatrixBytes;
+    // a smoothing level holds two value arrays on one column array; when
+    // together they reach the threshold, the operator's values (read two or
+    // three times per visit) stream and the smoother form (read five times
+    // per sweep) stays cached
+    const bool smooths = k < L - 1 && h->opt.degree > 0;
+    V.stream_a = V.stream || (stream_ok && stream_a_ok && smooths &&
+                              (double)V.S.stored * (double)(2 * es + 4) >= kStreamMatrixBytes);
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1 && h->opt.degree > 0) {
       // the smoother form 2 t(A) of this level (Chebyshev kernels)
