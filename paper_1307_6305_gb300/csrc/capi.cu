@@ -642,9 +642,11 @@ amg_status amg_kernel_timing_read_kind(amg_handle h, int kind, int64_t *launches
     const double nnz = (double)L.A.nnz, n = (double)L.n, nH = (double)L.nH;
     if (kind == 0) {
       // one fused smoother step on level 0: the stored SELL entries (value +
-      // column index) and diagonal once, the gathered vector T_j once, and
-      // the row-wise vectors T_{j-1} (read), T_{j+1} (write), x (read + write)
-      *bytes_per_launch = nnz * (vs + 4.0) + (double)(L.S.nslices + 1) * 8.0 + n * vs * 6.0;
+      // column index, 4 bytes or a 2-byte offset) and diagonal once, the
+      // gathered vector T_j once, and the row-wise vectors T_{j-1} (read),
+      // T_{j+1} (write), x (read + write)
+      const double cs = L.S.sdel ? 2.0 : 4.0;
+      *bytes_per_launch = nnz * (vs + cs) + (double)(L.S.nslices + 1) * 8.0 + n * vs * 6.0;
     } else if (kind == 1) {
       // r_H = P^T s: the member lists (the fixed-width table, or offsets +
       // members), s once, r_H written

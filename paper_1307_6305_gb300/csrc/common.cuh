@@ -128,6 +128,10 @@ struct Sell {  // SELL-32 off-diagonal part + diagonal
   int64_t stored = 0;  // padded entries
   int64_t *sptr = nullptr;
   int32_t *scol = nullptr;
+  // the same columns as 16-bit offsets j - i from the row, on levels where
+  // every stored |j - i| fits (banded numberings): 2 bytes per entry less in
+  // the solve kernels; null elsewhere
+  int16_t *sdel = nullptr;
   double *val64 = nullptr;
   float *val32 = nullptr;
   double *diag64 = nullptr;
@@ -150,6 +154,8 @@ struct SellView {
   // so that one pass over it does not evict the vectors and the smaller
   // levels' working sets
   int stream = 0;
+  // columns as offsets from the row (Sell::sdel), or null: read scol
+  const int16_t *__restrict__ sdel = nullptr;
 };
 
 struct Level {

@@ -18,9 +18,21 @@ __device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict_
   const int s = row >> 5, lane = row & 31;
   const int64_t base = A.sptr[s];
   const int w = (int)((A.sptr[s + 1] - base) >> 5);
-  const int32_t *__restrict__ c = A.scol + base + lane;
   const T *__restrict__ v = A.val + base + lane;
-  if (A.stream) {  // uniform over the launch
+  // both choices are uniform over the launch
+  if (A.sdel) {  // columns as 16-bit offsets from the row
+    const int16_t *__restrict__ d = A.sdel + base + lane;
+    if (A.stream) {
+#pragma unroll 4
+      for (int k = 0; k < w; ++k) acc = fma(__ldcs(v + k * kSlice), x[row + __ldcs(d + k * kSlice)], acc);
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[row + d[k * kSlice]], acc);
+    }
+    return acc;
+  }
+  const int32_t *__restrict__ c = A.scol + base + lane;
+  if (A.stream) {
 #pragma unroll 4
     for (int k = 0; k < w; ++k) acc = fma(__ldcs(v + k * kSlice), x[__ldcs(c + k * kSlice)], acc);
   } else {
@@ -28,6 +40,12 @@ __device__ __forceinline__ T sell_row(const SellView<T> &A, const T *__restrict_
     for (int k = 0; k < w; ++k) acc = fma(v[k * kSlice], x[c[k * kSlice]], acc);
   }
   return acc;
+}
+
+// column of stored position pos of row `row` (either layout)
+template <typename T>
+__device__ __forceinline__ int sell_col(const SellView<T> &A, int64_t pos, int row) {
+  return A.sdel ? row + (int)A.sdel[pos] : A.scol[pos];
 }
 
 template <typename T>
@@ -65,10 +83,16 @@ __device__ __forceinline__ T split_partial(const SellView<T> &A, const SplitIdx 
   if (ix.i < A.n) {
     const int64_t base = A.sptr[ix.s];
     const int w = (int)((A.sptr[ix.s + 1] - base) >> 5);
-    const int32_t *__restrict__ c = A.scol + base + ix.lane;
     const T *__restrict__ v = A.val + base + ix.lane;
+    if (A.sdel) {
+      const int16_t *__restrict__ d = A.sdel + base + ix.lane;
 #pragma unroll 2
-    for (int k = ix.q; k < w; k += WPS) acc = fma(v[k * kSlice], xf(c[k * kSlice]), acc);
+      for (int k = ix.q; k < w; k += WPS) acc = fma(v[k * kSlice], xf(ix.i + d[k * kSlice]), acc);
+    } else {
+      const int32_t *__restrict__ c = A.scol + base + ix.lane;
+#pragma unroll 2
+      for (int k = ix.q; k < w; k += WPS) acc = fma(v[k * kSlice], xf(c[k * kSlice]), acc);
+    }
   }
   return acc;
 }

@@ -922,21 +922,37 @@ __global__ void k_norm_inf(int n, const int64_t *__restrict__ rp, const double *
 // ---------------------------------------------------------------------------
 // SELL-32 conversion
 // ---------------------------------------------------------------------------
+// slice widths, and the largest |j - i| of the level in *maxdel
 __global__ void k_sell_width(int n, int nslices, const int64_t *__restrict__ rp,
-                             int64_t *__restrict__ slen) {
+                             const int32_t *__restrict__ col, int64_t *__restrict__ slen,
+                             unsigned long long *maxdel) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int row = s * kSlice + lane;
   int deg = 0;
-  if (s < nslices && row < n) deg = (int)(rp[row + 1] - rp[row]);
+  unsigned dmax = 0;
+  if (s < nslices && row < n) {
+    deg = (int)(rp[row + 1] - rp[row]);
+    for (int64_t p = rp[row]; p < rp[row + 1]; ++p) {
+      const int64_t d = (int64_t)col[p] - row;
+      const int64_t a = d < 0 ? -d : d;
+      dmax = max(dmax, a > 0xffffffffll ? 0xffffffffu : (unsigned)a);
+    }
+  }
   deg = __reduce_max_sync(0xffffffffu, deg);
-  if (s < nslices && lane == 0) slen[s] = (int64_t)deg * kSlice;
+  dmax = __reduce_max_sync(0xffffffffu, dmax);
+  if (s < nslices && lane == 0) {
+    slen[s] = (int64_t)deg * kSlice;
+    if (dmax) atomicMax(maxdel, (unsigned long long)dmax);
+  }
 }
 
+// the SELL layout of a level; sdel (optional: every |j - i| of the level
+// fits 16 bits) receives the columns as offsets from the row as well
 __global__ void k_sell_fill(int n, int nslices, const int64_t *__restrict__ rp,
                             const int32_t *__restrict__ col, const double *__restrict__ val,
                             const int64_t *__restrict__ sptr, int32_t *__restrict__ scol,
-                            double *__restrict__ sval) {
+                            double *__restrict__ sval, int16_t *__restrict__ sdel) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = row >> 5, lane = row & 31;
   if (s >= nslices) return;
@@ -947,11 +963,13 @@ __global__ void k_sell_fill(int n, int nslices, const int64_t *__restrict__ rp,
     for (int64_t p = rp[row]; p < rp[row + 1]; ++p, ++k) {
       scol[base + (int64_t)k * kSlice + lane] = col[p];
       sval[base + (int64_t)k * kSlice + lane] = val[p];
+      if (sdel) sdel[base + (int64_t)k * kSlice + lane] = (int16_t)(col[p] - row);
     }
   }
   for (; k < w; ++k) {  // padding: zero weight on the row itself
     scol[base + (int64_t)k * kSlice + lane] = row < n ? row : 0;
     sval[base + (int64_t)k * kSlice + lane] = 0.0;
+    if (sdel) sdel[base + (int64_t)k * kSlice + lane] = 0;
   }
 }
 
@@ -1438,8 +1456,13 @@ static amg_status persist_level(amg_handle_s *h, const LevelBuild &b, amg::Level
 static amg_status build_sell_all(amg_handle_s *h, bool want32) {
   cudaStream_t st = h->stream;
   const int L = h->L;
-  int64_t *totals = nullptr;  // stored entries per level (device)
-  AMG_TRY(pool_alloc((void **)&totals, sizeof(int64_t) * (size_t)L, st));
+  // AMG_GB300_DELTA=0 keeps 32-bit columns on every level (A/B timing)
+  const char *delta_env = getenv("AMG_GB300_DELTA");
+  const bool delta_ok = !(delta_env && delta_env[0] == '0');
+  // per level: stored entries, then the largest |j - i| (device)
+  int64_t *totals = nullptr;
+  AMG_TRY(pool_alloc((void **)&totals, sizeof(int64_t) * (size_t)(2 * L), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(totals + L, 0, sizeof(int64_t) * (size_t)L, st));
   for (int k = 0; k < L; ++k) {
     amg::Level &V = h->lv[k];
     Sell &S = V.S;
@@ -1448,15 +1471,16 @@ static amg_status build_sell_all(amg_handle_s *h, bool want32) {
     int64_t *slen = nullptr;
     AMG_TRY(pool_alloc((void **)&slen, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
     AMG_CUDA_TRY(cudaMemsetAsync(slen, 0, sizeof(int64_t) * (size_t)(S.nslices + 1), st));
-    k_sell_width<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(V.n, S.nslices, V.A.rowptr, slen);
+    k_sell_width<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(
+        V.n, S.nslices, V.A.rowptr, V.A.col, slen, (unsigned long long *)(totals + L + k));
     LAUNCH_CHECK(&h->launches);
     AMG_TRY(alloc_persist(h, (void **)&S.sptr, sizeof(int64_t) * (size_t)(S.nslices + 1)));
     AMG_TRY(exclusive_scan_i64(slen, S.sptr, S.nslices + 1, st, nullptr));
     AMG_CUDA_TRY(cudaMemcpyAsync(totals + k, S.sptr + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     pool_free(slen, st);
   }
-  std::vector<int64_t> stored((size_t)L, 0);
-  AMG_CUDA_TRY(cudaMemcpyAsync(stored.data(), totals, sizeof(int64_t) * (size_t)L, cudaMemcpyDeviceToHost, st));
+  std::vector<int64_t> stored((size_t)(2 * L), 0);
+  AMG_CUDA_TRY(cudaMemcpyAsync(stored.data(), totals, sizeof(int64_t) * (size_t)(2 * L), cudaMemcpyDeviceToHost, st));
   AMG_CUDA_TRY(cudaStreamSynchronize(st));
   pool_free(totals, st);
   for (int k = 0; k < L; ++k) {
@@ -1465,8 +1489,11 @@ static amg_status build_sell_all(amg_handle_s *h, bool want32) {
     S.stored = stored[k];
     AMG_TRY(alloc_persist(h, (void **)&S.scol, sizeof(int32_t) * (size_t)std::max<int64_t>(S.stored, 1)));
     AMG_TRY(alloc_persist(h, (void **)&S.val64, sizeof(double) * (size_t)std::max<int64_t>(S.stored, 1)));
+    S.sdel = nullptr;
+    if (delta_ok && stored[L + k] <= 32767)
+      AMG_TRY(alloc_persist(h, (void **)&S.sdel, sizeof(int16_t) * (size_t)std::max<int64_t>(S.stored, 1)));
     k_sell_fill<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(V.n, S.nslices, V.A.rowptr, V.A.col,
-                                                                           V.A.val, S.sptr, S.scol, S.val64);
+                                                                           V.A.val, S.sptr, S.scol, S.val64, S.sdel);
     LAUNCH_CHECK(&h->launches);
     S.diag64 = V.diag;
     if (want32) {

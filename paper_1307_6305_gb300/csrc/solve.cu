@@ -420,21 +420,13 @@ __global__ void __launch_bounds__(kThreads) k_prolong_residual(SellView<T> A, co
   const int sl = i >> 5, lane = i & 31;
   const int64_t base = A.sptr[sl];
   const int w = (int)((A.sptr[sl + 1] - base) >> 5);
-  const int32_t *__restrict__ c = A.scol + base + lane;
   const T *__restrict__ v = A.val + base + lane;
   T acc = A.diag[i] * xi;
-  if (A.stream) {
 #pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-      const int j = __ldcs(c + k * kSlice);
-      acc = fma(__ldcs(v + k * kSlice), u[j] + eH[agg[j]], acc);
-    }
-  } else {
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-      const int j = c[k * kSlice];
-      acc = fma(v[k * kSlice], u[j] + eH[agg[j]], acc);
-    }
+  for (int k = 0; k < w; ++k) {
+    const int64_t pos = base + lane + (int64_t)k * kSlice;
+    const int j = sell_col(A, pos, i);
+    acc = fma(A.stream ? __ldcs(v + k * kSlice) : v[k * kSlice], u[j] + eH[agg[j]], acc);
   }
   s[i] = r[i] - acc;
 }
@@ -581,22 +573,22 @@ template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
 SellView<double> view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream_a};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream_a, L.S.sdel};
 }
 template <>
 SellView<float> view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream_a};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream_a, L.S.sdel};
 }
 
 template <typename T>
 static SellView<T> smoother_view(const amg::Level &L);
 template <>
 SellView<double> smoother_view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64, L.stream};
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64, L.stream, L.S.sdel};
 }
 template <>
 SellView<float> smoother_view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32, L.stream};
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32, L.stream, L.S.sdel};
 }
 
 // r_H = P^T s on level k (the fixed-width member table when the level has one)
