@@ -162,7 +162,6 @@ struct Level {
   int n = 0;
   int wps = 1;           // warps per SELL slice in the solve kernels (1, 2, 4 or 8)
   int stream = 0;        // matrix loads with the streaming cache policy (SellView::stream)
-  int stream_a = 0;      // the same for the operator's own values (residuals, products)
   Csr A;                 // setup form
   double *diag = nullptr;
   double *dlow = nullptr;

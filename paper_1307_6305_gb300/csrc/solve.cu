@@ -573,11 +573,11 @@ template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
 SellView<double> view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream_a, L.S.sdel};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream, L.S.sdel};
 }
 template <>
 SellView<float> view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream_a, L.S.sdel};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream, L.S.sdel};
 }
 
 template <typename T>
@@ -1061,10 +1061,6 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // policy (A/B timing of the streaming loads)
   const char *stream_env = getenv("AMG_GB300_STREAM");
   const bool stream_ok = !(stream_env && stream_env[0] == '0');
-  // AMG_GB300_STREAM_A=0: the operator's values stream only where the
-  // matrix alone reaches the threshold (A/B timing of the rule below)
-  const char *stream_a_env = getenv("AMG_GB300_STREAM_A");
-  const bool stream_a_ok = !(stream_a_env && stream_a_env[0] == '0');
   // AMG_GB300_WPS=w0,w1,...: warps per slice of levels 0, 1, ... (1, 2, 4 or
   // 8; A/B timing), the rule above for levels not listed
   std::vector<int> wps_force;
@@ -1084,13 +1080,6 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
     // one pass over the level's stored values and columns is at least the
     // size of L2: stream it (the vectors and the coarser levels stay cached)
     V.stream = stream_ok && (double)V.S.stored * (double)(es + 4) >= kStreamMatrixBytes;
-    // a smoothing level holds two value arrays on one column array; when
-    // together they reach the threshold, the operator's values (read two or
-    // three times per visit) stream and the smoother form (read five times
-    // per sweep) stays cached
-    const bool smooths = k < L - 1 && h->opt.degree > 0;
-    V.stream_a = V.stream || (stream_ok && stream_a_ok && smooths &&
-                              (double)V.S.stored * (double)(2 * es + 4) >= kStreamMatrixBytes);
     AMG_TRY(h->arena.alloc((void **)&V.scal, sizeof(double) * 64));
     if (k < L - 1 && h->opt.degree > 0) {
       // the smoother form 2 t(A) of this level (Chebyshev kernels)
