@@ -645,7 +645,7 @@ amg_status amg_kernel_timing_read_kind(amg_handle h, int kind, int64_t *launches
       // column index, 4 bytes or a 2-byte offset) and diagonal once, the
       // gathered vector T_j once, and the row-wise vectors T_{j-1} (read),
       // T_{j+1} (write), x (read + write)
-      const double cs = L.S.sdel ? 2.0 : 4.0;
+      const double cs = (L.S.sdel && L.wps == 1) ? 2.0 : 4.0;
       *bytes_per_launch = nnz * (vs + cs) + (double)(L.S.nslices + 1) * 8.0 + n * vs * 6.0;
     } else if (kind == 1) {
       // r_H = P^T s: the member lists (the fixed-width table, or offsets +

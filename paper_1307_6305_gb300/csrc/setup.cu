@@ -1453,6 +1453,10 @@ static amg_status persist_level(amg_handle_s *h, const LevelBuild &b, amg::Level
 // SELL-32 layout of every level in two stages, so that one read-back serves
 // all levels: (1) slice widths and their scan (slice pointers) per level,
 // totals left on the device; (2) with the totals known, the padded arrays.
+// levels of at least this many rows get 16-bit column offsets (when they
+// fit): the levels whose solve kernels run one row per thread
+constexpr int kDeltaMinRows = 1 << 17;
+
 static amg_status build_sell_all(amg_handle_s *h, bool want32) {
   cudaStream_t st = h->stream;
   const int L = h->L;
@@ -1490,7 +1494,7 @@ static amg_status build_sell_all(amg_handle_s *h, bool want32) {
     AMG_TRY(alloc_persist(h, (void **)&S.scol, sizeof(int32_t) * (size_t)std::max<int64_t>(S.stored, 1)));
     AMG_TRY(alloc_persist(h, (void **)&S.val64, sizeof(double) * (size_t)std::max<int64_t>(S.stored, 1)));
     S.sdel = nullptr;
-    if (delta_ok && stored[L + k] <= 32767)
+    if (delta_ok && V.n >= kDeltaMinRows && stored[L + k] <= 32767)
       AMG_TRY(alloc_persist(h, (void **)&S.sdel, sizeof(int16_t) * (size_t)std::max<int64_t>(S.stored, 1)));
     k_sell_fill<<<blocks_for((int64_t)S.nslices * 32, 256), 256, 0, st>>>(V.n, S.nslices, V.A.rowptr, V.A.col,
                                                                            V.A.val, S.sptr, S.scol, S.val64, S.sdel);

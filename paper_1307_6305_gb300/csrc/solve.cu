@@ -569,26 +569,32 @@ static amg_status with_wps(int wps, F f) {
   }
 }
 
+// 16-bit column offsets serve the one-row-per-thread kernels (bandwidth-
+// bound levels); the split kernels of small levels keep 32-bit columns
+// (with offsets they measured slower: one more step in each entry's
+// dependent load chain)
+static inline const int16_t *delta_cols(const amg::Level &L) { return L.wps == 1 ? L.S.sdel : nullptr; }
+
 template <typename T>
 static SellView<T> view(const amg::Level &L);
 template <>
 SellView<double> view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream, L.S.sdel};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val64, L.S.diag64, L.stream, delta_cols(L)};
 }
 template <>
 SellView<float> view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream, L.S.sdel};
+  return {L.n, L.S.sptr, L.S.scol, L.S.val32, L.S.diag32, L.stream, delta_cols(L)};
 }
 
 template <typename T>
 static SellView<T> smoother_view(const amg::Level &L);
 template <>
 SellView<double> smoother_view<double>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64, L.stream, L.S.sdel};
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval64, L.S.sdiag64, L.stream, delta_cols(L)};
 }
 template <>
 SellView<float> smoother_view<float>(const amg::Level &L) {
-  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32, L.stream, L.S.sdel};
+  return {L.n, L.S.sptr, L.S.scol, L.S.sval32, L.S.sdiag32, L.stream, delta_cols(L)};
 }
 
 // r_H = P^T s on level k (the fixed-width member table when the level has one)
