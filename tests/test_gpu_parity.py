@@ -305,6 +305,38 @@ def test_split_prolongation_equals_fused(amg, monkeypatch, precision, cycle):
     assert ls > lf          # the split form ran (one more launch per level-0 cycle)
 
 
+@pytest.mark.parametrize("precision,cycle", [(0, 0), (1, 0), (0, 1)])
+def test_column_offsets_equal_full_columns(amg, monkeypatch, precision, cycle):
+    """Levels of >= 2^17 rows whose every |j - i| fits 16 bits store their
+    columns also as offsets from the row, and the one-row-per-thread kernels
+    read those; the same entries are summed in the same order, so residual
+    histories and solutions equal those of the 32-bit columns bit for bit
+    (AMG_GB300_DELTA=0 keeps 32-bit columns everywhere).  The smoother step's
+    byte count (2 or 4 bytes per column) shows which layout ran."""
+    g = gg.grid3d_7pt(64, 1.0)
+    b = gg.rhs(g.n, 13, False)
+    runs = []
+    for delta in ("1", "0"):
+        monkeypatch.setenv("AMG_GB300_DELTA", delta)
+        gh = amg.Hierarchy.from_graph(g, mem_space=amg.AMG_MEM_DEVICE, degree=5, passes=3,
+                                      precision=precision, cycle=cycle)
+        assert gh.status == 0, gh.error
+        assert gh.level_n(0) >= 1 << 17
+        gh.kernel_timing(True)
+        x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        st, info, hist = gh.solve(cuda(b), x, tol=1e-8)
+        assert st == amg.AMG_OK, amg.amg_last_error(gh.h)
+        launches, _, bytes_per_launch = gh.kernel_timing_read()
+        assert launches > 0
+        runs.append((hist, x.cpu().numpy(), info.iterations, bytes_per_launch))
+        gh.close()
+    (h1, x1, i1, b1), (h0, x0, i0, b0) = runs
+    nnz = g.col.size  # stored off-diagonals of level 0
+    assert b0 - b1 == pytest.approx(2.0 * nnz)
+    assert i1 == i0
+    assert np.array_equal(h1, h0) and np.array_equal(x1, x0)
+
+
 @pytest.mark.parametrize("opts", [
     dict(degree=4, passes=3, lambda0_ratio=0.05),
     dict(degree=4, passes=3, hash_salt=0x9E3779B97F4A7C15),
