@@ -547,10 +547,12 @@ static inline unsigned sell_grid(int n, int wps) {
 }
 
 // Warps per slice for a level of n rows: the smallest of 1, 2, 4, 8 that
-// gives at least `per_sm` warps per SM (152 SMs; 32 unless
-// AMG_GB300_WPS_WARPS overrides -- measured on the 128^3 hierarchy: 16 / 32
-// / 64 / 128 give 36.5 / 36.2 / 37.8 / 37.7 ms per solve), so that small
-// levels spread their FP64 work and their dependent loads over the GPU.
+// gives at least `per_sm` warps per SM (152 SMs), so that small levels
+// spread their work and their dependent loads over the GPU.  per_sm is 16
+// for fp64 levels and 32 for fp32 (AMG_GB300_WPS_WARPS overrides): on the
+// 128^3 hierarchy these give the 45K-row level 2 and 4 warps per slice;
+// measured per solve, fp64 31.35-31.44 ms with 2 against 31.59-31.62 with 4,
+// fp32 24.42-24.45 ms with 4 against 24.98-25.06 with 2 (8: +0.8-0.9 ms).
 int choose_wps(int n, int per_sm) {
   const int64_t slices = (n + kSlice - 1) / kSlice;
   int w = 1;
@@ -1061,7 +1063,7 @@ amg_status allocate_solve_buffers(amg_handle_s *h) {
   // AMG_GB300_SPLIT=0 keeps one thread per row on every level
   const char *split_env = getenv("AMG_GB300_SPLIT");
   const bool split = !(split_env && split_env[0] == '0');
-  int per_sm = 32;
+  int per_sm = f32 ? 32 : 16;
   if (const char *e = getenv("AMG_GB300_WPS_WARPS")) per_sm = std::max(1, std::min(2048, atoi(e)));
   // AMG_GB300_STREAM=0 reads every level's matrix with the default cache
   // policy (A/B timing of the streaming loads)
