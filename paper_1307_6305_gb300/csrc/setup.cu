@@ -91,20 +91,20 @@ template <typename T>
 static amg_status scan_rec(const T *in, T *out, int64_t n, cudaStream_t st, T *total_dev) {
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb < 1) nb = 1;
-  T *bsum = nullptr;
+  if (nb == 1) {  // one tile: its block sum is the total
+    k_scan_tile<T><<<1, kScanThreads, 0, st>>>(in, out, total_dev, n);
+    LAUNCH_CHECK((int64_t *)nullptr);
+    return AMG_OK;
+  }
+  T *bsum = nullptr, *boff = nullptr;
   AMG_TRY(pool_alloc((void **)&bsum, sizeof(T) * nb, st));
   k_scan_tile<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, bsum, n);
   LAUNCH_CHECK((int64_t *)nullptr);
-  if (nb == 1) {
-    AMG_CUDA_TRY(cudaMemcpyAsync(total_dev, bsum, sizeof(T), cudaMemcpyDeviceToDevice, st));
-  } else {
-    T *boff = nullptr;
-    AMG_TRY(pool_alloc((void **)&boff, sizeof(T) * nb, st));
-    AMG_TRY(scan_rec<T>(bsum, boff, nb, st, total_dev));
-    k_scan_add<T><<<blocks_for(n, 256), 256, 0, st>>>(out, boff, n);
-    LAUNCH_CHECK((int64_t *)nullptr);
-    pool_free(boff, st);
-  }
+  AMG_TRY(pool_alloc((void **)&boff, sizeof(T) * nb, st));
+  AMG_TRY(scan_rec<T>(bsum, boff, nb, st, total_dev));
+  k_scan_add<T><<<blocks_for(n, 256), 256, 0, st>>>(out, boff, n);
+  LAUNCH_CHECK((int64_t *)nullptr);
+  pool_free(boff, st);
   pool_free(bsum, st);
   return AMG_OK;
 }
@@ -474,9 +474,11 @@ amg_status match_pass(cudaStream_t st, int n, const int64_t *rowptr, const int32
                     launches, kMatchBatch);
 }
 
+// b[i] = a[i] widened for i < n, and b[n] = 0 (the scan's last entry)
 __global__ void k_widen(int n, const int *a, int64_t *b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = a[i];
+  else if (i == n) b[n] = 0;
 }
 
 __global__ void k_max_abs(int n, const double *a, unsigned long long *out) {
@@ -506,9 +508,18 @@ struct ListMembers {
   __device__ int get(int I, int q) const { return mem[ptr[I] + q]; }
 };
 
+// segment lengths len[I] of the coarse rows (len[nH] = 0 for the scan), and
+// the gather's three list counters cleared on the way
 template <typename M>
-__global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, M mb, int64_t *__restrict__ len) {
+__global__ void k_pair_seglen(int nH, const int64_t *__restrict__ rp, M mb, int64_t *__restrict__ len,
+                              int *longrows, int *huge, unsigned long long *hugeoff) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I == 0) {
+    *longrows = 0;
+    *huge = 0;
+    *hugeoff = 0ull;
+  }
+  if (I == nH) len[nH] = 0;
   if (I >= nH) return;
   int64_t l = 0;
   for (int q = 0; q < mb.count(I); ++q) {
@@ -1144,9 +1155,14 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   int64_t *seglen = nullptr, *seg = nullptr;
   AMG_TRY(pool_alloc((void **)&seglen, sizeof(int64_t) * (size_t)(nH + 1), st));
   AMG_TRY(pool_alloc((void **)&seg, sizeof(int64_t) * (size_t)(nH + 1), st));
-  k_pair_seglen<<<nbH, 256, 0, st>>>(nH, cur.A.rowptr, mb, seglen);
+  int *longrows = nullptr, *huge = nullptr;  // [0]: count, then the rows
+  unsigned long long *hugeoff = nullptr;     // [0]: total length, then scratch offsets
+  AMG_TRY(pool_alloc((void **)&longrows, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&huge, sizeof(int) * (size_t)(nH + 1), st));
+  AMG_TRY(pool_alloc((void **)&hugeoff, sizeof(unsigned long long) * (size_t)(nH + 1), st));
+  k_pair_seglen<<<blocks_for((int64_t)nH + 1, 256), 256, 0, st>>>(nH, cur.A.rowptr, mb, seglen, longrows, huge,
+                                                                   hugeoff);
   LAUNCH_CHECK(&h->launches);
-  AMG_CUDA_TRY(cudaMemsetAsync(seglen + nH, 0, sizeof(int64_t), st));
   // every fine row belongs to exactly one aggregate: the segments hold the
   // fine level's entries, cur.A.nnz of them (or fewer when that is a bound)
   const int64_t segtot = cur.A.nnz;
@@ -1156,14 +1172,7 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   AMG_TRY(pool_alloc((void **)&keyJ, sizeof(int) * (size_t)std::max<int64_t>(segtot, 1), st));
   AMG_TRY(pool_alloc((void **)&kval, sizeof(double) * (size_t)std::max<int64_t>(segtot, 1), st));
   AMG_TRY(pool_alloc((void **)&count, sizeof(int64_t) * (size_t)(nH + 1), st));
-  int *longrows = nullptr, *huge = nullptr;  // [0]: count, then the rows
-  unsigned long long *hugeoff = nullptr;     // [0]: total length, then scratch offsets
-  AMG_TRY(pool_alloc((void **)&longrows, sizeof(int) * (size_t)(nH + 1), st));
-  AMG_TRY(pool_alloc((void **)&huge, sizeof(int) * (size_t)(nH + 1), st));
-  AMG_TRY(pool_alloc((void **)&hugeoff, sizeof(unsigned long long) * (size_t)(nH + 1), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(longrows, 0, sizeof(int), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(huge, 0, sizeof(int), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(hugeoff, 0, sizeof(unsigned long long), st));
+
   k_pair_gather<<<blocks_for(nH, kGatherThreads), kGatherThreads, 0, st>>>(
       nH, cur.A.rowptr, cur.A.col, cur.A.val, aggp, mb, seg, keyJ, kval, count, longrows, huge, hugeoff);
   LAUNCH_CHECK(&h->launches);
@@ -1191,8 +1200,7 @@ static amg_status galerkin(amg_handle_s *h, const LevelBuild &cur, const int *ag
   // widen counts to int64 for the row-offset scan
   int64_t *cnt64 = nullptr;
   AMG_TRY(pool_alloc((void **)&cnt64, sizeof(int64_t) * (size_t)(nH + 1), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(cnt64, 0, sizeof(int64_t) * (size_t)(nH + 1), st));
-  k_widen<<<nbH, 256, 0, st>>>(nH, count, cnt64);
+  k_widen<<<blocks_for((int64_t)nH + 1, 256), 256, 0, st>>>(nH, count, cnt64);
   LAUNCH_CHECK(&h->launches);
   next.A.n = nH;
   AMG_TRY(pool_alloc((void **)&next.A.rowptr, sizeof(int64_t) * (size_t)(nH + 1), st));
