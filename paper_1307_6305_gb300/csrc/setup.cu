@@ -139,10 +139,6 @@ amg_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaSt
 // matching rounds per batch (the first batch of a pass may be longer)
 constexpr int kCcBatch = 3;
 constexpr int kMatchBatch = 4;
-// passes of at least kListMinN vertices run rounds kListFrom, ... over a
-// list of the vertices still unmatched
-constexpr int kListMinN = 1 << 17;
-constexpr int kListFrom = 2;
 constexpr int kMatchMaxBatch = 16;
 
 // ---------------------------------------------------------------------------
@@ -316,119 +312,64 @@ __global__ void k_match_init(int n, int *mate) {
   if (i < n) mate[i] = -1;
 }
 
-// the proposal of unmatched vertex i: its largest-key edge to an unmatched
-// neighbour, key = (s_ij, hash, lo, hi) compared lexicographically (-1: none)
-__device__ __forceinline__ int propose_one(int i, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                           const double *__restrict__ s, uint64_t salt,
-                                           const int *__restrict__ mate) {
-  int best = -1;
-  double bw = 0.0;
-  uint64_t bh = 0;
-  bool bh_ok = false;
-  // entries are taken in stored order, in chunks whose loads (columns and
-  // strengths, then the neighbours' mates) are issued together
-  constexpr int kChunk = 8;
-  const int64_t end = rp[i + 1];
-  for (int64_t p0 = rp[i]; p0 < end; p0 += kChunk) {
-    int jj[kChunk], mm[kChunk];
-    double ww[kChunk];
-#pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-      const bool in = p0 + k < end;
-      jj[k] = in ? col[p0 + k] : -1;
-      ww[k] = in ? s[p0 + k] : 0.0;
-    }
-#pragma unroll
-    for (int k = 0; k < kChunk; ++k) mm[k] = jj[k] >= 0 ? mate[jj[k]] : 0;
-#pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-      const int j = jj[k];
-      if (j < 0 || mm[k] >= 0) continue;
-      const double wj = ww[k];
-      if (best < 0) { best = j; bw = wj; bh_ok = false; continue; }
-      bool take;
-      if (wj != bw) {
-        take = wj > bw;
-      } else {
-        if (!bh_ok) { bh = edge_hash(salt, i, best); bh_ok = true; }
-        const uint64_t hj = edge_hash(salt, i, j);
-        if (hj != bh) {
-          take = hj > bh;
-        } else {
-          const int lj = min(i, j), hj2 = max(i, j), lb = min(i, best), hb = max(i, best);
-          take = (lj != lb) ? (lj > lb) : (hj2 > hb);
-        }
-      }
-      if (take) {
-        best = j;
-        bw = wj;
-        bh_ok = false;
-      }
-    }
-  }
-  return best;
-}
-
-// one round's proposals over all vertices (matched ones point nowhere).
-// `prev` (optional) is the previous round's count of new pairs: once a round
-// has added none, the matching is maximal and later rounds do nothing.
+// each unmatched vertex points across its largest-key edge to an unmatched
+// neighbour; key = (s_ij, hash, lo, hi) compared lexicographically.  `prev`
+// (optional) is the previous round's count of new pairs: once a round has
+// added none, the matching is maximal and later rounds do nothing.
 __global__ void k_propose(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                           const double *__restrict__ s, uint64_t salt, const int *__restrict__ mate,
                           int *__restrict__ ptr, const int *prev) {
   if (prev && *prev == 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  ptr[i] = mate[i] < 0 ? propose_one(i, rp, col, s, salt, mate) : -1;
-}
-
-// Later rounds of a large pass run over a list of the vertices still
-// unmatched (a round's cost then follows the vertices left, not n; their
-// order in the list is arbitrary and does not matter: each vertex's proposal
-// and acceptance depend on the shared arrays only).  Matched vertices keep a
-// stale ptr entry, which no one reads: an unmatched vertex proposes only to
-// unmatched neighbours, which are in the list and propose afresh.
-__global__ void k_unmatched(int n, const int *__restrict__ mate, const int *prev, int *__restrict__ list,
-                            int *cnt) {
-  if (prev && *prev == 0) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool want = i < n && mate[i] < 0;
-  const unsigned bal = __ballot_sync(0xffffffffu, want);
-  if (!bal) return;
-  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(cnt, __popc(bal));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (want) list[base + __popc(bal & ((1u << lane) - 1u))] = i;
-}
-
-__global__ void k_propose_list(const int *__restrict__ list, const int *cnt, const int64_t *__restrict__ rp,
-                               const int32_t *__restrict__ col, const double *__restrict__ s, uint64_t salt,
-                               const int *__restrict__ mate, int *__restrict__ ptr, const int *prev) {
-  if (prev && *prev == 0) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= *cnt) return;
-  const int i = list[idx];
-  ptr[i] = propose_one(i, rp, col, s, salt, mate);
-}
-
-// acceptance over the list; also clears the counter the next round's list
-// is built in
-__global__ void k_accept_list(const int *__restrict__ list, const int *cnt, const int *__restrict__ ptr,
-                              int *__restrict__ mate, int *added, const int *prev, int *cnt_next) {
-  if (prev && *prev == 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *cnt_next = 0;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int hit = 0;
-  if (idx < *cnt) {
-    const int i = list[idx];
-    const int p = ptr[i];
-    if (p >= 0 && ptr[p] == i) {
-      mate[i] = p;
-      hit = 1;
+  int best = -1;
+  if (mate[i] < 0) {
+    double bw = 0.0;
+    uint64_t bh = 0;
+    bool bh_ok = false;
+    // entries are taken in stored order, in chunks whose loads (columns and
+    // strengths, then the neighbours' mates) are issued together
+    constexpr int kChunk = 8;
+    const int64_t end = rp[i + 1];
+    for (int64_t p0 = rp[i]; p0 < end; p0 += kChunk) {
+      int jj[kChunk], mm[kChunk];
+      double ww[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        const bool in = p0 + k < end;
+        jj[k] = in ? col[p0 + k] : -1;
+        ww[k] = in ? s[p0 + k] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) mm[k] = jj[k] >= 0 ? mate[jj[k]] : 0;
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        const int j = jj[k];
+        if (j < 0 || mm[k] >= 0) continue;
+        const double wj = ww[k];
+        if (best < 0) { best = j; bw = wj; bh_ok = false; continue; }
+        bool take;
+        if (wj != bw) {
+          take = wj > bw;
+        } else {
+          if (!bh_ok) { bh = edge_hash(salt, i, best); bh_ok = true; }
+          const uint64_t hj = edge_hash(salt, i, j);
+          if (hj != bh) {
+            take = hj > bh;
+          } else {
+            const int lj = min(i, j), hj2 = max(i, j), lb = min(i, best), hb = max(i, best);
+            take = (lj != lb) ? (lj > lb) : (hj2 > hb);
+          }
+        }
+        if (take) {
+          best = j;
+          bw = wj;
+          bh_ok = false;
+        }
+      }
     }
   }
-  hit = __syncthreads_count(hit);
-  if (threadIdx.x == 0 && hit) atomicAdd(added, hit);
+  ptr[i] = best;
 }
 
 __global__ void k_accept(int n, const int *__restrict__ ptr, int *__restrict__ mate, int *added,
@@ -488,36 +429,14 @@ static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, cons
   int rounds = 0;
   int64_t matched = 0;  // vertices matched so far (two per pair)
   int h_added[kMatchMaxBatch];
-  // large passes run their rounds from kListFrom on over the unmatched
-  // vertices only (two counters, cleared alternately by the rounds)
-  // (AMG_GB300_MATCH_LIST=0 runs every round over all vertices: A/B timing)
-  const char *list_env = getenv("AMG_GB300_MATCH_LIST");
-  const bool use_list = n >= kListMinN && !(list_env && list_env[0] == '0');
-  int *list = nullptr, *cnt = nullptr;
-  if (use_list) {
-    AMG_TRY(pool_alloc((void **)&list, sizeof(int) * (size_t)n, st));
-    AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * 2, st));
-    AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * 2, st));
-  }
   for (int batch = maxb;; batch = kMatchBatch) {
     AMG_CUDA_TRY(cudaMemsetAsync(added, 0, sizeof(int) * batch, st));
     for (int b = 0; b < batch; ++b) {
       const int *prev = b ? added + b - 1 : nullptr;
-      const int r = rounds + b;  // rounds of this pass before this one
-      if (use_list && r >= kListFrom) {
-        int *c = cnt + (r & 1), *c_next = cnt + ((r + 1) & 1);
-        k_unmatched<<<nb, 256, 0, st>>>(n, mate, prev, list, c);
-        LAUNCH_CHECK(launches);
-        k_propose_list<<<nb, 256, 0, st>>>(list, c, rowptr, col, s, salt, mate, ptr, prev);
-        LAUNCH_CHECK(launches);
-        k_accept_list<<<nb, 256, 0, st>>>(list, c, ptr, mate, added + b, prev, c_next);
-        LAUNCH_CHECK(launches);
-      } else {
-        k_propose<<<nb, 256, 0, st>>>(n, rowptr, col, s, salt, mate, ptr, prev);
-        LAUNCH_CHECK(launches);
-        k_accept<<<nb, 256, 0, st>>>(n, ptr, mate, added + b, prev);
-        LAUNCH_CHECK(launches);
-      }
+      k_propose<<<nb, 256, 0, st>>>(n, rowptr, col, s, salt, mate, ptr, prev);
+      LAUNCH_CHECK(launches);
+      k_accept<<<nb, 256, 0, st>>>(n, ptr, mate, added + b, prev);
+      LAUNCH_CHECK(launches);
     }
     AMG_CUDA_TRY(cudaMemcpyAsync(h_added, added, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
@@ -543,8 +462,6 @@ static amg_status match_core(cudaStream_t st, int n, const int64_t *rowptr, cons
   pool_free(added, st);
   pool_free(rep, st);
   pool_free(id, st);
-  pool_free(list, st);
-  pool_free(cnt, st);
   if (nH_out) *nH_out = (int)(n - matched / 2);
   if (rounds_out) *rounds_out = rounds;
   return AMG_OK;
